@@ -1,0 +1,203 @@
+"""Curvilinear steepest descent with Barzilai-Borwein steps (FP64 reference).
+
+Paper, Sec. 2.1-2.3:
+  * H(m) := -m x grad phi_t(m)                         (Sec. 2.1)
+  * m^{n+1} = m^n - tau (m^n + m^{n+1})/2 x H(m^n)     (Eq. 8, curvilinear search)
+    keeps |m^{n+1}| = |m^n| and has an explicit solution (cited to Goldfarb et
+    al.; the explicit form below is derived here, see `cayley`);
+  * g^n := m^n x (-m^n x grad phi_t(m^n)) = m^n x H(m^n), s^{n-1} = m^n - m^{n-1},
+    y^{n-1} = g^n - g^{n-1}; tau^1 = s.s/s.y, tau^2 = s.y/y.y            (Sec. 2.3)
+  * the first step by inexact line search; then BB steps chosen by the adaptive
+    rule from gradient-projection methods; a line search whenever the new energy
+    exceeds the previous 20 energies (nonmonotone globalisation)           (Sec. 2.3)
+  * hysteresis: the applied field is stepped and each point starts from the
+    previous minimum                                                      (Sec. 1.1, 3.1)
+
+Readings where the paper prints no detail:
+  * explicit update: with w = tau H/2 the implicit equation is x + x x w = m - m x w,
+    solved by x = [(1 - |w|^2) m - 2 m x w + 2 (m.w) w] / (1 + |w|^2);
+  * first trial step tau = 1 / max_i |H_i|;  Armijo test
+    E(tau) <= E_ref - c1 tau sum_i |g_i|^2 with c1 = 1e-4 (dE/dtau at 0 is
+    -sum |g|^2 because dY/dtau(0) = -m x H = -g), step halving, at most 30
+    halvings (then status LINESEARCH);
+  * nonmonotone test: a BB trial is rejected iff its energy is strictly larger
+    than the maximum of the last min(k, 20) accepted energies (the initial one
+    included); the line search then uses E_ref = that maximum;
+  * adaptive BB rule: if s.y <= 0 keep the previous step; else push tau^2 into a
+    memory of the last 3 values; if tau^2/tau^1 <= kappa take tau = min of that
+    memory and kappa *= 0.9, else tau = tau^1 and kappa *= 1.1; kappa_0 = 0.5;
+    tau clamped to [1e-10, 1e10];
+  * stop when max_i |m_i x h_i| / Js < tol (or, optionally, sum |g|^2 < tol_g,
+    the paper's grad h^T grad h < 1e-12 of Sec. 3.1);
+  * sweep: at every field point the step memory, the energy history and the
+    first-step line search start afresh.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .micromag import CubeProblem
+
+OK, MAX_ITER, LINESEARCH = 0, 1, 2
+
+
+@dataclass
+class StepRule:
+    c1: float = 1e-4
+    max_backtracks: int = 30
+    memory: int = 20
+    kappa0: float = 0.5
+    m_alpha: int = 3
+    tau_min: float = 1e-10
+    tau_max: float = 1e10
+
+
+def cayley(m: np.ndarray, H: np.ndarray, tau: float) -> np.ndarray:
+    """Explicit solution x of x = m - tau (m + x)/2 x H, row-wise."""
+    w = 0.5 * tau * H
+    ww = np.sum(w * w, axis=1, keepdims=True)
+    mw = np.sum(m * w, axis=1, keepdims=True)
+    return ((1.0 - ww) * m - 2.0 * np.cross(m, w) + 2.0 * mw * w) / (1.0 + ww)
+
+
+def bb_steps(s: np.ndarray, y: np.ndarray):
+    """(tau^1, tau^2) of the secant equation tau^-1 s = y, or None if s.y <= 0."""
+    sy = float(np.sum(s * y))
+    if sy <= 0.0:
+        return None
+    return float(np.sum(s * s)) / sy, sy / float(np.sum(y * y))
+
+
+@dataclass
+class BBState:
+    kappa: float
+    tau2: list = field(default_factory=list)
+
+
+def next_bb_tau(s, y, tau_prev: float, st: BBState, rule: StepRule) -> float:
+    steps = bb_steps(s, y)
+    if steps is None:
+        tau = tau_prev
+    else:
+        t1, t2 = steps
+        st.tau2.append(t2)
+        del st.tau2[:-rule.m_alpha]
+        if t2 / t1 <= st.kappa:
+            tau = min(st.tau2)
+            st.kappa *= 0.9
+        else:
+            tau = t1
+            st.kappa *= 1.1
+    return float(min(max(tau, rule.tau_min), rule.tau_max))
+
+
+@dataclass
+class Result:
+    m: np.ndarray
+    E: float
+    terms: dict
+    torque: float
+    status: int
+    iterations: int
+    evaluations: int
+    line_searches: int
+    trajectory: list = field(default_factory=list)
+    history: list = field(default_factory=list)      # accepted energies / E0
+
+
+def minimise(prob: CubeProblem, m0: np.ndarray, h_ext, tol: float = 1e-6, max_iter: int = 100000,
+             rule: StepRule | None = None, record=(), grad_tol: float | None = None) -> Result:
+    """Minimise phi_t from m0 at applied field h_ext (tesla).  `record` lists
+    iteration counts after which a copy of m is kept in `trajectory`."""
+    rule = rule or StepRule()
+    record = set(record)
+    m = np.array(m0, dtype=np.float64)
+    ev = prob.evaluate(m, h_ext)
+    evals = 1
+    H = -np.cross(m, ev.grad)
+    g = np.cross(m, H)
+    E0 = prob.E0                             # energies compared in the unit of grad phi
+    hist = [ev.E / E0]
+    traj = []
+    if 0 in record:
+        traj.append((0, m.copy()))
+
+    def converged(e, gg):
+        if grad_tol is not None:
+            return gg < grad_tol
+        return e.torque < tol
+
+    gg = float(np.sum(g * g))
+    if converged(ev, gg):
+        return Result(m, ev.E, ev.terms, ev.torque, OK, 0, evals, 0, traj, hist)
+    hmax = float(np.max(np.linalg.norm(H, axis=1)))
+    tau = 1.0 / hmax
+    searching, E_ref = True, ev.E / E0       # first step: inexact line search
+    backtracks, line_searches = 0, 1
+    bb = BBState(kappa=rule.kappa0)
+    it = 0
+    status = MAX_ITER
+    while it < max_iter:
+        mt = cayley(m, H, tau)
+        et = prob.evaluate(mt, h_ext)
+        evals += 1
+        phit = et.E / E0
+        if searching:
+            accept = phit <= E_ref - rule.c1 * tau * gg
+        else:
+            emax = max(hist[-rule.memory:])
+            accept = not (phit > emax)
+            if not accept:
+                searching, E_ref = True, emax
+                line_searches += 1
+                backtracks = 0
+        if not accept:
+            backtracks += 1
+            if backtracks > rule.max_backtracks:
+                status = LINESEARCH
+                break
+            tau *= 0.5
+            continue
+        Ht = -np.cross(mt, et.grad)
+        gt = np.cross(mt, Ht)
+        s, y = mt - m, gt - g
+        m, H, g, ev = mt, Ht, gt, et
+        gg = float(np.sum(g * g))
+        hist.append(phit)
+        it += 1
+        if it in record:
+            traj.append((it, m.copy()))
+        if converged(ev, gg):
+            status = OK
+            break
+        tau = next_bb_tau(s, y, tau, bb, rule)
+        searching, backtracks = False, 0
+    return Result(m, ev.E, ev.terms, ev.torque, status, it, evals, line_searches, traj, hist)
+
+
+def hysteresis(prob: CubeProblem, m0: np.ndarray, direction, fields, tol: float = 1e-6,
+               max_iter: int = 100000, rule: StepRule | None = None):
+    """Field continuation: minimise at each field value (tesla along `direction`),
+    warm-started from the previous minimum.  Returns per-point V-weighted
+    m.direction, energy, and the list of results."""
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    m = np.array(m0, dtype=np.float64)
+    mpar, energy, results = [], [], []
+    for hv in fields:
+        r = minimise(prob, m, hv * d, tol=tol, max_iter=max_iter, rule=rule)
+        m = r.m
+        mpar.append(float(prob.mean_m(m) @ d))
+        energy.append(r.E)
+        results.append(r)
+    return np.array(mpar), np.array(energy), results
+
+
+def switching_field(fields, mpar) -> float | None:
+    """First field value at which the mean projection changes sign."""
+    for k in range(1, len(fields)):
+        if np.sign(mpar[k]) != np.sign(mpar[k - 1]) and mpar[k - 1] != 0.0:
+            return float(fields[k])
+    return None
