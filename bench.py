@@ -1,0 +1,348 @@
+"""Benchmark: batched mixed-precision minimisation throughput (solves/s) on GB300.
+
+Workload (default): 64 independent minimisation problems on one 60 nm cube
+(30^3 cells, 6 Kuhn tetrahedra per cell, 29 791 nodes, 5 402 surface nodes),
+Nd2Fe14B, applied fields U[-8,0] T along z and easy-axis tilts U[0,5] deg drawn
+from seed 4, m0 = +z perturbed; each solve runs the curvilinear steepest-descent
+minimiser to max|m x h_eff|/Js < 1e-6.  One step = set m0 (device resident) and
+minimise the whole batch.  Inputs are synthetic (seeded), shaped like the
+paper's permanent-magnet grain workload.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+the host cores instead (bounded sample per step, same metric).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth.inputs import A_JM, JS_T, K1_JM3, batched_case  # noqa: E402
+
+METRIC = "solves/s, batched mixed-prec vs plain FP64 on GB300 at <=1e-6 rel energy; p50/p99 ms"
+N_CELLS = 30
+BATCH = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "fp64"])
+    ap.add_argument("--fp64-sample", type=int, default=4,
+                    help="instances of the plain-FP64 single-instance comparison arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(insts, evals_per_solve, budget_s):
+    """Time the FP64 oracle on one instance of the workload: field evaluations
+    and steps for about `budget_s` seconds (set-up -- assembly, BEM, LU -- is
+    excluded, as in the paper's CPU timings), scaled to solves/s with the
+    evaluations per solve measured on the GPU."""
+    from oracle.micromag import CubeProblem
+    from oracle.minimise import minimise
+    inst = insts[0]
+    p = CubeProblem(inst.n, inst.Js, inst.A, inst.K1, inst.axis)
+    t0 = time.perf_counter()
+    done_evals = 0
+    chunk = 8
+    m = inst.m0
+    while time.perf_counter() - t0 < budget_s:
+        r = minimise(p, m, inst.h_ext, tol=1e-6, max_iter=chunk)
+        done_evals += r.evaluations
+        m = r.m
+        if r.status == 0:
+            m = inst.m0
+    dt = time.perf_counter() - t0
+    per_eval = dt / max(done_evals, 1)
+    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or "1"
+    return {"value": 1.0 / (per_eval * evals_per_solve), "unit": "solves/s", "cores": int(threads),
+            "kind": "oracle",
+            "sample": (f"FP64 numpy/scipy oracle, one instance of the {N_CELLS}^3-cell workload: "
+                       f"{done_evals} energy-gradient evaluations in {dt:.1f} s "
+                       f"({per_eval * 1e3:.1f} ms each, set-up excluded), scaled by "
+                       f"{evals_per_solve:.0f} evaluations per solve measured on the GPU")}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    insts = batched_case(N_CELLS, BATCH, seed=4)
+    from oracle.micromag import CubeProblem
+    from oracle.minimise import minimise
+    inst = insts[0]
+    p = CubeProblem(inst.n, inst.Js, inst.A, inst.K1, inst.axis)
+    per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    total_evals = 0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ev = 0
+        m = inst.m0
+        while time.perf_counter() - t0 < per_step:
+            r = minimise(p, m, inst.h_ext, tol=1e-6, max_iter=8)
+            ev += r.evaluations
+            m = r.m if r.status != 0 else inst.m0
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            vals.append(dt / ev)
+            total_evals += ev
+    # evaluations per solve of this workload (GPU-measured, FP64 path, mean over the batch)
+    evals_per_solve = float(os.environ.get("LBM_EVALS_PER_SOLVE", "600"))
+    per_eval = float(np.mean(vals))
+    value = 1.0 / (per_eval * evals_per_solve)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_eval * evals_per_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched same-mesh, {BATCH} instances, {N_CELLS}^3-cell cube",
+                       "n": N_CELLS, "batch": BATCH},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{total_evals} oracle evaluations over {args.steps} steps of "
+                                       f"{per_step:.0f} s; scaled by {evals_per_solve:.0f} "
+                                       f"evaluations per solve"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def pcg_bytes_per_instance_iter(N, tsize):
+    # z gather, p rw, q rw, x rw, r rw, p, q read, z write: 12 vector words per node
+    return 12 * tsize * N
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1309_5796_gb300 as lbm
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = {"mixed": lbm.LBM_MIXED, "mixed_tc": lbm.LBM_MIXED_TC, "fp64": lbm.LBM_FP64}[args.precision]
+    stream = torch.cuda.current_stream()
+    ctx = lbm.Context(local, stream=stream.cuda_stream)
+    insts = batched_case(N_CELLS, BATCH, seed=4)
+    mesh = ctx.mesh_cube(2e-9, N_CELLS)
+    info = ctx.mesh_info(mesh)
+    N = info["N"]
+    inst = ctx.instance_create(mesh, BATCH, prec)
+    axes = np.stack([i.axis for i in insts])
+    fields = np.stack([i.h_ext for i in insts])
+    inst.set_material(JS_T, A_JM, K1_JM3, axes)
+    inst.set_field(fields)
+    m0_host = np.stack([i.m0 for i in insts])
+    m0_dev = torch.from_numpy(m0_host).to(f"cuda:{local}")
+    opts = lbm.default_opts(prec)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def step():
+        inst.set_m_device(m0_dev.data_ptr())
+        return inst.minimise(opts)
+
+    for _ in range(args.warmup):
+        res = step()
+    bad = [r["status"] for r in res if r["status"] != 0]
+    ctx.profile_read(reset=True)
+    ctx.profile_enable(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    step_ms = []
+    evals = []
+    for _ in range(args.steps):
+        flush.zero_()                                 # L2 flush between timed steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        evals.extend(r["evaluations"] for r in res)
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    clocks = sampler.stop()
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * BATCH * args.steps / total_s
+    final_res = res
+
+    # end to end through the public API with host buffers (H2D of m0, D2H of m)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inst.set_m(m0_host)
+        inst.minimise(opts)
+        m_out = inst.get_m()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = ws * BATCH / (statistics.mean(e2e_ms) / 1e3)
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (the potential solves)
+    tsize = 8 if prec == lbm.LBM_FP64 else 4
+    pcg_ms = prof["pcg_neumann"]["ms"] + prof["pcg_dirichlet"]["ms"]
+    pcg_launches = prof["pcg_neumann"]["launches"] + prof["pcg_dirichlet"]["launches"]
+    it_total = prof["cg_iters"][0] + prof["cg_iters"][1]
+    pcg_bytes = it_total * pcg_bytes_per_instance_iter(N, tsize)
+    achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    kinds = {k: v for k, v in prof.items() if k != "cg_iters"}
+    total_kernel_ms = sum(v["ms"] for v in kinds.values())
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(insts, statistics.mean(evals), args.cpu_sample_s)
+
+    fp64_arm = None
+    if args.fp64_sample > 0 and prec != lbm.LBM_FP64:
+        single = ctx.instance_create(mesh, 1, lbm.LBM_FP64)
+        o64 = lbm.default_opts(lbm.LBM_FP64)
+        t_fp64 = []
+        e_err = []
+        for b in range(args.fp64_sample):
+            single.set_material(JS_T, A_JM, K1_JM3, axes[b])
+            single.set_field(fields[b])
+            single.set_m(m0_host[b])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r64 = single.minimise(o64)[0]
+            t_fp64.append(time.perf_counter() - t0)
+            Eref = r64["energy"][4]
+            Kd = JS_T ** 2 / (2 * 4e-7 * math.pi)
+            scale = max(abs(Eref), Kd * (N_CELLS * 2e-9) ** 3)
+            e_err.append(abs(final_res[b]["energy"][4] - Eref) / scale)
+        fp64_arm = {"solves_per_s": 1.0 / statistics.mean(t_fp64), "instances_timed": args.fp64_sample,
+                    "max_rel_energy_err_batched_vs_fp64": max(e_err)}
+        single.destroy()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "mixed_tc": "f32+tf32x3+f64", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"batched same-mesh: {BATCH} instances on a {N_CELLS}^3-cell "
+                               f"(60 nm) Kuhn cube, {N} nodes, {info['nb']} surface nodes",
+                   "n": N_CELLS, "batch": BATCH, "precision": args.precision, "tol": 1e-6,
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "statuses_nonzero": bad,
+        "evaluations_per_solve": statistics.mean(evals),
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "kernel": "k_pcg (potential solves)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                     "bytes_per_launch": pcg_bytes / max(pcg_launches, 1),
+                     "avg_launch_ms": pcg_ms / max(pcg_launches, 1),
+                     "share_of_kernel_time": pcg_ms / total_kernel_ms if total_kernel_ms else None},
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()},
+        "cpu_baseline": cpu,
+        "fp64_single_instance": fp64_arm,
+        "e2e": {"value": e2e_value, "unit": "solves/s",
+                "h2d_bytes_per_step": int(m0_host.nbytes), "d2h_bytes_per_step": int(m_out.nbytes)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * lbm.h -- C ABI of the GB300 curvilinear steepest-descent micromagnetic minimiser.
+ *
+ * Method: Exl, Bance, Reichel, Schrefl, Stimming, Mauser, "LaBonte's method
+ * revisited: An effective steepest descent method for micromagnetic energy
+ * minimization" (arXiv:1309.5796).  Every entry point below names the passage
+ * of the paper that defines what it computes.
+ *
+ * Conventions for every call:
+ *   - The return value is a status code (LBM_OK = 0 or one of LBM_E_*).  No C++
+ *     exception crosses this interface.  lbm_last_error() returns a
+ *     thread-local message describing the last failure of this thread.
+ *   - Host pointers are owned by the caller; the library copies what it needs
+ *     and never keeps them.  Device memory is owned by the library (allocated
+ *     at mesh/instance creation and freed by the matching destroy call or by
+ *     lbm_destroy).
+ *   - Units are SI.  Applied and effective fields are mu0*H in tesla; energies
+ *     are in joule; lengths in metre.  Magnetisation arrays are unit vectors,
+ *     node-major: m[(b*N + i)*3 + c] for instance b, node i, component c.
+ *   - A context is bound to one CUDA device and one stream.  Calls on one
+ *     context must not be made concurrently from several threads.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define LBM_OK               0
+#define LBM_E_INVALID        1   /* bad argument or handle */
+#define LBM_E_OOM            2   /* device or host allocation failed */
+#define LBM_E_NOT_CONVERGED  3   /* iteration limit reached before the stop test */
+#define LBM_E_NAN            4   /* non-finite energy or field */
+#define LBM_E_TIMEOUT        5   /* a device-side wait ran out of time (kernel returned) */
+#define LBM_E_LINESEARCH     6   /* the step-halving line search gave up */
+#define LBM_E_CUDA           7   /* CUDA runtime error */
+
+/* ---- precision modes ---------------------------------------------------------- */
+#define LBM_FP64      0  /* every vector, field and reduction in FP64 */
+#define LBM_MIXED     1  /* FP32 node vectors, SpMV, potential solves and BEM
+                            product; FP64 reductions (dots, energy, stop test,
+                            CG residual norms) */
+#define LBM_MIXED_TC  2  /* as LBM_MIXED, BEM product on the tensor cores
+                            (3xTF32 split, FP32 accumulation) when batch > 1 */
+
+typedef struct lbm_ctx lbm_ctx;
+typedef int64_t lbm_mesh;   /* mesh handle (> 0) */
+typedef int64_t lbm_inst;   /* instance-batch handle (> 0) */
+
+/* Material of one instance (Sec. 3.1 uses Nd2Fe14B). */
+typedef struct {
+    double Js;        /* saturation polarisation mu0*Ms (T) */
+    double A;         /* exchange constant (J/m) */
+    double K1;        /* uniaxial anisotropy constant (J/m^3) */
+    double axis[3];   /* easy axis (normalised by the library) */
+} lbm_material;
+
+/* Options of the minimiser (Sec. 2.3 step rules; Sec. 3.1 stop test). */
+typedef struct {
+    double  tol;            /* stop when max_i |m_i x h_i| / Js < tol */
+    double  grad_tol;       /* > 0: stop when sum_i |g_i|^2 < grad_tol instead
+                               (the paper's grad h^T grad h test, Sec. 3.1) */
+    int32_t max_iter;       /* accepted steps per minimisation */
+    double  cg_tol;         /* relative residual |r|/|b| of both potential solves */
+    int32_t cg_max_iter;    /* iteration cap of each potential solve */
+    double  c1;             /* Armijo constant of the line search */
+    int32_t max_backtracks; /* step halvings before LBM_E_LINESEARCH */
+    int32_t memory;         /* nonmonotone memory (20 in Sec. 2.3) */
+    double  kappa0;         /* initial threshold of the adaptive BB1/BB2 rule */
+    int32_t m_alpha;        /* memory of the BB2 values in that rule */
+    double  tau_min, tau_max;
+    int32_t demag;          /* 1: stray field on (default), 0: off */
+    int32_t check_every;    /* host polls convergence every this many steps */
+} lbm_solve_opts;
+
+/* Per-instance outcome of a minimisation or an evaluation. */
+typedef struct {
+    int32_t status;         /* LBM_OK, LBM_E_NOT_CONVERGED, LBM_E_LINESEARCH, LBM_E_NAN */
+    int32_t iterations;     /* accepted steps */
+    int32_t evaluations;    /* energy-gradient evaluations (incl. the initial one) */
+    int32_t line_searches;  /* times the line search was entered */
+    int64_t cg_iters1;      /* total iterations of the Neumann (u1) solves */
+    int64_t cg_iters2;      /* total iterations of the Dirichlet (u2) solves */
+    double  energy[5];      /* exchange, anisotropy, Zeeman, stray field, total (J) */
+    double  torque;         /* max_i |m_i x h_i| / Js at the final state */
+    double  gg;             /* sum_i |g_i|^2 (units of Kd h^3) */
+    double  mean_m[3];      /* volume-weighted mean magnetisation */
+    double  wall_ms;        /* host wall time of the call (whole batch) */
+} lbm_result;
+
+/* Fill `o` with the defaults for `precision` (tol 1e-6, memory 20, c1 1e-4,
+ * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-7 mixed). */
+void lbm_default_opts(lbm_solve_opts* o, int32_t precision);
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t
+ * (NULL: the library creates its own non-blocking stream). */
+int lbm_create(lbm_ctx** out, int32_t device, void* stream);
+int lbm_destroy(lbm_ctx* ctx);
+const char* lbm_last_error(void);
+
+/* ---- meshes (Sec. 2.1: standard linear tetrahedral finite elements) ---------- */
+
+/* Canonical Kuhn-split cube: n^3 cubic cells of edge `cell_m`, 6 tetrahedra per
+ * cell, node (i,j,k) -> id i + (n+1)(j + (n+1)k).  Builds on the device the
+ * CSR pattern, the integer stiffness/divergence/volume tables, the boundary
+ * lists and the dense double-layer BEM matrix (FP64 and FP32).
+ * 1 <= n <= 96.  Device memory: about 12*nb^2 + 17*nnz + 40*N bytes. */
+int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out);
+int lbm_mesh_destroy(lbm_ctx* ctx, lbm_mesh mesh);
+
+/* info[0..7] = N, nb, nnz, tets, boundary triangles, device bytes, n, 0. */
+int lbm_mesh_info(lbm_ctx* ctx, lbm_mesh mesh, int64_t info[8]);
+
+/* Host copies of the assembled tables (any pointer may be NULL):
+ *   tets[T*4], rowptr[N+1], col[nnz] (node ids, boundary flag removed),
+ *   kval[nnz] (K in units h/6), gval[nnz*3] (G_ij in units h^2/24),
+ *   gtval[nnz*3] (G_ji), vol[N] (V in units h^3/24), bnd[nb] (ascending ids),
+ *   tris[F*3] (outward surface triangles, node ids). */
+int lbm_mesh_export(lbm_ctx* ctx, lbm_mesh mesh, int32_t* tets, int32_t* rowptr, int32_t* col,
+                    int32_t* kval, int32_t* gval, int32_t* gtval, int32_t* vol, int32_t* bnd,
+                    int32_t* tris);
+
+/* Rows row0..row0+nrows-1 of the FP64 double-layer matrix B (nb columns each),
+ * u2|S = B u1|S of the hybrid FEM/BEM open boundary (Sec. 3.1). */
+int lbm_bem_rows(lbm_ctx* ctx, lbm_mesh mesh, int64_t row0, int64_t nrows, double* out);
+
+/* ---- instances (Eq. 1: min phi_t(m) s.t. |m| = 1) ----------------------------- */
+
+/* A batch of `batch` independent problems on one mesh, solved together
+ * (1 <= batch <= 256).  m starts at +z, fields at zero, potentials at zero. */
+int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t precision,
+                        lbm_inst* out);
+int lbm_instance_destroy(lbm_ctx* ctx, lbm_inst inst);
+int lbm_set_material(lbm_ctx* ctx, lbm_inst inst, const lbm_material* mats /* [batch] */);
+int lbm_set_field(lbm_ctx* ctx, lbm_inst inst, const double* h /* [batch*3], tesla */);
+int lbm_set_m(lbm_ctx* ctx, lbm_inst inst, const double* m /* [batch*N*3] host */);
+int lbm_get_m(lbm_ctx* ctx, lbm_inst inst, double* m /* [batch*N*3] host */);
+
+/* Energy and effective field at the current m (Eq. 1 terms; h_eff of Sec. 2.2).
+ * h (nullable): [batch*N*3] mu0*h_eff in tesla; u (nullable): [batch*2*N]
+ * potentials u1, u2 in metres (U = Ms u).  res (nullable): [batch]. */
+int lbm_evaluate(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, double* h, double* u,
+                 lbm_result* res);
+
+/* Minimise every instance of the batch from its current m (Sec. 2.2-2.3).
+ * res: [batch].  Returns LBM_OK when the call ran; per-instance outcomes are
+ * in res[b].status. */
+int lbm_minimise(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, lbm_result* res);
+
+/* Hysteresis branch (Sec. 1.1, 3.1): for k = 0..n_pts-1 set the applied field
+ * of every instance to fields[k]*dir (tesla) and minimise, warm-started from
+ * the previous point.  m_par[k*batch+b] = volume-weighted mean of m.dir,
+ * energy[k*batch+b] = total energy (J); res (nullable): [n_pts*batch]. */
+int lbm_hysteresis(lbm_ctx* ctx, lbm_inst inst, const double dir[3], const double* fields,
+                   int32_t n_pts, const lbm_solve_opts* opt, double* m_par, double* energy,
+                   lbm_result* res);
+
+/* Same as lbm_set_m with a DEVICE pointer d_m (batch*N*3 doubles on the
+ * context's device, same layout); no host copy.  The read is stream-ordered on
+ * the context's stream. */
+int lbm_set_m_device(lbm_ctx* ctx, lbm_inst inst, const double* d_m);
+
+/* Number of kernels this context has launched so far. */
+int lbm_launch_count(lbm_ctx* ctx, int64_t* count);
+
+/* Per-kind device time of the minimiser's kernels, measured with CUDA events
+ * recorded on the context's stream around every launch while enabled.
+ * Kinds: 0 trial update (Eq. 8), 1 Neumann potential solve, 2 BEM product,
+ * 3 Dirichlet potential solve, 4 field/energy/dot products, 5 step decision. */
+#define LBM_PROF_KINDS 8
+typedef struct {
+    int64_t launches[LBM_PROF_KINDS];
+    double  ms[LBM_PROF_KINDS];
+    int64_t cg_iters[2];       /* potential-solve iterations summed over instances */
+} lbm_profile_stats;
+int lbm_profile_enable(lbm_ctx* ctx, int32_t on);
+int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

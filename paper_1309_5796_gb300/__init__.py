@@ -1,0 +1,277 @@
+"""Python binding of liblbm, the GB300 curvilinear steepest-descent micromagnetic
+minimiser (Exl et al., "LaBonte's method revisited", arXiv:1309.5796).
+
+Thin ctypes marshalling over the C ABI of include/lbm.h: every call here maps
+one-to-one onto an `lbm_*` entry point, and all computation happens in the
+library's CUDA kernels.  There is no CPU fallback: importing `lib()` fails
+loudly when liblbm.so has not been built (run `python -m
+paper_1309_5796_gb300.build`).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
+
+LBM_OK, LBM_E_INVALID, LBM_E_OOM, LBM_E_NOT_CONVERGED = 0, 1, 2, 3
+LBM_E_NAN, LBM_E_TIMEOUT, LBM_E_LINESEARCH, LBM_E_CUDA = 4, 5, 6, 7
+LBM_FP64, LBM_MIXED, LBM_MIXED_TC = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NOT_CONVERGED", 4: "NAN", 5: "TIMEOUT",
+                6: "LINESEARCH", 7: "CUDA"}
+
+
+class Material(C.Structure):
+    _fields_ = [("Js", C.c_double), ("A", C.c_double), ("K1", C.c_double), ("axis", C.c_double * 3)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("grad_tol", C.c_double), ("max_iter", C.c_int32),
+                ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("c1", C.c_double),
+                ("max_backtracks", C.c_int32), ("memory", C.c_int32), ("kappa0", C.c_double),
+                ("m_alpha", C.c_int32), ("tau_min", C.c_double), ("tau_max", C.c_double),
+                ("demag", C.c_int32), ("check_every", C.c_int32)]
+
+
+class ProfileStats(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("cg_iters", C.c_int64 * 2)]
+
+
+PROFILE_KINDS = ("trial_update", "pcg_neumann", "bem_product", "pcg_dirichlet", "field", "decide")
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("evaluations", C.c_int32),
+                ("line_searches", C.c_int32), ("cg_iters1", C.c_int64), ("cg_iters2", C.c_int64),
+                ("energy", C.c_double * 5), ("torque", C.c_double), ("gg", C.c_double),
+                ("mean_m", C.c_double * 3), ("wall_ms", C.c_double)]
+
+    def as_dict(self):
+        return dict(status=self.status, iterations=self.iterations, evaluations=self.evaluations,
+                    line_searches=self.line_searches, cg_iters1=self.cg_iters1,
+                    cg_iters2=self.cg_iters2, energy=list(self.energy), torque=self.torque,
+                    gg=self.gg, mean_m=list(self.mean_m), wall_ms=self.wall_ms)
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int32)
+
+# (name, restype, argtypes) of every exported symbol of include/lbm.h
+SIGNATURES = [
+    ("lbm_default_opts", None, [C.POINTER(SolveOpts), C.c_int32]),
+    ("lbm_create", C.c_int, [C.POINTER(_P), C.c_int32, _P]),
+    ("lbm_destroy", C.c_int, [_P]),
+    ("lbm_last_error", C.c_char_p, []),
+    ("lbm_mesh_cube", C.c_int, [_P, C.c_double, C.c_int32, C.POINTER(_I64)]),
+    ("lbm_mesh_destroy", C.c_int, [_P, _I64]),
+    ("lbm_mesh_info", C.c_int, [_P, _I64, C.POINTER(_I64)]),
+    ("lbm_mesh_export", C.c_int, [_P, _I64] + [_IP] * 9),
+    ("lbm_bem_rows", C.c_int, [_P, _I64, _I64, _I64, _DP]),
+    ("lbm_instance_create", C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(_I64)]),
+    ("lbm_instance_destroy", C.c_int, [_P, _I64]),
+    ("lbm_set_material", C.c_int, [_P, _I64, C.POINTER(Material)]),
+    ("lbm_set_field", C.c_int, [_P, _I64, _DP]),
+    ("lbm_set_m", C.c_int, [_P, _I64, _DP]),
+    ("lbm_get_m", C.c_int, [_P, _I64, _DP]),
+    ("lbm_evaluate", C.c_int, [_P, _I64, C.POINTER(SolveOpts), _DP, _DP, C.POINTER(Result)]),
+    ("lbm_minimise", C.c_int, [_P, _I64, C.POINTER(SolveOpts), C.POINTER(Result)]),
+    ("lbm_hysteresis", C.c_int, [_P, _I64, _DP, _DP, C.c_int32, C.POINTER(SolveOpts), _DP, _DP,
+                                 C.POINTER(Result)]),
+    ("lbm_launch_count", C.c_int, [_P, C.POINTER(_I64)]),
+    ("lbm_set_m_device", C.c_int, [_P, _I64, C.c_void_p]),
+    ("lbm_profile_enable", C.c_int, [_P, C.c_int32]),
+    ("lbm_profile_read", C.c_int, [_P, C.POINTER(ProfileStats), C.c_int32]),
+]
+
+_lib = None
+
+
+def lib():
+    """The loaded liblbm.so with typed signatures (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblbm.so not found at {LIB_PATH}; build it with "
+                               "`python -m paper_1309_5796_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != LBM_OK:
+        raise LBMError(rc, lib().lbm_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP) if a is not None else None
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_IP) if a is not None else None
+
+
+def default_opts(precision=LBM_FP64, **kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().lbm_default_opts(C.byref(o), precision)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """A liblbm context on one CUDA device (lbm_create / lbm_destroy)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._h = _P()
+        _check(lib().lbm_create(C.byref(self._h), device, stream))
+
+    def close(self):
+        if self._h:
+            lib().lbm_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- meshes --------------------------------------------------------------
+    def mesh_cube(self, cell_m: float, n: int) -> int:
+        h = _I64()
+        _check(lib().lbm_mesh_cube(self._h, cell_m, n, C.byref(h)))
+        return h.value
+
+    def mesh_destroy(self, mesh: int):
+        _check(lib().lbm_mesh_destroy(self._h, mesh))
+
+    def mesh_info(self, mesh: int) -> dict:
+        info = (_I64 * 8)()
+        _check(lib().lbm_mesh_info(self._h, mesh, info))
+        keys = ("N", "nb", "nnz", "tets", "tris", "bytes", "n")
+        return {k: int(info[i]) for i, k in enumerate(keys)}
+
+    def mesh_export(self, mesh: int) -> dict:
+        i = self.mesh_info(mesh)
+        N, nb, nnz, T, F = i["N"], i["nb"], i["nnz"], i["tets"], i["tris"]
+        out = dict(tets=np.empty((T, 4), np.int32), rowptr=np.empty(N + 1, np.int32),
+                   col=np.empty(nnz, np.int32), kval=np.empty(nnz, np.int32),
+                   gval=np.empty((nnz, 3), np.int32), gtval=np.empty((nnz, 3), np.int32),
+                   vol=np.empty(N, np.int32), bnd=np.empty(nb, np.int32),
+                   tris=np.empty((F, 3), np.int32))
+        _check(lib().lbm_mesh_export(self._h, mesh, *[_iptr(out[k]) for k in
+                                                      ("tets", "rowptr", "col", "kval", "gval",
+                                                       "gtval", "vol", "bnd", "tris")]))
+        return out
+
+    def bem_rows(self, mesh: int, row0: int, nrows: int) -> np.ndarray:
+        nb = self.mesh_info(mesh)["nb"]
+        out = np.empty((nrows, nb))
+        _check(lib().lbm_bem_rows(self._h, mesh, row0, nrows, _dptr(out)))
+        return out
+
+    # -- instances -----------------------------------------------------------
+    def instance_create(self, mesh: int, batch: int = 1, precision: int = LBM_FP64) -> "Instance":
+        h = _I64()
+        _check(lib().lbm_instance_create(self._h, mesh, batch, precision, C.byref(h)))
+        return Instance(self, h.value, mesh, batch, precision)
+
+    def launch_count(self) -> int:
+        c = _I64()
+        _check(lib().lbm_launch_count(self._h, C.byref(c)))
+        return c.value
+
+    def profile_enable(self, on: bool = True):
+        _check(lib().lbm_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        s = ProfileStats()
+        _check(lib().lbm_profile_read(self._h, C.byref(s), 1 if reset else 0))
+        out = {k: dict(launches=int(s.launches[i]), ms=float(s.ms[i]))
+               for i, k in enumerate(PROFILE_KINDS)}
+        out["cg_iters"] = [int(s.cg_iters[0]), int(s.cg_iters[1])]
+        return out
+
+
+class Instance:
+    """A batch of problems on one mesh (lbm_instance_* calls)."""
+
+    def __init__(self, ctx: Context, handle: int, mesh: int, batch: int, precision: int):
+        self.ctx, self.h, self.mesh, self.B, self.precision = ctx, handle, mesh, batch, precision
+        self.N = ctx.mesh_info(mesh)["N"]
+
+    def destroy(self):
+        _check(lib().lbm_instance_destroy(self.ctx._h, self.h))
+
+    def set_material(self, Js, A, K1, axes):
+        axes = np.broadcast_to(np.asarray(axes, dtype=np.float64), (self.B, 3))
+        mats = (Material * self.B)()
+        for b in range(self.B):
+            mats[b].Js, mats[b].A, mats[b].K1 = Js, A, K1
+            for d in range(3):
+                mats[b].axis[d] = axes[b, d]
+        _check(lib().lbm_set_material(self.ctx._h, self.h, mats))
+
+    def set_field(self, h):
+        h = np.ascontiguousarray(np.broadcast_to(np.asarray(h, np.float64), (self.B, 3)))
+        _check(lib().lbm_set_field(self.ctx._h, self.h, _dptr(h)))
+
+    def set_m(self, m):
+        m = np.ascontiguousarray(np.broadcast_to(np.asarray(m, np.float64), (self.B, self.N, 3)))
+        _check(lib().lbm_set_m(self.ctx._h, self.h, _dptr(m)))
+
+    def set_m_device(self, ptr: int):
+        """m from a device buffer (batch*N*3 doubles), e.g. a torch tensor's data_ptr()."""
+        _check(lib().lbm_set_m_device(self.ctx._h, self.h, C.c_void_p(ptr)))
+
+    def get_m(self) -> np.ndarray:
+        out = np.empty((self.B, self.N, 3))
+        _check(lib().lbm_get_m(self.ctx._h, self.h, _dptr(out)))
+        return out
+
+    def evaluate(self, opts: SolveOpts | None = None, want_h=True, want_u=True):
+        res = (Result * self.B)()
+        h = np.empty((self.B, self.N, 3)) if want_h else None
+        u = np.empty((self.B, 2, self.N)) if want_u else None
+        _check(lib().lbm_evaluate(self.ctx._h, self.h, C.byref(opts) if opts else None,
+                                  _dptr(h), _dptr(u), res))
+        return [r.as_dict() for r in res], h, u
+
+    def minimise(self, opts: SolveOpts | None = None):
+        res = (Result * self.B)()
+        _check(lib().lbm_minimise(self.ctx._h, self.h, C.byref(opts) if opts else None, res))
+        return [r.as_dict() for r in res]
+
+    def hysteresis(self, direction, fields, opts: SolveOpts | None = None):
+        d = np.ascontiguousarray(np.asarray(direction, np.float64))
+        f = np.ascontiguousarray(np.asarray(fields, np.float64))
+        npts = f.size
+        mpar = np.empty((npts, self.B))
+        energy = np.empty((npts, self.B))
+        res = (Result * (npts * self.B))()
+        _check(lib().lbm_hysteresis(self.ctx._h, self.h, _dptr(d), _dptr(f), npts,
+                                    C.byref(opts) if opts else None, _dptr(mpar), _dptr(energy),
+                                    res))
+        return mpar, energy, [r.as_dict() for r in res]
