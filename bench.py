@@ -277,7 +277,7 @@ def run_ours(args, ws, rank, local):
     except Exception:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    kinds = {k: v for k, v in prof.items() if k != "cg_iters"}
+    kinds = {k: v for k, v in prof.items() if k not in ("cg_iters", "cg_sweeps")}
     total_kernel_ms = sum(v["ms"] for v in kinds.values())
     cpu = None
     if not args.no_cpu_baseline:

@@ -176,6 +176,8 @@ typedef struct {
     int64_t launches[LBM_PROF_KINDS];
     double  ms[LBM_PROF_KINDS];
     int64_t cg_iters[2];       /* potential-solve iterations summed over instances */
+    int64_t cg_sweeps[2];      /* potential-solve iterations of the whole batch (each
+                                  sweep advances every unconverged instance) */
 } lbm_profile_stats;
 int lbm_profile_enable(lbm_ctx* ctx, int32_t on);
 int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);

@@ -11,13 +11,22 @@ Discrete forms (SI units, P1 magnetisation m with |m_i| = 1 at the nodes):
   E_an = K1 sum_i V_i (1 - (m_i . a)^2)             (lumped; >= 0)
   E_z  = -(Js/mu0) sum_i V_i m_i . (mu0 H_ext)        (exact for P1: int phi_i = V_i)
   E_d  = -(Js/(2 mu0)) sum_i V_i m_i . (mu0 h_d,i)
-and the effective field as mu0*H in tesla, mu0 h_i = -(mu0/(Js V_i)) dE/dm_i:
+and the effective field as mu0*H in tesla, mu0 h_i = -(mu0/(Js V_i)) dE/dm_i
+(so that -(Js/mu0) V_i h_i is exactly the gradient of the discrete energy):
   mu0 h_ex,i = -(2 A mu0/(Js V_i)) (K m)_i
   mu0 h_an,i = (2 K1 mu0/Js) (m_i . a) a
-  mu0 h_d,i  = -(Js/V_i) sum_j G_ji u_j          (lumped projection of -grad u)
+  mu0 h_d,i  = -(Js/V_i) sum_j G_ji (u_j + uT_j)/2
 with the potential (U = Ms u, u in metres) from the hybrid FEM/BEM:
-  K u1 = G m  (Neumann; gauge: the V-weighted mean of u1 is removed),
-  u2|S = B u1|S,   K_II u2,I = -K_IS u2,S,   u = u1 + u2.
+  b = G m;  K u1 = b  (Neumann; gauge: the V-weighted mean of u1 is removed),
+  u2|S = B u1|S,   K_II u2,I = -K_IS u2,S,   u = u1 + u2 =: X b,
+and the adjoint potential uT = X^T b:
+  K_II w_I = b_I (w_S = 0),  t_S = b_S - K_SI w_I,  c_S = B^T t_S,
+  K uT = b + c (scattered to the surface; Neumann, defined up to a constant).
+Reading: Sec. 2.1-2.3 define the step from grad phi_t, the gradient of the
+discrete energy.  E_d is the quadratic form (Js^2/(2 mu0)) b^T X b / 2 (b = G m), so
+its gradient involves (X + X^T)/2; the collocation BEM makes X non-symmetric,
+and the plain forward field (X b alone) is then not the gradient of E_d --
+with it the energy-based line search of Sec. 2.3 fails near the minimum.
 The potential solves here are direct sparse LU factorisations (the exact
 solution of the linear systems), not the iterative solver of the GPU path.
 
@@ -49,6 +58,7 @@ class Evaluation:
     torque: float            # max_i |m_i x h_i| / Js
     u1: np.ndarray
     u2: np.ndarray
+    uT: np.ndarray
 
 
 class CubeProblem:
@@ -81,6 +91,7 @@ class CubeProblem:
             Kd_ = self.Kcsr
             self.K_II = Kd_[self.interior][:, self.interior].tocsc()
             self.K_IS = Kd_[self.interior][:, self.bnd].tocsr()
+            self.K_SI = Kd_[self.bnd][:, self.interior].tocsr()
             self.lu_dir = spla.splu(self.K_II) if self.interior.size else None
 
     # -- magnetostatics -----------------------------------------------------
@@ -88,16 +99,33 @@ class CubeProblem:
         """b_i = sum_j G_ij . m_j = int m . grad phi_i (m^2)."""
         return self.G[0] @ m[:, 0] + self.G[1] @ m[:, 1] + self.G[2] @ m[:, 2]
 
+    def _neumann(self, rhs: np.ndarray) -> np.ndarray:
+        """Solution of K u = rhs (rhs made consistent by removing its mean), node 0
+        pinned, then the V-weighted mean removed."""
+        rhs = rhs - rhs.mean()
+        u = np.zeros(rhs.shape[0])
+        u[1:] = self.lu_neu.solve(rhs[1:])
+        return u - np.dot(self.V, u) / self.V.sum()
+
     def potential(self, m: np.ndarray):
         b = self.rhs(m)
-        u1 = np.zeros(m.shape[0])
-        u1[1:] = self.lu_neu.solve(b[1:])
-        u1 -= np.dot(self.V, u1) / self.V.sum()
+        u1 = self._neumann(b)
         u2 = np.zeros_like(u1)
         u2[self.bnd] = self.B @ u1[self.bnd]
         if self.interior.size:
             u2[self.interior] = self.lu_dir.solve(-(self.K_IS @ u2[self.bnd]))
         return u1, u2
+
+    def adjoint_potential(self, m: np.ndarray) -> np.ndarray:
+        """uT = X^T b, the transposed FEM/BEM chain applied to b = G m."""
+        b = self.rhs(m)
+        t = b[self.bnd].copy()
+        if self.interior.size:
+            w = self.lu_dir.solve(b[self.interior])
+            t -= self.K_SI @ w
+        rhs = b.copy()
+        rhs[self.bnd] += self.B.T @ t
+        return self._neumann(rhs)
 
     # -- fields and energies -------------------------------------------------
     def evaluate(self, m: np.ndarray, h_ext) -> Evaluation:
@@ -111,10 +139,11 @@ class CubeProblem:
         h_z = np.broadcast_to(h_ext, m.shape)
         if self.demag:
             u1, u2 = self.potential(m)
-            u = u1 + u2
+            uT = self.adjoint_potential(m)
+            u = 0.5 * (u1 + u2 + uT)
             h_d = -Js * np.stack([self.Gt[d] @ u for d in range(3)], axis=1) / V[:, None]
         else:
-            u1 = u2 = np.zeros(m.shape[0])
+            u1 = u2 = uT = np.zeros(m.shape[0])
             h_d = np.zeros_like(m)
         e_ex = self.A * float(np.sum(m * Km))
         e_an = self.K1 * float(np.dot(V, 1.0 - ma * ma))
@@ -125,7 +154,7 @@ class CubeProblem:
         torque = float(np.max(np.linalg.norm(np.cross(m, h), axis=1))) / Js
         terms = dict(ex=e_ex, an=e_an, z=e_z, d=e_d)
         return Evaluation(E=e_ex + e_an + e_z + e_d, terms=terms, h=h, grad=grad,
-                          torque=torque, u1=u1, u2=u2)
+                          torque=torque, u1=u1, u2=u2, uT=uT)
 
     def energy_only(self, m: np.ndarray, h_ext) -> float:
         return self.evaluate(m, h_ext).E

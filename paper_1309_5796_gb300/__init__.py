@@ -37,7 +37,8 @@ class SolveOpts(C.Structure):
 
 
 class ProfileStats(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("cg_iters", C.c_int64 * 2)]
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("cg_iters", C.c_int64 * 2),
+                ("cg_sweeps", C.c_int64 * 2)]
 
 
 PROFILE_KINDS = ("trial_update", "pcg_neumann", "bem_product", "pcg_dirichlet", "field", "decide")
@@ -212,6 +213,7 @@ class Context:
         out = {k: dict(launches=int(s.launches[i]), ms=float(s.ms[i]))
                for i, k in enumerate(PROFILE_KINDS)}
         out["cg_iters"] = [int(s.cg_iters[0]), int(s.cg_iters[1])]
+        out["cg_sweeps"] = [int(s.cg_sweeps[0]), int(s.cg_sweeps[1])]
         return out
 
 

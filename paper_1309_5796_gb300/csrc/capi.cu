@@ -99,7 +99,8 @@ struct lbm_ctx {
     int64_t next_id = 1;
     std::map<int64_t, Mesh*> meshes;
     std::map<int64_t, Inst*> insts;
-    Launch launch() { return Launch{stream, num_sms, bar, err, &launches}; }
+    unsigned long long* sweeps = nullptr;   // device [2]
+    Launch launch() { return Launch{stream, num_sms, bar, err, &launches, sweeps}; }
 };
 
 namespace {
@@ -154,10 +155,12 @@ BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool w
     (void)ctx;
     BatchView<T> v;
     const size_t N = M.N, B = I.B, nb = M.nb;
-    T* p = (T*)I.vec;
+    double* d = (double*)I.vec;
     v.B = I.B;
-    v.m = p; p += 2 * N * 3 * B;
-    v.H = p; p += 2 * N * 3 * B;
+    v.m = d; d += 2 * N * 3 * B;
+    v.H = d; d += 2 * N * 3 * B;
+    v.hout = with_hout ? d : nullptr; d += N * 3 * B;
+    T* p = (T*)d;
     v.u1 = p; p += N * B;
     v.u2 = p; p += N * B;
     v.r = p; p += N * B;
@@ -166,21 +169,22 @@ BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool w
     v.q = p; p += N * B;
     v.ub1 = p; p += nb * B;
     v.ub2 = p; p += nb * B;
-    v.hout = with_hout ? p : nullptr; p += N * 3 * B;
     v.part = I.part;
     v.st = I.st;
     v.ic = I.ic;
     return v;
 }
 
-size_t vec_elems(const Mesh& M, int B) {
+// bytes of the per-instance vectors: FP64 state (m, H at base and trial, the
+// optional field output) and T-typed potential / CG / BEM vectors
+size_t vec_bytes(const Mesh& M, int B, int tsize) {
     const size_t N = M.N, nb = M.nb;
-    return (size_t)B * (2 * N * 3 * 2 + 6 * N + 2 * nb + 3 * N);
+    return (size_t)B * (8 * (2 * N * 3 * 2 + 3 * N) + tsize * (6 * N + 2 * nb));
 }
 
 size_t part_elems(const lbm_ctx* ctx, int B) {
     const size_t a = (size_t)4 * ctx->num_sms * B * NQ;   // field kernel partials
-    const size_t b = (size_t)2 * 2 * ctx->num_sms * B * 4;  // PCG (two regions)
+    const size_t b = pcg_part_elems(ctx->num_sms, B);          // PCG (two regions)
     return a > b ? a : b;
 }
 
@@ -423,6 +427,11 @@ int lbm_create(lbm_ctx** out, int32_t device, void* stream) {
     }
     cudaMemset(c->bar, 0, 64);
     cudaMemset(c->err, 0, 64);
+    if (cudaMalloc(&c->sweeps, 64) != cudaSuccess) {
+        delete c;
+        return fail(LBM_E_OOM, "context allocation failed");
+    }
+    cudaMemset(c->sweeps, 0, 64);
     *out = c;
     return LBM_OK;
 }
@@ -437,6 +446,7 @@ int lbm_destroy(lbm_ctx* ctx) {
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     cudaFree(ctx->bar);
     cudaFree(ctx->err);
+    cudaFree(ctx->sweeps);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LBM_OK;
@@ -615,7 +625,7 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
     I->B = batch;
     I->precision = precision;
     I->tsize = precision == LBM_FP64 ? 8 : 4;
-    const size_t ve = vec_elems(*M, batch), pe = part_elems(ctx, batch);
+    const size_t vb = vec_bytes(*M, batch, precision == LBM_FP64 ? 8 : 4), pe = part_elems(ctx, batch);
     const size_t N = M->N;
 #define CKI(call)                                                                                   \
     do {                                                                                            \
@@ -626,16 +636,16 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
                         cudaGetErrorString(e_));                                                    \
         }                                                                                           \
     } while (0)
-    CKI(cudaMalloc(&I->vec, ve * I->tsize));
+    CKI(cudaMalloc(&I->vec, vb));
     CKI(cudaMalloc(&I->part, pe * sizeof(double)));
     CKI(cudaMalloc(&I->st, sizeof(InstState) * batch));
     CKI(cudaMalloc(&I->ic, sizeof(InstConst) * batch));
     CKI(cudaMalloc(&I->staged, sizeof(double) * batch * N * 3));
     CKI(cudaMalloc(&I->staged_u, sizeof(double) * batch * N * 2));
-    CKI(cudaMemsetAsync(I->vec, 0, ve * I->tsize, ctx->stream));
+    CKI(cudaMemsetAsync(I->vec, 0, vb, ctx->stream));
     CKI(cudaMemsetAsync(I->st, 0, sizeof(InstState) * batch, ctx->stream));
 #undef CKI
-    I->bytes = ve * I->tsize + pe * 8 + (sizeof(InstState) + sizeof(InstConst)) * batch + 40 * batch * N;
+    I->bytes = vb + pe * 8 + (sizeof(InstState) + sizeof(InstConst)) * batch + 40 * batch * N;
     lbm_material nd = {1.61, 7.7e-12, 4.3e6, {0.0, 0.0, 1.0}};
     I->mats.assign(batch, nd);
     I->h.assign(3 * batch, 0.0);
@@ -722,7 +732,12 @@ int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset) {
     }
     out->cg_iters[0] = ctx->prof_cg[0];
     out->cg_iters[1] = ctx->prof_cg[1];
+    unsigned long long sw[2];
+    CK(cudaMemcpy(sw, ctx->sweeps, sizeof sw, cudaMemcpyDeviceToHost));
+    out->cg_sweeps[0] = (int64_t)sw[0];
+    out->cg_sweeps[1] = (int64_t)sw[1];
     if (reset) {
+        CK(cudaMemsetAsync(ctx->sweeps, 0, sizeof sw, ctx->stream));
         for (int k = 0; k < LBM_PROF_KINDS; ++k) {
             ctx->prof_launches[k] = 0;
             ctx->prof_ms[k] = 0;

@@ -42,8 +42,8 @@ struct MeshView {
 template <typename T>
 struct BatchView {
     int B;
-    T* m;        // [2][N][3][B]   m[cur] = base point, m[1-cur] = trial
-    T* H;        // [2][N][3][B]   H = -m x grad phi at the same points
+    double* m;   // [2][N][3][B]   m[cur] = base point, m[1-cur] = trial (FP64 in every mode)
+    double* H;   // [2][N][3][B]   H = -m x grad phi at the same points (FP64)
     T* u1;       // [N][B]
     T* u2;       // [N][B]
     T* r; T* z; T* p; T* q;    // [N][B] PCG work vectors
@@ -52,7 +52,7 @@ struct BatchView {
     double* part;              // partial sums, >= maxblocks * B * NQ
     InstState* st;             // [B]
     const InstConst* ic;       // [B]
-    T* hout;                   // optional [N][3][B] effective field (nullable)
+    double* hout;              // optional [N][3][B] effective field (nullable)
 };
 
 struct Launch {
@@ -61,6 +61,7 @@ struct Launch {
     unsigned* bar;     // grid-barrier counter (device)
     int* err;          // device error word
     int64_t* launches; // host counter of kernel launches
+    unsigned long long* sweeps;  // device counters [2]: batched PCG iterations (Neumann, Dirichlet)
 };
 
 template <typename T>
@@ -83,5 +84,6 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
                   double* staged_u);
 void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0);
 int field_blocks(const Launch& L, const MeshView& M, int B);
+size_t pcg_part_elems(int num_sms, int B);
 
 }  // namespace lbm

@@ -19,43 +19,108 @@
 
 namespace lbm {
 
-constexpr int PCG_THREADS = 512;
+constexpr int PCG_THREADS = 512;        // grid-wide (cooperative) variant
+constexpr int PCG_SINGLE_THREADS = 1024; // one-CTA variant for small batches
 constexpr int FIELD_THREADS = 256;
+constexpr int MAXR = 16;                 // row length served by the unrolled gather (Kuhn rows: 15)
+constexpr long long SINGLE_CTA_MAX_WORK = 24576;   // N * B up to which one CTA solves
 
-template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <typename T, bool CG> __device__ __forceinline__ T ld_vec(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
 
-// Deterministic per-instance tree reduction over the RB row lanes of a block.
-// red[q*bd + tid] holds lane values (0 on idle lanes); the result for instance
-// b ends in red[q*bd + b].  Bit q of maxmask selects max instead of sum.
-__device__ __forceinline__ void inst_tree(double* red, int nq, unsigned maxmask, int B, int RB) {
-    const int tid = threadIdx.x, bd = blockDim.x, rl = tid / B;
-    int p2 = 1;
-    while (p2 < RB) p2 <<= 1;
-    for (int st = p2 >> 1; st > 0; st >>= 1) {
-        __syncthreads();
-        if (tid < RB * B && rl < st && rl + st < RB) {
-            for (int q = 0; q < nq; ++q) {
-                const double a = red[q * bd + tid], c = red[q * bd + tid + st * B];
-                red[q * bd + tid] = ((maxmask >> q) & 1u) ? fmax(a, c) : a + c;
+// Deterministic per-instance block reduction of NQV values per thread.  Thread
+// tid holds row lane rl = tid / B of instance b = tid % B; the totals land in
+// out[q*B + b].  Bit q of maxmask selects max instead of sum.
+template <int NQV>
+__device__ __forceinline__ void block_reduce_inst(double (&v)[NQV], double* scratch, double* out, int B, int RB,
+                                                  unsigned maxmask) {
+    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    if (B <= 32 && (32 % B) == 0) {
+        // lanes of one instance differ by multiples of B within the warp
+        for (int off = 16; off >= B; off >>= 1)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) {
+                const double o = __shfl_xor_sync(0xffffffffu, v[q], off);
+                v[q] = ((maxmask >> q) & 1u) ? fmax(v[q], o) : v[q] + o;
             }
-        }
+        if (lane < B)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) scratch[q * bd + warp * B + lane] = v[q];
+        __syncthreads();
+        const int nw = bd >> 5;
+        if (tid < B)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) {
+                double acc = scratch[q * bd + tid];
+                for (int w = 1; w < nw; ++w) {
+                    const double o = scratch[q * bd + w * B + tid];
+                    acc = ((maxmask >> q) & 1u) ? fmax(acc, o) : acc + o;
+                }
+                out[q * B + tid] = acc;
+            }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NQV; ++q) scratch[q * bd + tid] = (tid < RB * B) ? v[q] : 0.0;
+        __syncthreads();
+        if (tid < B)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) {
+                double acc = scratch[q * bd + tid];
+                for (int r = 1; r < RB; ++r) {
+                    const double o = scratch[q * bd + r * B + tid];
+                    acc = ((maxmask >> q) & 1u) ? fmax(acc, o) : acc + o;
+                }
+                out[q * B + tid] = acc;
+            }
     }
     __syncthreads();
 }
 
-// Sum of partials [blk][B][stride] over blocks, in a fixed order, into red[q*bd + b].
-__device__ __forceinline__ void cross_reduce(const double* part, int nblk, int stride, int nq, int B, int RB,
-                                             double* red) {
-    const int tid = threadIdx.x, bd = blockDim.x, b = tid % B, rl = tid / B;
-    for (int q = 0; q < nq; ++q) {
-        double acc = 0.0;
-        if (tid < RB * B) {
-#pragma unroll 8
-            for (int blk = rl; blk < nblk; blk += RB) acc += __ldcg(&part[((size_t)blk * B + b) * stride + q]);
-        }
-        red[q * bd + tid] = acc;
+// Totals over blocks of partials part[blk][B][4] (quantities q0..q0+NQV-1), in a
+// fixed order, into out[q*B + b].
+template <int NQV>
+__device__ __forceinline__ void cross_reduce(const double* part, int q0, int nblk, int B, int RB, double* scratch,
+                                             double* out) {
+    const int tid = threadIdx.x, b = tid % B, rl = tid / B;
+    double v[NQV];
+#pragma unroll
+    for (int q = 0; q < NQV; ++q) v[q] = 0.0;
+    if (tid < RB * B) {
+#pragma unroll 4
+        for (int blk = rl; blk < nblk; blk += RB)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q) v[q] += __ldcg(&part[((size_t)blk * B + b) * 4 + q0 + q]);
     }
-    inst_tree(red, nq, 0u, B, RB);
+    block_reduce_inst<NQV>(v, scratch, out, B, RB, 0u);
+}
+
+// sum_j K_ij (v_j - v_i) (DIFF) or sum_j K_ij v_j over one CSR row; all column
+// indices, then all values, are loaded before any arithmetic so the gathers of
+// a row are in flight together.
+template <typename T, bool CG, bool DIFF>
+__device__ __forceinline__ T row_k(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
+                                   const T* v, int B, int b, T vi) {
+    int cj[MAXR], kj[MAXR];
+#pragma unroll
+    for (int t = 0; t < MAXR; ++t) {
+        const int e = e0 + t;
+        const bool ok = e < e1;
+        cj[t] = ok ? (__ldg(&col[e]) & 0x7fffffff) : -1;
+        kj[t] = ok ? sbyte(__ldg(&pkA[e]), 0) : 0;
+    }
+    T vj[MAXR];
+#pragma unroll
+    for (int t = 0; t < MAXR; ++t) vj[t] = cj[t] >= 0 ? ld_vec<T, CG>(&v[(size_t)cj[t] * B + b]) : vi;
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < MAXR; ++t) acc += T(kj[t]) * (DIFF ? (vj[t] - vi) : vj[t]);
+    for (int e = e0 + MAXR; e < e1; ++e) {
+        const T x = ld_vec<T, CG>(&v[(size_t)(col[e] & 0x7fffffff) * B + b]);
+        acc += T(sbyte(pkA[e], 0)) * (DIFF ? (x - vi) : x);
+    }
+    return acc;
 }
 
 template <typename T>
@@ -67,24 +132,40 @@ struct PcgArgs {
     int max_iter;
     unsigned* bar;
     int* err;
-    int* iters;        // [B] iterations of this solve
+    unsigned long long* sweeps;
 };
 
-// Jacobi-PCG on Kint, fused so that every iteration needs two grid barriers:
+template <bool SINGLE>
+__device__ __forceinline__ bool pcg_sync(unsigned* bar, unsigned& epoch, int* err) {
+    if constexpr (SINGLE) {
+        __syncthreads();
+        return true;
+    } else {
+        return grid_sync(bar, gridDim.x, epoch, err);
+    }
+}
+
+// Jacobi-PCG on Kint for B instances at once, fused so that every iteration
+// needs two synchronisations (grid barriers, or __syncthreads in the one-CTA
+// variant):
 //   A: w = K z, p = z + beta p, q = w + beta q (= K p), partial p.q
 //   B: alpha = rho/p.q, x += alpha p, r -= alpha q, z = r / K_ii, partials r.z, r.r
-// Neumann: rhs = (1/4) Gint m (trial point), gauge by the V-weighted mean, and
-// the surface values are gathered for the BEM product.  Dirichlet: the surface
-// values come from the BEM product; boundary rows are frozen (r = z = p = q = 0).
-template <typename T>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> A) {
+// Neumann: rhs = (1/4) Gint m at the trial point, made consistent (mean
+// removed); the residual is tested without its mean; the solution is gauged to
+// zero V-weighted mean and its surface values are gathered for the BEM.
+// Dirichlet: the surface values come from the BEM product; surface rows are
+// frozen (r = z = p = q = 0).
+template <typename T, bool SINGLE>
+__global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) k_pcg(PcgArgs<T> A) {
     extern __shared__ double sm[];
+    constexpr bool CG = !SINGLE;
     const int bd = blockDim.x, tid = threadIdx.x;
     const int B = A.V.B, RB = bd / B;
     const bool lane = tid < RB * B;
     const int b = tid % B, rl = tid / B;
-    double* red = sm;                    // [4][bd]
-    double* s_rho = red + 4 * bd;        // [B]
+    double* scratch = sm;                // [4][bd]
+    double* out = scratch + 4 * bd;      // [4][B]
+    double* s_rho = out + 4 * B;         // [B]
     double* s_rhop = s_rho + B;
     double* s_ab = s_rhop + B;
     double* s_tol = s_ab + B;
@@ -117,7 +198,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> A) {
     double* part_rz = A.V.part;
     double* part_pq = A.V.part + (size_t)gridDim.x * B * 4;
     unsigned epoch = 0;
-    const T* meval = A.V.m + (size_t)(1 - s_cur[b]) * N * 3 * B;
+    const double* meval = A.V.m + (size_t)(1 - s_cur[b]) * N * 3 * B;
 
     if (dir) {
         if (act)
@@ -125,56 +206,87 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> A) {
                 const int bp = (int)((unsigned)node[row] >> 16);
                 if (bp) x[(size_t)row * B + b] = A.V.ub2[(size_t)(bp - 1) * B + b];
             }
-        if (!grid_sync(A.bar, gridDim.x, epoch, A.err)) return;
+        if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
     }
     {   // residual of the warm start
-        double prz = 0.0, prr = 0.0, pbb = 0.0;
+        // Neumann: the system is singular with null space span{1}; the right-hand
+        // side is made consistent (sum zero) by removing its mean before use.
+        double psum[1] = {0.0};
         if (act)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 const size_t ib = (size_t)row * B + b;
                 if (dir && ((unsigned)nd >> 16)) { r[ib] = T(0); z[ib] = T(0); p[ib] = T(0); q[ib] = T(0); continue; }
-                const T kii = T((nd >> 8) & 0xff);
+                const int e0 = rowptr[row], e1 = rowptr[row + 1];
                 const T xi = x[ib];
-                T kx = T(0), rhs = T(0);
-                for (int e = rowptr[row]; e < rowptr[row + 1]; ++e) {
-                    const int c = col[e];
-                    const int j = c & 0x7fffffff;
-                    const int w = pkA[e];
-                    const T xj = ldcg(&x[(size_t)j * B + b]);
-                    kx += T(sbyte(w, 0)) * (xj - xi);
-                    if (!dir) {
-                        const size_t mj = (size_t)j * 3 * B + b;
-                        rhs += T(sbyte(w, 1)) * meval[mj] + T(sbyte(w, 2)) * meval[mj + B] +
-                               T(sbyte(w, 3)) * meval[mj + 2 * B];
-                    } else if (c < 0) {
-                        rhs -= T(sbyte(w, 0)) * xj;    // -K_IS u_S
+                const T kx = row_k<T, CG, true>(col, pkA, e0, e1, x, B, b, xi);
+                T rhs = T(0);
+                if (!dir) {
+                    double acc = 0.0;
+                    for (int e = e0; e < e1; ++e) {
+                        const int w = pkA[e];
+                        const size_t mj = (size_t)(col[e] & 0x7fffffff) * 3 * B + b;
+                        acc += sbyte(w, 1) * meval[mj] + sbyte(w, 2) * meval[mj + B] + sbyte(w, 3) * meval[mj + 2 * B];
+                    }
+                    rhs = T(0.25 * acc);
+                } else {
+                    for (int e = e0; e < e1; ++e) {
+                        const int c = col[e];
+                        if (c < 0) rhs -= T(sbyte(pkA[e], 0)) * ld_vec<T, CG>(&x[(size_t)(c & 0x7fffffff) * B + b]);
                     }
                 }
-                if (!dir) rhs *= T(0.25);
-                const T ri = dir ? -kx : rhs - kx;
-                const T zi = ri / kii;
-                r[ib] = ri;
-                z[ib] = zi;
+                r[ib] = dir ? -kx : rhs - kx;
+                z[ib] = rhs;                          // kept for the second pass
                 p[ib] = T(0);
                 q[ib] = T(0);
-                prz += (double)ri * (double)zi;
-                prr += (double)ri * (double)ri;
-                pbb += (double)rhs * (double)rhs;
+                psum[0] += (double)rhs;
             }
-        red[0 * bd + tid] = prz;
-        red[1 * bd + tid] = prr;
-        red[2 * bd + tid] = pbb;
-        inst_tree(red, 3, 0u, B, RB);
-        if (tid < B)
-            for (int k = 0; k < 3; ++k) part_rz[((size_t)blockIdx.x * B + tid) * 4 + k] = red[k * bd + tid];
-        if (!grid_sync(A.bar, gridDim.x, epoch, A.err)) return;
+        double mean = 0.0;
+        if (!dir) {
+            block_reduce_inst<1>(psum, scratch, out, B, RB, 0u);
+            if (SINGLE) {
+                if (tid < B) s_ab[tid] = out[tid] / (double)N;
+            } else {
+                if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4 + 2] = out[tid];
+                if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+                cross_reduce<1>(part_pq, 2, gridDim.x, B, RB, scratch, out);
+                if (tid < B) s_ab[tid] = out[tid] / (double)N;
+            }
+            __syncthreads();
+            mean = s_ab[b];
+        }
+        double v4[4] = {0.0, 0.0, 0.0, 0.0};   // r.z, r.r, rhs.rhs, sum r
+        if (act)
+            for (int row = row0; row < N; row += rstride) {
+                const int nd = node[row];
+                if (dir && ((unsigned)nd >> 16)) continue;
+                const size_t ib = (size_t)row * B + b;
+                const T rhs = z[ib] - T(mean);
+                const T ri = r[ib] - T(mean);
+                const T zi = ri / T((nd >> 8) & 0xff);
+                r[ib] = ri;
+                z[ib] = zi;
+                v4[0] += (double)ri * (double)zi;
+                v4[1] += (double)ri * (double)ri;
+                v4[2] += (double)rhs * (double)rhs;
+                v4[3] += (double)ri;
+            }
+        block_reduce_inst<4>(v4, scratch, out, B, RB, 0u);
+        if (!SINGLE) {
+            if (tid < B)
+                for (int k = 0; k < 4; ++k) part_rz[((size_t)blockIdx.x * B + tid) * 4 + k] = out[k * B + tid];
+            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+        }
     }
     for (int k = 0;; ++k) {
-        cross_reduce(part_rz, gridDim.x, 4, k == 0 ? 3 : 2, B, RB, red);
+        if (!SINGLE) cross_reduce<4>(part_rz, 0, gridDim.x, B, RB, scratch, out);
         if (tid < B) {
-            const double rho = red[tid], rr = red[bd + tid];
-            if (k == 0) s_tol[tid] = A.tol2 * red[2 * bd + tid];
+            const double rho = out[tid];
+            // Neumann: test the residual without its null-space (mean) component,
+            // which rounding feeds and CG cannot remove
+            const double sr = out[3 * B + tid];
+            const double rr = dir ? out[B + tid] : fmax(out[B + tid] - sr * sr / (double)N, 0.0);
+            if (k == 0) s_tol[tid] = A.tol2 * out[2 * B + tid];
             const int conv = !s_act[tid] || rr <= s_tol[tid] || k >= A.max_iter;
             s_ab[tid] = (k == 0 || conv) ? 0.0 : rho / s_rhop[tid];
             s_rho[tid] = rho;
@@ -189,33 +301,30 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> A) {
         __syncthreads();
         if (s_all) break;
         const bool run = act && !s_flag[b];
-        double ppq = 0.0;
+        double ppq[1] = {0.0};
         if (run) {
             const T beta = T(s_ab[b]);
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 if (dir && ((unsigned)nd >> 16)) continue;
                 const size_t ib = (size_t)row * B + b;
-                T w = T(0);
-                for (int e = rowptr[row]; e < rowptr[row + 1]; ++e) {
-                    const int j = col[e] & 0x7fffffff;
-                    w += T(sbyte(pkA[e], 0)) * ldcg(&z[(size_t)j * B + b]);
-                }
+                const T w = row_k<T, CG, false>(col, pkA, rowptr[row], rowptr[row + 1], z, B, b, T(0));
                 const T pi = z[ib] + beta * p[ib];
                 const T qi = w + beta * q[ib];
                 p[ib] = pi;
                 q[ib] = qi;
-                ppq += (double)pi * (double)qi;
+                ppq[0] += (double)pi * (double)qi;
             }
         }
-        red[tid] = ppq;
-        inst_tree(red, 1, 0u, B, RB);
-        if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4] = red[tid];
-        if (!grid_sync(A.bar, gridDim.x, epoch, A.err)) return;
-        cross_reduce(part_pq, gridDim.x, 4, 1, B, RB, red);
-        if (tid < B) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / red[tid];
+        block_reduce_inst<1>(ppq, scratch, out, B, RB, 0u);
+        if (!SINGLE) {
+            if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4] = out[tid];
+            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+            cross_reduce<1>(part_pq, 0, gridDim.x, B, RB, scratch, out);
+        }
+        if (tid < B) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
         __syncthreads();
-        double prz = 0.0, prr = 0.0;
+        double v4[4] = {0.0, 0.0, 0.0, 0.0};
         if (run) {
             const T alpha = T(s_ab[b]);
             for (int row = row0; row < N; row += rstride) {
@@ -228,39 +337,50 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> A) {
                 x[ib] = xi;
                 r[ib] = ri;
                 z[ib] = zi;
-                prz += (double)ri * (double)zi;
-                prr += (double)ri * (double)ri;
+                v4[0] += (double)ri * (double)zi;
+                v4[1] += (double)ri * (double)ri;
+                v4[3] += (double)ri;
             }
         }
-        red[0 * bd + tid] = prz;
-        red[1 * bd + tid] = prr;
-        inst_tree(red, 2, 0u, B, RB);
-        if (tid < B)
-            for (int kk = 0; kk < 2; ++kk) part_rz[((size_t)blockIdx.x * B + tid) * 4 + kk] = red[kk * bd + tid];
-        if (!grid_sync(A.bar, gridDim.x, epoch, A.err)) return;
+        block_reduce_inst<4>(v4, scratch, out, B, RB, 0u);
+        if (!SINGLE) {
+            if (tid < B)
+                for (int kk = 0; kk < 4; ++kk)
+                    if (kk != 2) part_rz[((size_t)blockIdx.x * B + tid) * 4 + kk] = out[kk * B + tid];
+            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+        } else {
+            __syncthreads();
+        }
         if (tid < B) {
             s_rhop[tid] = s_rho[tid];
             if (!s_flag[tid]) s_it[tid] += 1;
         }
     }
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int i = tid; i < B; i += bd) {
             if (dir) A.V.st[i].cg2 += s_it[i];
             else A.V.st[i].cg1 += s_it[i];
         }
+        if (tid == 0 && A.sweeps) {
+            int kmax = 0;
+            for (int i = 0; i < B; ++i) kmax = max(kmax, s_it[i]);
+            A.sweeps[dir ? 1 : 0] += (unsigned long long)kmax;
+        }
+    }
     if (dir) return;
     // gauge: remove the V-weighted mean; gather the surface values
     {
-        double pv = 0.0;
+        double pv[1] = {0.0};
         if (act)
             for (int row = row0; row < N; row += rstride)
-                pv += (double)(node[row] & 0xff) * (double)x[(size_t)row * B + b];
-        red[tid] = pv;
-        inst_tree(red, 1, 0u, B, RB);
-        if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4 + 1] = red[tid];
-        if (!grid_sync(A.bar, gridDim.x, epoch, A.err)) return;
-        cross_reduce(part_pq + 1, gridDim.x, 4, 1, B, RB, red);
-        if (tid < B) s_ab[tid] = red[tid] / A.M.vsum;
+                pv[0] += (double)(node[row] & 0xff) * (double)x[(size_t)row * B + b];
+        block_reduce_inst<1>(pv, scratch, out, B, RB, 0u);
+        if (!SINGLE) {
+            if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4 + 1] = out[tid];
+            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+            cross_reduce<1>(part_pq, 1, gridDim.x, B, RB, scratch, out);
+        }
+        if (tid < B) s_ab[tid] = out[tid] / A.M.vsum;
         __syncthreads();
         if (act) {
             const T mean = T(s_ab[b]);
@@ -275,28 +395,41 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs<T> A) {
     }
 }
 
+size_t pcg_part_elems(int num_sms, int B) { return (size_t)2 * num_sms * B * 4; }
+
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
               int* iters_dev) {
+    (void)iters_dev;
     const int B = V.B;
-    const int RB = PCG_THREADS / B;
-    const size_t smem = sizeof(double) * (4 * PCG_THREADS + 4 * B) + sizeof(int) * 4 * B;
-    static int occ_cache[2] = {0, 0};
-    int& occ = occ_cache[sizeof(T) == 8];
-    if (!occ) {
-        cudaFuncSetAttribute(k_pcg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem + 4096);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T>, PCG_THREADS, smem + 4096);
-        if (occ < 1) occ = 1;
-        if (occ > 2) occ = 2;
-    }
-    int nblk = (M.N + RB - 1) / RB;
-    const int maxblk = occ * L.num_sms;
-    if (nblk > maxblk) nblk = maxblk;
-    PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, iters_dev};
-    cudaMemsetAsync(L.bar, 0, sizeof(unsigned), L.stream);
+    PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps};
     void* args[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_pcg<T>, dim3(nblk), dim3(PCG_THREADS), args, smem,
-                                                L.stream);
+    cudaError_t e;
+    if ((long long)M.N * B <= SINGLE_CTA_MAX_WORK) {
+        const size_t smem = sizeof(double) * (4 * PCG_SINGLE_THREADS + 8 * B) + sizeof(int) * 4 * B;
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[sizeof(T) == 8]) {
+            cudaFuncSetAttribute(k_pcg<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+            attr_set[sizeof(T) == 8] = true;
+        }
+        e = cudaLaunchKernel((void*)k_pcg<T, true>, dim3(1), dim3(PCG_SINGLE_THREADS), args, smem, L.stream);
+    } else {
+        const int RB = PCG_THREADS / B;
+        const size_t smem = sizeof(double) * (4 * PCG_THREADS + 8 * B) + sizeof(int) * 4 * B;
+        static int occ_cache[2] = {0, 0};
+        int& occ = occ_cache[sizeof(T) == 8];
+        if (!occ) {
+            cudaFuncSetAttribute(k_pcg<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, false>, PCG_THREADS, 64 * 1024);
+            if (occ < 1) occ = 1;
+            if (occ > 1) occ = 1;
+        }
+        int nblk = (M.N + RB - 1) / RB;
+        const int maxblk = occ * L.num_sms;
+        if (nblk > maxblk) nblk = maxblk;
+        cudaMemsetAsync(L.bar, 0, sizeof(unsigned), L.stream);
+        e = cudaLaunchCooperativeKernel((void*)k_pcg<T, false>, dim3(nblk), dim3(PCG_THREADS), args, smem, L.stream);
+    }
     *L.launches += 1;
     return e == cudaSuccess ? 0 : (int)e;
 }
@@ -385,68 +518,69 @@ int field_blocks(const Launch& L, const MeshView& M, int B) {
 
 template <typename T>
 __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T> V, int demag) {
-    __shared__ double red[Q_COUNT * FIELD_THREADS];
-    const int bd = blockDim.x, tid = threadIdx.x;
-    const int B = V.B, RB = bd / B;
+    extern __shared__ double fsm[];
+    double* scratch = fsm;                        // [Q_COUNT][bd]
+    double* out = fsm + Q_COUNT * FIELD_THREADS;  // [Q_COUNT][B]
+    const int tid = threadIdx.x;
+    const int B = V.B, RB = FIELD_THREADS / B;
     const bool lane = tid < RB * B;
     const int b = tid % B, rl = tid / B;
     const int N = M.N;
     double acc[Q_COUNT];
+#pragma unroll
     for (int k = 0; k < Q_COUNT; ++k) acc[k] = 0.0;
     const int phase = lane ? V.st[b].phase : PH_DONE;
     if (lane && phase != PH_DONE) {
         const int cur = V.st[b].cur;
         const InstConst ic = V.ic[b];
-        const T* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
-        const T* mb = V.m + (size_t)cur * N * 3 * B;
-        T* Ht = V.H + (size_t)(1 - cur) * N * 3 * B;
-        const T* Hb = V.H + (size_t)cur * N * 3 * B;
+        const double* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
+        const double* mb = V.m + (size_t)cur * N * 3 * B;
+        double* Ht = V.H + (size_t)(1 - cur) * N * 3 * B;
+        const double* Hb = V.H + (size_t)cur * N * 3 * B;
         for (int row = blockIdx.x * RB + rl; row < N; row += gridDim.x * RB) {
             const int nd = M.node[row];
             const double vi = (double)(nd & 0xff);
             const size_t i3 = (size_t)row * 3 * B + b;
-            const T mx = mt[i3], my = mt[i3 + B], mz = mt[i3 + 2 * B];
+            const double mx = mt[i3], my = mt[i3 + B], mz = mt[i3 + 2 * B];
             T ex0 = T(0), ex1 = T(0), ex2 = T(0), hd0 = T(0), hd1 = T(0), hd2 = T(0);
-            for (int e = M.rowptr[row]; e < M.rowptr[row + 1]; ++e) {
-                const int j = M.col[e] & 0x7fffffff;
-                const int wa = M.pkA[e];
-                const T k = T(sbyte(wa, 0));
+            const int e0 = M.rowptr[row], e1 = M.rowptr[row + 1];
+            for (int e = e0; e < e1; ++e) {
+                const int j = __ldg(&M.col[e]) & 0x7fffffff;
+                const T k = T(sbyte(__ldg(&M.pkA[e]), 0));
                 const size_t j3 = (size_t)j * 3 * B + b;
-                ex0 += k * (mt[j3] - mx);
-                ex1 += k * (mt[j3 + B] - my);
-                ex2 += k * (mt[j3 + 2 * B] - mz);
+                // difference form: exact zero for a uniform state, no cancellation
+                ex0 += k * T(mt[j3] - mx);
+                ex1 += k * T(mt[j3 + B] - my);
+                ex2 += k * T(mt[j3 + 2 * B] - mz);
                 if (demag) {
-                    const int wb = M.pkB[e];
+                    const int wb = __ldg(&M.pkB[e]);
                     const T u = V.u1[(size_t)j * B + b] + V.u2[(size_t)j * B + b];
                     hd0 += T(sbyte(wb, 0)) * u;
                     hd1 += T(sbyte(wb, 1)) * u;
                     hd2 += T(sbyte(wb, 2)) * u;
                 }
             }
-            const double m[3] = {(double)mx, (double)my, (double)mz};
+            const double m[3] = {mx, my, mz};
             const double kx[3] = {(double)ex0, (double)ex1, (double)ex2};
             const double ma = m[0] * ic.a[0] + m[1] * ic.a[1] + m[2] * ic.a[2];
-            double h[3], hd[3];
-            for (int c = 0; c < 3; ++c) {
-                const double hex = -4.0 * ic.lam * kx[c] / vi;
-                hd[c] = -(double)(c == 0 ? hd0 : (c == 1 ? hd1 : hd2)) / vi;
-                h[c] = hex + ic.Q * ma * ic.a[c] + ic.hz[c] + hd[c];
-            }
+            const double hd[3] = {-(double)hd0 / vi, -(double)hd1 / vi, -(double)hd2 / vi};
+            double h[3];
+            for (int c = 0; c < 3; ++c) h[c] = -4.0 * ic.lam * kx[c] / vi + ic.Q * ma * ic.a[c] + ic.hz[c] + hd[c];
             // H = -m x grad phi = (V/12) m x h ;  g = m x H
             const double mh[3] = {m[1] * h[2] - m[2] * h[1], m[2] * h[0] - m[0] * h[2], m[0] * h[1] - m[1] * h[0]};
             const double Hv[3] = {vi / 12.0 * mh[0], vi / 12.0 * mh[1], vi / 12.0 * mh[2]};
-            Ht[i3] = T(Hv[0]);
-            Ht[i3 + B] = T(Hv[1]);
-            Ht[i3 + 2 * B] = T(Hv[2]);
+            Ht[i3] = Hv[0];
+            Ht[i3 + B] = Hv[1];
+            Ht[i3 + 2 * B] = Hv[2];
             if (V.hout) {
-                V.hout[i3] = T(h[0]);
-                V.hout[i3 + B] = T(h[1]);
-                V.hout[i3 + 2 * B] = T(h[2]);
+                V.hout[i3] = h[0];
+                V.hout[i3 + B] = h[1];
+                V.hout[i3 + 2 * B] = h[2];
             }
             const double g[3] = {m[1] * Hv[2] - m[2] * Hv[1], m[2] * Hv[0] - m[0] * Hv[2],
                                  m[0] * Hv[1] - m[1] * Hv[0]};
-            const double bm[3] = {(double)mb[i3], (double)mb[i3 + B], (double)mb[i3 + 2 * B]};
-            const double bH[3] = {(double)Hb[i3], (double)Hb[i3 + B], (double)Hb[i3 + 2 * B]};
+            const double bm[3] = {mb[i3], mb[i3 + B], mb[i3 + 2 * B]};
+            const double bH[3] = {Hb[i3], Hb[i3 + B], Hb[i3 + 2 * B]};
             const double gb[3] = {bm[1] * bH[2] - bm[2] * bH[1], bm[2] * bH[0] - bm[0] * bH[2],
                                   bm[0] * bH[1] - bm[1] * bH[0]};
             const double mxa[3] = {m[1] * ic.a[2] - m[2] * ic.a[1], m[2] * ic.a[0] - m[0] * ic.a[2],
@@ -459,10 +593,10 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
             acc[Q_HMAX] = fmax(acc[Q_HMAX], sqrt(Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2]));
             double ss = 0.0, sy = 0.0, yy = 0.0, gg = 0.0;
             for (int c = 0; c < 3; ++c) {
-                const double s = m[c] - bm[c], y = g[c] - gb[c];
-                ss += s * s;
-                sy += s * y;
-                yy += y * y;
+                const double sc = m[c] - bm[c], yc = g[c] - gb[c];
+                ss += sc * sc;
+                sy += sc * yc;
+                yy += yc * yc;
                 gg += g[c] * g[c];
             }
             acc[Q_GG] += gg;
@@ -475,17 +609,22 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
             if (!(isfinite(h[0]) && isfinite(h[1]) && isfinite(h[2]))) acc[Q_BAD] = 1.0;
         }
     }
-    for (int k = 0; k < Q_COUNT; ++k) red[k * bd + tid] = acc[k];
     const unsigned maxmask = (1u << Q_TORQUE) | (1u << Q_HMAX) | (1u << Q_BAD);
-    inst_tree(red, Q_COUNT, maxmask, B, RB);
+    block_reduce_inst<Q_COUNT>(acc, scratch, out, B, RB, maxmask);
     if (tid < B)
-        for (int k = 0; k < Q_COUNT; ++k) V.part[((size_t)blockIdx.x * B + tid) * NQ + k] = red[k * bd + tid];
+        for (int k = 0; k < Q_COUNT; ++k) V.part[((size_t)blockIdx.x * B + tid) * NQ + k] = out[k * B + tid];
 }
 
 template <typename T>
 void field_eval(const Launch& L, const MeshView& M, const BatchView<T>& V, int demag) {
     const int nblk = field_blocks(L, M, V.B);
-    k_field<T><<<nblk, FIELD_THREADS, 0, L.stream>>>(M, V, demag);
+    const size_t smem = sizeof(double) * Q_COUNT * (FIELD_THREADS + V.B);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        attr_set = true;
+    }
+    k_field<T><<<nblk, FIELD_THREADS, smem, L.stream>>>(M, V, demag);
     *L.launches += 1;
 }
 
@@ -636,34 +775,26 @@ __global__ void k_trial(int N, BatchView<T> V) {
         if (phase == PH_DONE) continue;
         const int cur = V.st[b].cur;
         const size_t i3 = row * 3 * B + b;
-        const T* mb = V.m + (size_t)cur * N * 3 * B;
-        T* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
+        const double* mb = V.m + (size_t)cur * N * 3 * B;
+        double* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
         if (phase == PH_INIT) {
             mt[i3] = mb[i3];
             mt[i3 + B] = mb[i3 + B];
             mt[i3 + 2 * B] = mb[i3 + 2 * B];
             continue;
         }
-        const T* Hb = V.H + (size_t)cur * N * 3 * B;
-        const T ht = T(0.5 * V.st[b].tau);
-        const T m0 = mb[i3], m1 = mb[i3 + B], m2 = mb[i3 + 2 * B];
-        const T w0 = ht * Hb[i3], w1 = ht * Hb[i3 + B], w2 = ht * Hb[i3 + 2 * B];
-        const T ww = w0 * w0 + w1 * w1 + w2 * w2;
-        const T mw = m0 * w0 + m1 * w1 + m2 * w2;
-        const T inv = T(1) / (T(1) + ww);
-        const T c0 = m1 * w2 - m2 * w1, c1 = m2 * w0 - m0 * w2, c2 = m0 * w1 - m1 * w0;
-        T x0 = ((T(1) - ww) * m0 - T(2) * c0 + T(2) * mw * w0) * inv;
-        T x1 = ((T(1) - ww) * m1 - T(2) * c1 + T(2) * mw * w1) * inv;
-        T x2 = ((T(1) - ww) * m2 - T(2) * c2 + T(2) * mw * w2) * inv;
-        if (sizeof(T) == 4) {   // FP32 storage: undo the rounding drift of |m|
-            const T s = rsqrtf((float)(x0 * x0 + x1 * x1 + x2 * x2));
-            x0 *= s;
-            x1 *= s;
-            x2 *= s;
-        }
-        mt[i3] = x0;
-        mt[i3 + B] = x1;
-        mt[i3 + 2 * B] = x2;
+        // x = [(1 - |w|^2) m - 2 m x w + 2 (m.w) w] / (1 + |w|^2),  w = tau H / 2
+        const double* Hb = V.H + (size_t)cur * N * 3 * B;
+        const double ht = 0.5 * V.st[b].tau;
+        const double m0 = mb[i3], m1 = mb[i3 + B], m2 = mb[i3 + 2 * B];
+        const double w0 = ht * Hb[i3], w1 = ht * Hb[i3 + B], w2 = ht * Hb[i3 + 2 * B];
+        const double ww = w0 * w0 + w1 * w1 + w2 * w2;
+        const double mw = m0 * w0 + m1 * w1 + m2 * w2;
+        const double c0 = m1 * w2 - m2 * w1, c1 = m2 * w0 - m0 * w2, c2 = m0 * w1 - m1 * w0;
+        const double den = 1.0 + ww;
+        mt[i3] = ((1.0 - ww) * m0 - 2.0 * c0 + 2.0 * mw * w0) / den;
+        mt[i3 + B] = ((1.0 - ww) * m1 - 2.0 * c1 + 2.0 * mw * w1) / den;
+        mt[i3 + 2 * B] = ((1.0 - ww) * m2 - 2.0 * c2 + 2.0 * mw * w2) / den;
     }
 }
 
@@ -704,7 +835,7 @@ __global__ void k_pack_m(int N, BatchView<T> V, const double* __restrict__ in) {
         const size_t ic = t / B;   // i*3 + c
         const size_t i = ic / 3, c = ic % 3;
         const int cur = V.st[b].cur;
-        V.m[(size_t)cur * N * 3 * B + t] = T(in[((size_t)b * N + i) * 3 + c]);
+        V.m[(size_t)cur * N * 3 * B + t] = in[((size_t)b * N + i) * 3 + c];
     }
 }
 
@@ -717,7 +848,7 @@ __global__ void k_unpack_m(int N, BatchView<T> V, double* __restrict__ out) {
         const size_t ic = t / B;
         const size_t i = ic / 3, c = ic % 3;
         const int cur = V.st[b].cur;
-        out[((size_t)b * N + i) * 3 + c] = (double)V.m[(size_t)cur * N * 3 * B + t];
+        out[((size_t)b * N + i) * 3 + c] = V.m[(size_t)cur * N * 3 * B + t];
     }
 }
 
@@ -730,7 +861,7 @@ __global__ void k_unpack_field(int N, BatchView<T> V, double* __restrict__ h, do
         const size_t i = t / B;
         const double Js = V.ic[b].Js;
         if (h)
-            for (int c = 0; c < 3; ++c) h[((size_t)b * N + i) * 3 + c] = Js * (double)V.hout[(i * 3 + c) * B + b];
+            for (int c = 0; c < 3; ++c) h[((size_t)b * N + i) * 3 + c] = Js * V.hout[(i * 3 + c) * B + b];
         if (u) {
             u[((size_t)b * 2 + 0) * N + i] = cell * (double)V.u1[t];
             u[((size_t)b * 2 + 1) * N + i] = cell * (double)V.u2[t];
