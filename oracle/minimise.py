@@ -23,8 +23,9 @@ Readings where the paper prints no detail:
   * nonmonotone test: a BB trial is rejected iff its energy is strictly larger
     than the maximum of the last min(k, 20) accepted energies (the initial one
     included); the line search then uses E_ref = that maximum;
-  * adaptive BB rule: if s.y <= 0 keep the previous step; else push tau^2 into a
-    memory of the last 3 values; if tau^2/tau^1 <= kappa take tau = min of that
+  * adaptive BB rule: if s.y <= 0 (no positive curvature along the step) restart
+    with the first-step trial tau = 1/max_i |H_i| at the new point; else push
+    tau^2 into a memory of the last 3 values; if tau^2/tau^1 <= kappa take tau = min of that
     memory and kappa *= 0.9, else tau = tau^1 and kappa *= 1.1; kappa_0 = 0.5;
     tau clamped to [1e-10, 1e10];
   * stop when max_i |m_i x h_i| / Js < tol (or, optionally, sum |g|^2 < tol_g,
@@ -76,10 +77,10 @@ class BBState:
     tau2: list = field(default_factory=list)
 
 
-def next_bb_tau(s, y, tau_prev: float, st: BBState, rule: StepRule) -> float:
+def next_bb_tau(s, y, tau_restart: float, st: BBState, rule: StepRule) -> float:
     steps = bb_steps(s, y)
     if steps is None:
-        tau = tau_prev
+        tau = tau_restart
     else:
         t1, t2 = steps
         st.tau2.append(t2)
@@ -172,7 +173,7 @@ def minimise(prob: CubeProblem, m0: np.ndarray, h_ext, tol: float = 1e-6, max_it
         if converged(ev, gg):
             status = OK
             break
-        tau = next_bb_tau(s, y, tau, bb, rule)
+        tau = next_bb_tau(s, y, 1.0 / float(np.max(np.linalg.norm(H, axis=1))), bb, rule)
         searching, backtracks = False, 0
     return Result(m, ev.E, ev.terms, ev.torque, status, it, evals, line_searches, traj, hist)
 
