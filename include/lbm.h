@@ -75,6 +75,11 @@ typedef struct {
     double  tau_min, tau_max;
     int32_t demag;          /* 1: stray field on (default), 0: off */
     int32_t check_every;    /* host polls convergence every this many steps */
+    double  switch_tol;     /* mixed precision: the FP32 phase runs until
+                               max|m x h|/Js < switch_tol (or its line search
+                               stalls), then an FP64 phase finishes to tol */
+    double  cg_tol_polish;  /* relative residual of the potential solves in the
+                               FP64 phase of a mixed-precision run */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -93,7 +98,8 @@ typedef struct {
 } lbm_result;
 
 /* Fill `o` with the defaults for `precision` (tol 1e-6, memory 20, c1 1e-4,
- * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-7 mixed). */
+ * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-6 mixed,
+ * switch_tol 1e-4, cg_tol_polish 1e-13). */
 void lbm_default_opts(lbm_solve_opts* o, int32_t precision);
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t

@@ -33,7 +33,8 @@ class SolveOpts(C.Structure):
                 ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("c1", C.c_double),
                 ("max_backtracks", C.c_int32), ("memory", C.c_int32), ("kappa0", C.c_double),
                 ("m_alpha", C.c_int32), ("tau_min", C.c_double), ("tau_max", C.c_double),
-                ("demag", C.c_int32), ("check_every", C.c_int32)]
+                ("demag", C.c_int32), ("check_every", C.c_int32), ("switch_tol", C.c_double),
+                ("cg_tol_polish", C.c_double)]
 
 
 class ProfileStats(C.Structure):

@@ -70,6 +70,7 @@ struct Inst {
     InstConst* ic = nullptr;
     double* staged = nullptr;      // B*N*3 doubles (host <-> device layout conversion)
     double* staged_u = nullptr;    // B*2*N doubles
+    Inst* polish = nullptr;        // FP64 shadow batch finishing mixed-precision runs
     std::vector<lbm_material> mats;
     std::vector<double> h;         // B*3 tesla
     size_t bytes = 0;
@@ -150,41 +151,65 @@ void prof_harvest(lbm_ctx* ctx) {
     ctx->ev_live.clear();
 }
 
+// Byte offsets of the per-instance arrays inside one allocation; every array
+// starts on a 256-byte boundary (the PCG reads 8- and 16-byte vectors).
+struct VecLayout {
+    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+VecLayout vec_layout(const Mesh& M, int B, int tsize) {
+    const size_t N = M.N, nb = M.nb, C = 2 * (size_t)B;
+    VecLayout L;
+    size_t o = 0;
+    auto take = [&o](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+    L.m = take(8 * 2 * N * 3 * B);
+    L.g = take(8 * 2 * N * 3 * B);
+    L.hout = take(8 * N * 3 * B);
+    L.U1 = take(tsize * N * C);
+    L.U2 = take(tsize * N * C);
+    L.r = take(tsize * N * C);
+    L.z = take(tsize * N * C);
+    L.p = take(tsize * N * C);
+    L.q = take(tsize * N * C);
+    L.ub_in = take(tsize * nb * C);
+    L.ub_out = take(tsize * nb * C);
+    L.bem_part = take(8 * 32 * nb);
+    L.total = o;
+    return L;
+}
+
 template <typename T>
 BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool with_hout) {
     (void)ctx;
+    const VecLayout L = vec_layout(M, I.B, sizeof(T));
+    char* base = (char*)I.vec;
     BatchView<T> v;
-    const size_t N = M.N, B = I.B, nb = M.nb;
-    double* d = (double*)I.vec;
     v.B = I.B;
-    v.m = d; d += 2 * N * 3 * B;
-    v.H = d; d += 2 * N * 3 * B;
-    v.hout = with_hout ? d : nullptr; d += N * 3 * B;
-    T* p = (T*)d;
-    v.u1 = p; p += N * B;
-    v.u2 = p; p += N * B;
-    v.r = p; p += N * B;
-    v.z = p; p += N * B;
-    v.p = p; p += N * B;
-    v.q = p; p += N * B;
-    v.ub1 = p; p += nb * B;
-    v.ub2 = p; p += nb * B;
+    v.m = (double*)(base + L.m);
+    v.H = (double*)(base + L.g);
+    v.hout = with_hout ? (double*)(base + L.hout) : nullptr;
+    v.U1 = (T*)(base + L.U1);
+    v.U2 = (T*)(base + L.U2);
+    v.r = (T*)(base + L.r);
+    v.z = (T*)(base + L.z);
+    v.p = (T*)(base + L.p);
+    v.q = (T*)(base + L.q);
+    v.ub_in = (T*)(base + L.ub_in);
+    v.ub_out = (T*)(base + L.ub_out);
+    v.bem_part = (T*)(base + L.bem_part);
     v.part = I.part;
     v.st = I.st;
     v.ic = I.ic;
     return v;
 }
 
-// bytes of the per-instance vectors: FP64 state (m, H at base and trial, the
-// optional field output) and T-typed potential / CG / BEM vectors
-size_t vec_bytes(const Mesh& M, int B, int tsize) {
-    const size_t N = M.N, nb = M.nb;
-    return (size_t)B * (8 * (2 * N * 3 * 2 + 3 * N) + tsize * (6 * N + 2 * nb));
-}
+size_t vec_bytes(const Mesh& M, int B, int tsize) { return vec_layout(M, B, tsize).total; }
 
 size_t part_elems(const lbm_ctx* ctx, int B) {
     const size_t a = (size_t)4 * ctx->num_sms * B * NQ;   // field kernel partials
-    const size_t b = pcg_part_elems(ctx->num_sms, B);          // PCG (two regions)
+    const size_t b = pcg_part_elems(ctx->num_sms, B);          // PCG (two regions, 2B systems)
     return a > b ? a : b;
 }
 
@@ -206,6 +231,7 @@ void free_mesh(Mesh* m) {
 }
 
 void free_inst(Inst* I) {
+    if (I->polish) free_inst(I->polish);
     void* ptrs[] = {I->vec, I->part, I->st, I->ic, I->staged, I->staged_u};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -253,7 +279,8 @@ StepOpts step_opts(const lbm_solve_opts& o) {
 int check_opts(const lbm_solve_opts& o) {
     if (!(o.tol >= 0) || o.max_iter < 0 || o.memory < 1 || o.memory > HIST_MAX || o.m_alpha < 1 ||
         o.m_alpha > MALPHA_MAX || o.max_backtracks < 0 || o.cg_max_iter < 1 || !(o.cg_tol > 0) ||
-        o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min))
+        o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
+        !(o.cg_tol_polish > 0))
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -304,7 +331,7 @@ void fill_result(const InstState& s, const InstConst& c, lbm_result& r, double w
 
 template <typename T>
 int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res, bool evaluate_only,
-                 double* hout, double* uout) {
+                 double* hout, double* uout, std::vector<InstState>* states_out = nullptr) {
     Mesh& M = *ctx->meshes[I->mesh];
     const auto t0 = std::chrono::steady_clock::now();
     BatchView<T> V = batch_view<T>(ctx, M, *I, evaluate_only && hout);
@@ -370,7 +397,88 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
             ctx->prof_cg[0] += hs[b].cg1;
             ctx->prof_cg[1] += hs[b].cg2;
         }
+    if (states_out) *states_out = hs;
     (void)rc;
+    return LBM_OK;
+}
+
+__global__ void k_widen(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+// Mixed precision: an FP32 phase (FP32 potentials, BEM product and SpMV; FP64
+// state, reductions and step decisions) to switch_tol, then an FP64 phase on a
+// shadow batch warm-started from the FP32 state and potentials, to tol.
+int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res) {
+    Mesh& M = *ctx->meshes[I->mesh];
+    const auto t0 = std::chrono::steady_clock::now();
+    lbm_solve_opts o1 = o;
+    o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;
+    std::vector<InstState> s1, s2;
+    int rc = run_minimise<float>(ctx, I, o1, nullptr, false, nullptr, nullptr, &s1);
+    if (rc) return rc;
+    bool need = false;
+    for (int b = 0; b < I->B; ++b)
+        need |= s1[b].status != 4 && !(s1[b].status == 0 && s1[b].torque < o.tol);
+    const size_t N = M.N, B = I->B;
+    if (need) {
+        if (!I->polish) {
+            Inst* P = new Inst();
+            P->mesh = I->mesh;
+            P->B = I->B;
+            P->precision = LBM_FP64;
+            P->tsize = 8;
+            const size_t vb = vec_bytes(M, I->B, 8), pe = part_elems(ctx, I->B);
+            if (cudaMalloc(&P->vec, vb) != cudaSuccess || cudaMalloc(&P->part, pe * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&P->st, sizeof(InstState) * B) != cudaSuccess ||
+                cudaMalloc(&P->ic, sizeof(InstConst) * B) != cudaSuccess ||
+                cudaMalloc(&P->staged, sizeof(double) * B * N * 3) != cudaSuccess ||
+                cudaMalloc(&P->staged_u, sizeof(double) * B * N * 2) != cudaSuccess) {
+                free_inst(P);
+                return fail(LBM_E_OOM, "allocation of the FP64 phase of a mixed run failed");
+            }
+            CK(cudaMemsetAsync(P->vec, 0, vb, ctx->stream));
+            I->polish = P;
+        }
+        Inst* P = I->polish;
+        P->mats = I->mats;
+        P->h = I->h;
+        // state (m at base and trial, cur) and constants; potentials widened to FP64
+        CK(cudaMemcpyAsync(P->vec, I->vec, sizeof(double) * 2 * N * 3 * B, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(P->st, I->st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(P->ic, I->ic, sizeof(InstConst) * B, cudaMemcpyDeviceToDevice, ctx->stream));
+        const VecLayout L32 = vec_layout(M, I->B, 4), L64 = vec_layout(M, I->B, 8);
+        const size_t npot = N * 2 * B;
+        k_widen<<<4 * ctx->num_sms, 256, 0, ctx->stream>>>((const float*)((const char*)I->vec + L32.U1),
+                                                           (double*)((char*)P->vec + L64.U1), npot);
+        k_widen<<<4 * ctx->num_sms, 256, 0, ctx->stream>>>((const float*)((const char*)I->vec + L32.U2),
+                                                           (double*)((char*)P->vec + L64.U2), npot);
+        ctx->launches += 2;
+        lbm_solve_opts o2 = o;
+        o2.cg_tol = o.cg_tol_polish;
+        rc = run_minimise<double>(ctx, P, o2, nullptr, false, nullptr, nullptr, &s2);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(I->vec, P->vec, sizeof(double) * 2 * N * 3 * B, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(I->st, P->st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (res) {
+        std::vector<InstConst> hc(I->B);
+        CK(cudaMemcpy(hc.data(), I->ic, sizeof(InstConst) * I->B, cudaMemcpyDeviceToHost));
+        for (int b = 0; b < I->B; ++b) {
+            const bool two = need && s1[b].status != 4;
+            fill_result(two ? s2[b] : s1[b], hc[b], res[b], ms);
+            if (two) {
+                res[b].iterations += s1[b].iters;
+                res[b].evaluations += s1[b].evals;
+                res[b].line_searches += s1[b].line_searches;
+                res[b].cg_iters1 += s1[b].cg1;
+                res[b].cg_iters2 += s1[b].cg2;
+            }
+        }
+    }
     return LBM_OK;
 }
 
@@ -394,6 +502,9 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->tau_max = 1e10;
     o->demag = 1;
     o->check_every = 16;
+    o->switch_tol = 1e-4;
+    o->cg_tol_polish = 1e-13;
+    if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
 const char* lbm_last_error(void) { return g_err.c_str(); }
@@ -780,8 +891,8 @@ int lbm_minimise(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, lbm_res
     int rc = check_opts(o);
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
-    return I->tsize == 8 ? run_minimise<double>(ctx, I, o, res, false, nullptr, nullptr)
-                         : run_minimise<float>(ctx, I, o, res, false, nullptr, nullptr);
+    if (I->tsize == 8) return run_minimise<double>(ctx, I, o, res, false, nullptr, nullptr);
+    return minimise_mixed(ctx, I, o, res);
 }
 
 int lbm_hysteresis(lbm_ctx* ctx, lbm_inst inst, const double dir[3], const double* fields, int32_t n_pts,

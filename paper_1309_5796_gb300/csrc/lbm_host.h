@@ -43,12 +43,16 @@ template <typename T>
 struct BatchView {
     int B;
     double* m;   // [2][N][3][B]   m[cur] = base point, m[1-cur] = trial (FP64 in every mode)
-    double* H;   // [2][N][3][B]   H = -m x grad phi at the same points (FP64)
-    T* u1;       // [N][B]
-    T* u2;       // [N][B]
-    T* r; T* z; T* p; T* q;    // [N][B] PCG work vectors
-    T* ub1;      // [nb][B]  u1 on the surface (BEM input)
-    T* ub2;      // [nb][B]  u2 on the surface (BEM output)
+    double* H;   // [2][N][3][B]   grad phi at the same points (FP64)
+    // Potentials of the forward FEM/BEM chain (u = X b) and of its adjoint
+    // (uT = X^T b), solved side by side: column c < B belongs to instance c
+    // (forward), column B + b to instance b (adjoint).
+    T* U1;       // [N][2B]  stage 1: u1 (Neumann) | w (Dirichlet, zero surface values)
+    T* U2;       // [N][2B]  stage 2: u2 (Dirichlet, surface values B u1) | uT (Neumann)
+    T* r; T* z; T* p; T* q;    // [N][2B] PCG work vectors
+    T* ub_in;    // [nb][2B] BEM input:  u1 on the surface | t = b_S - K_SI w
+    T* ub_out;   // [nb][2B] BEM output: B u1_S | B^T t
+    T* bem_part; // column-split partial sums of the transposed product (scratch)
     double* part;              // partial sums, >= maxblocks * B * NQ
     InstState* st;             // [B]
     const InstConst* ic;       // [B]

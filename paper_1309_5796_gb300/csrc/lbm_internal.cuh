@@ -19,6 +19,7 @@ enum {
     Q_GG, Q_SS, Q_SY, Q_YY,            // sum |g|^2, s.s, s.y, y.y (sum)
     Q_MX, Q_MY, Q_MZ,                  // sum Vint m (sum)
     Q_BAD,                             // non-finite flag (max)
+    Q_DE,                              // E(trial) - E(base) by the trapezoid rule (sum)
     Q_COUNT
 };
 constexpr int NQ = 16;                 // stride of the partials array
@@ -42,12 +43,14 @@ struct InstConst {
 struct StepOpts {
     double tol, grad_tol, c1, kappa0, tau_min, tau_max;
     int max_iter, max_backtracks, memory, m_alpha;
+    int stop_on_linesearch_fail;   // 1: a failed line search ends the run (status LINESEARCH)
 };
 
 struct InstState {
     int phase, status, cur, iters, evals, line_searches, backtracks, nhist, hpos, ntau2;
     long long cg1, cg2;
     double tau, E_ref, gg_base, E, kappa, torque, gg;
+    double Eacc;                   // base energy carried by exact differences (decisions)
     double terms[4];
     double mean_m[3];
     double hist[HIST_MAX];

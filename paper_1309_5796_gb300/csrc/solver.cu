@@ -20,7 +20,7 @@
 namespace lbm {
 
 constexpr int PCG_THREADS = 512;        // grid-wide (cooperative) variant
-constexpr int PCG_SINGLE_THREADS = 1024; // one-CTA variant for small batches
+constexpr int PCG_SINGLE_THREADS = 512;  // one-CTA variant for small batches
 constexpr int FIELD_THREADS = 256;
 constexpr int MAXR = 16;                 // row length served by the unrolled gather (Kuhn rows: 15)
 constexpr long long SINGLE_CTA_MAX_WORK = 24576;   // N * B up to which one CTA solves
@@ -38,7 +38,6 @@ __device__ __forceinline__ void block_reduce_inst(double (&v)[NQV], double* scra
                                                   unsigned maxmask) {
     const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
     if (B <= 32 && (32 % B) == 0) {
-        // lanes of one instance differ by multiples of B within the warp
         for (int off = 16; off >= B; off >>= 1)
 #pragma unroll
             for (int q = 0; q < NQV; ++q) {
@@ -78,30 +77,99 @@ __device__ __forceinline__ void block_reduce_inst(double (&v)[NQV], double* scra
     __syncthreads();
 }
 
-// Totals over blocks of partials part[blk][B][4] (quantities q0..q0+NQV-1), in a
-// fixed order, into out[q*B + b].
-template <int NQV>
-__device__ __forceinline__ void cross_reduce(const double* part, int q0, int nblk, int B, int RB, double* scratch,
-                                             double* out) {
-    const int tid = threadIdx.x, b = tid % B, rl = tid / B;
-    double v[NQV];
+// Column sums for threads that each hold VEC consecutive columns: thread tid is
+// row lane rl = tid / G of column group g = tid % G (columns g*VEC .. +VEC-1,
+// C = G*VEC).  Fixed summation order; totals in out[q*C + c].  `scratch` holds
+// at least NQV * max(bd/32, RB) * C doubles.
+template <int NQV, int VEC>
+__device__ __forceinline__ void block_reduce_cols(double (&v)[NQV][VEC], double* scratch, double* out, int C,
+                                                  int G, int RB) {
+    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, g = tid % G;
+    int nrow;
+    if (G <= 32 && (32 % G) == 0) {
+        // lanes of one column group differ by multiples of G within the warp
+        for (int off = 16; off >= G; off >>= 1)
 #pragma unroll
-    for (int q = 0; q < NQV; ++q) v[q] = 0.0;
-    if (tid < RB * B) {
-#pragma unroll 4
-        for (int blk = rl; blk < nblk; blk += RB)
+            for (int q = 0; q < NQV; ++q)
 #pragma unroll
-            for (int q = 0; q < NQV; ++q) v[q] += __ldcg(&part[((size_t)blk * B + b) * 4 + q0 + q]);
+                for (int k = 0; k < VEC; ++k) v[q][k] += __shfl_xor_sync(0xffffffffu, v[q][k], off);
+        nrow = bd >> 5;
+        if (lane < G)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q)
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) scratch[(q * nrow + warp) * C + g * VEC + k] = v[q][k];
+    } else {
+        nrow = RB;
+        const int rl = tid / G;
+        if (tid < RB * G)
+#pragma unroll
+            for (int q = 0; q < NQV; ++q)
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) scratch[(q * nrow + rl) * C + g * VEC + k] = v[q][k];
     }
-    block_reduce_inst<NQV>(v, scratch, out, B, RB, 0u);
+    __syncthreads();
+    for (int t = tid; t < NQV * C; t += bd) {
+        const int q = t / C, c = t % C;
+        double acc = 0.0;
+        for (int r = 0; r < nrow; ++r) acc += scratch[(q * nrow + r) * C + c];
+        out[q * C + c] = acc;
+    }
+    __syncthreads();
 }
 
-// sum_j K_ij (v_j - v_i) (DIFF) or sum_j K_ij v_j over one CSR row; all column
-// indices, then all values, are loaded before any arithmetic so the gathers of
-// a row are in flight together.
-template <typename T, bool CG, bool DIFF>
-__device__ __forceinline__ T row_k(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
-                                   const T* v, int B, int b, T vi) {
+// Totals over blocks of partials part[blk][C][4] (quantities q0..q0+NQV-1), in a
+// fixed order, into out[q*C + c] (threads hold VEC columns each, as above).
+template <int NQV, int VEC>
+__device__ __forceinline__ void cross_reduce_cols(const double* part, int q0, int nblk, int C, int G, int RB,
+                                                  double* scratch, double* out) {
+    const int tid = threadIdx.x, g = tid % G, rl = tid / G;
+    double v[NQV][VEC];
+#pragma unroll
+    for (int q = 0; q < NQV; ++q)
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[q][k] = 0.0;
+    if (tid < RB * G) {
+#pragma unroll 2
+        for (int blk = rl; blk < nblk; blk += RB)
+#pragma unroll
+            for (int k = 0; k < VEC; ++k)
+#pragma unroll
+                for (int q = 0; q < NQV; ++q) v[q][k] += __ldcg(&part[((size_t)blk * C + g * VEC + k) * 4 + q0 + q]);
+    }
+    block_reduce_cols<NQV, VEC>(v, scratch, out, C, G, RB);
+}
+
+template <typename T, int VEC> struct VecOf;
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<double, 2> { using type = double2; };
+
+template <typename T, int VEC, bool CG>
+__device__ __forceinline__ void vload(T (&d)[VEC], const T* p) {
+    using V = typename VecOf<T, VEC>::type;
+    V x;
+    if constexpr (CG) x = __ldcg(reinterpret_cast<const V*>(p));
+    else x = *reinterpret_cast<const V*>(p);
+    if constexpr (VEC == 4) { d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w; }
+    else { d[0] = x.x; d[1] = x.y; }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void vstore(T* p, const T (&d)[VEC]) {
+    using V = typename VecOf<T, VEC>::type;
+    V x;
+    if constexpr (VEC == 4) { x.x = d[0]; x.y = d[1]; x.z = d[2]; x.w = d[3]; }
+    else { x.x = d[0]; x.y = d[1]; }
+    *reinterpret_cast<V*>(p) = x;
+}
+
+// acc[k] = sum_j K_ij (v_j - v_i) (DIFF) or sum_j K_ij v_j for VEC consecutive
+// columns of one CSR row; the row's column indices, then all its vector loads,
+// are issued before any arithmetic so that they are in flight together.
+template <typename T, int VEC, bool CG, bool DIFF>
+__device__ __forceinline__ void row_kv(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
+                                       const T* v, int C, int c0, const T (&vi)[VEC], T (&acc)[VEC]) {
     int cj[MAXR], kj[MAXR];
 #pragma unroll
     for (int t = 0; t < MAXR; ++t) {
@@ -110,24 +178,33 @@ __device__ __forceinline__ T row_k(const int* __restrict__ col, const int* __res
         cj[t] = ok ? (__ldg(&col[e]) & 0x7fffffff) : -1;
         kj[t] = ok ? sbyte(__ldg(&pkA[e]), 0) : 0;
     }
-    T vj[MAXR];
+    T vj[MAXR][VEC];
 #pragma unroll
-    for (int t = 0; t < MAXR; ++t) vj[t] = cj[t] >= 0 ? ld_vec<T, CG>(&v[(size_t)cj[t] * B + b]) : vi;
-    T acc = T(0);
+    for (int t = 0; t < MAXR; ++t) {
+        if (cj[t] >= 0) vload<T, VEC, CG>(vj[t], &v[(size_t)cj[t] * C + c0]);
+        else
 #pragma unroll
-    for (int t = 0; t < MAXR; ++t) acc += T(kj[t]) * (DIFF ? (vj[t] - vi) : vj[t]);
-    for (int e = e0 + MAXR; e < e1; ++e) {
-        const T x = ld_vec<T, CG>(&v[(size_t)(col[e] & 0x7fffffff) * B + b]);
-        acc += T(sbyte(pkA[e], 0)) * (DIFF ? (x - vi) : x);
+            for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
     }
-    return acc;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) acc[k] = T(0);
+#pragma unroll
+    for (int t = 0; t < MAXR; ++t)
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc[k] += T(kj[t]) * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
+    for (int e = e0 + MAXR; e < e1; ++e) {
+        T x[VEC];
+        vload<T, VEC, CG>(x, &v[(size_t)(col[e] & 0x7fffffff) * C + c0]);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc[k] += T(sbyte(pkA[e], 0)) * (DIFF ? (x[k] - vi[k]) : x[k]);
+    }
 }
 
 template <typename T>
 struct PcgArgs {
     MeshView M;
     BatchView<T> V;
-    int mode;          // 0: Neumann (u1), 1: Dirichlet (u2)
+    int mode;          // 0: stage 1 (u1 | w), 1: stage 2 (u2 | uT)
     double tol2;       // squared relative residual
     int max_iter;
     unsigned* bar;
@@ -145,313 +222,443 @@ __device__ __forceinline__ bool pcg_sync(unsigned* bar, unsigned& epoch, int* er
     }
 }
 
-// Jacobi-PCG on Kint for B instances at once, fused so that every iteration
-// needs two synchronisations (grid barriers, or __syncthreads in the one-CTA
-// variant):
+// b_i = (1/4) sum_j Gint_ij . m_j (the divergence right-hand side) at the trial point
+__device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
+                                        const double* meval, int B, int b) {
+    double acc = 0.0;
+    for (int e = e0; e < e1; ++e) {
+        const int w = __ldg(&pkA[e]);
+        const size_t mj = (size_t)(__ldg(&col[e]) & 0x7fffffff) * 3 * B + b;
+        acc += sbyte(w, 1) * meval[mj] + sbyte(w, 2) * meval[mj + B] + sbyte(w, 3) * meval[mj + 2 * B];
+    }
+    return 0.25 * acc;
+}
+
+// Jacobi-PCG on Kint for the 2B systems of one stage of the forward and adjoint
+// FEM/BEM chains (column c: instance c % B, adjoint if c >= B):
+//   stage 1: forward  K u1 = b               (Neumann)
+//            adjoint  K_II w_I = b_I, w_S = 0 (Dirichlet)
+//   stage 2: forward  K_II u2_I = -K_IS u2_S, u2_S = B u1_S   (Dirichlet)
+//            adjoint  K uT = b + S^T B^T t,  t = b_S - K_SI w  (Neumann)
+// Each thread owns VEC consecutive columns of a row (one 8- or 16-byte vector),
+// so every neighbour gather of the SpMV moves VEC values per lane.  Fused so
+// that every iteration needs two synchronisations (grid barriers, or
+// __syncthreads in the one-CTA variant):
 //   A: w = K z, p = z + beta p, q = w + beta q (= K p), partial p.q
 //   B: alpha = rho/p.q, x += alpha p, r -= alpha q, z = r / K_ii, partials r.z, r.r
-// Neumann: rhs = (1/4) Gint m at the trial point, made consistent (mean
-// removed); the residual is tested without its mean; the solution is gauged to
-// zero V-weighted mean and its surface values are gathered for the BEM.
-// Dirichlet: the surface values come from the BEM product; surface rows are
-// frozen (r = z = p = q = 0).
-template <typename T, bool SINGLE>
+// Neumann systems: the right-hand side is made consistent (mean removed), the
+// residual is tested without its mean, and the solution is gauged to zero
+// V-weighted mean.  Dirichlet systems freeze the surface rows (p = q = r = z = 0).
+template <typename T, bool SINGLE, int VEC>
 __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) k_pcg(PcgArgs<T> A) {
     extern __shared__ double sm[];
     constexpr bool CG = !SINGLE;
     const int bd = blockDim.x, tid = threadIdx.x;
-    const int B = A.V.B, RB = bd / B;
-    const bool lane = tid < RB * B;
-    const int b = tid % B, rl = tid / B;
-    double* scratch = sm;                // [4][bd]
-    double* out = scratch + 4 * bd;      // [4][B]
-    double* s_rho = out + 4 * B;         // [B]
-    double* s_rhop = s_rho + B;
-    double* s_ab = s_rhop + B;
-    double* s_tol = s_ab + B;
-    int* s_flag = (int*)(s_tol + B);
-    int* s_act = s_flag + B;
-    int* s_cur = s_act + B;
-    int* s_it = s_cur + B;
+    const int B = A.V.B, C = 2 * B, G = C / VEC, RB = bd / G;
+    const bool lane = tid < RB * G;
+    const int g = tid % G, rl = tid / G, c0 = g * VEC;
+    const int mode = A.mode;
+    // shared memory: reduction scratch, then per-column state
+    const int nrow_red = (G <= 32 && (32 % G) == 0) ? (bd >> 5) : RB;
+    double* scratch = sm;                               // [4][nrow_red][C]
+    double* out = scratch + 4 * nrow_red * C;           // [4][C]
+    double* s_rho = out + 4 * C;                        // [C]
+    double* s_rhop = s_rho + C;
+    double* s_ab = s_rhop + C;
+    double* s_tol = s_ab + C;
+    int* s_flag = (int*)(s_tol + C);
+    int* s_act = s_flag + C;
+    int* s_cur = s_act + C;
+    int* s_it = s_cur + C;
     __shared__ int s_all;
 
-    for (int i = tid; i < B; i += bd) {
-        s_act[i] = A.V.st[i].phase != PH_DONE;
-        s_cur[i] = A.V.st[i].cur;
+    for (int i = tid; i < C; i += bd) {
+        s_act[i] = A.V.st[i % B].phase != PH_DONE;
+        s_cur[i] = A.V.st[i % B].cur;
         s_it[i] = 0;
         s_rhop[i] = 1.0;
     }
     __syncthreads();
     const int N = A.M.N;
-    const bool dir = A.mode == 1;
-    const bool act = lane && s_act[b];
+    int bk[VEC];            // instance of each owned column
+    bool neu[VEC], actk[VEC];
+    bool any_act = false;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        const int c = c0 + k;
+        bk[k] = c % B;
+        neu[k] = (mode == c / B);
+        actk[k] = lane && s_act[c];
+        any_act |= actk[k];
+    }
     const int row0 = blockIdx.x * RB + rl, rstride = gridDim.x * RB;
     const int* __restrict__ rowptr = A.M.rowptr;
     const int* __restrict__ col = A.M.col;
     const int* __restrict__ pkA = A.M.pkA;
     const int* __restrict__ node = A.M.node;
-    T* __restrict__ x = dir ? A.V.u2 : A.V.u1;
+    T* __restrict__ x = mode ? A.V.U2 : A.V.U1;
     T* __restrict__ r = A.V.r;
     T* __restrict__ z = A.V.z;
     T* __restrict__ p = A.V.p;
     T* __restrict__ q = A.V.q;
     double* part_rz = A.V.part;
-    double* part_pq = A.V.part + (size_t)gridDim.x * B * 4;
+    double* part_pq = A.V.part + (size_t)gridDim.x * C * 4;
     unsigned epoch = 0;
-    const double* meval = A.V.m + (size_t)(1 - s_cur[b]) * N * 3 * B;
 
-    if (dir) {
-        if (act)
-            for (int row = row0; row < N; row += rstride) {
-                const int bp = (int)((unsigned)node[row] >> 16);
-                if (bp) x[(size_t)row * B + b] = A.V.ub2[(size_t)(bp - 1) * B + b];
-            }
-        if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-    }
+    // Dirichlet systems: surface values (stage 1 adjoint: zero; stage 2 forward: B u1_S)
+    if (any_act)
+        for (int row = row0; row < N; row += rstride) {
+            const int bp = (int)((unsigned)node[row] >> 16);
+            if (!bp) continue;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k)
+                if (actk[k] && !neu[k])
+                    x[(size_t)row * C + c0 + k] = mode ? A.V.ub_out[(size_t)(bp - 1) * C + bk[k]] : T(0);
+        }
+    if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
     {   // residual of the warm start
-        // Neumann: the system is singular with null space span{1}; the right-hand
-        // side is made consistent (sum zero) by removing its mean before use.
-        double psum[1] = {0.0};
-        if (act)
+        double psum[1][VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) psum[0][k] = 0.0;
+        if (any_act)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
-                const size_t ib = (size_t)row * B + b;
-                if (dir && ((unsigned)nd >> 16)) { r[ib] = T(0); z[ib] = T(0); p[ib] = T(0); q[ib] = T(0); continue; }
+                const int bp = (int)((unsigned)nd >> 16);
+                const size_t ib = (size_t)row * C + c0;
                 const int e0 = rowptr[row], e1 = rowptr[row + 1];
-                const T xi = x[ib];
-                const T kx = row_k<T, CG, true>(col, pkA, e0, e1, x, B, b, xi);
-                T rhs = T(0);
-                if (!dir) {
-                    double acc = 0.0;
-                    for (int e = e0; e < e1; ++e) {
-                        const int w = pkA[e];
-                        const size_t mj = (size_t)(col[e] & 0x7fffffff) * 3 * B + b;
-                        acc += sbyte(w, 1) * meval[mj] + sbyte(w, 2) * meval[mj + B] + sbyte(w, 3) * meval[mj + 2 * B];
-                    }
-                    rhs = T(0.25 * acc);
-                } else {
-                    for (int e = e0; e < e1; ++e) {
-                        const int c = col[e];
-                        if (c < 0) rhs -= T(sbyte(pkA[e], 0)) * ld_vec<T, CG>(&x[(size_t)(c & 0x7fffffff) * B + b]);
+                T xi[VEC], kx[VEC], rv[VEC], zv[VEC];
+                vload<T, VEC, false>(xi, &x[ib]);
+                row_kv<T, VEC, CG, true>(col, pkA, e0, e1, x, C, c0, xi, kx);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    if (!neu[k] && bp) { rv[k] = T(0); zv[k] = T(0); continue; }
+                    // f: the right-hand side (b in every system but the stage-2 forward one)
+                    double f = 0.0;
+                    if (!(mode == 1 && !neu[k]))
+                        f = rhs_b(col, pkA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k]);
+                    if (mode == 1 && neu[k] && bp) f += (double)A.V.ub_out[(size_t)(bp - 1) * C + c0 + k];
+                    double ref = f;   // norm reference: f (Neumann), f - K_IS x_S (Dirichlet)
+                    if (!neu[k])
+                        for (int e = e0; e < e1; ++e) {
+                            const int cc = col[e];
+                            if (cc < 0) ref -= (double)sbyte(pkA[e], 0) *
+                                               (double)ld_vec<T, CG>(&x[(size_t)(cc & 0x7fffffff) * C + c0 + k]);
+                        }
+                    rv[k] = T(f) - kx[k];
+                    zv[k] = T(ref);                       // kept for the second pass
+                    if (actk[k]) psum[0][k] += f;
+                }
+                const T zero[VEC] = {};
+                vstore<T, VEC>(&r[ib], rv);
+                vstore<T, VEC>(&z[ib], zv);
+                vstore<T, VEC>(&p[ib], zero);
+                vstore<T, VEC>(&q[ib], zero);
+            }
+        // Neumann: consistent right-hand side (sum zero)
+        block_reduce_cols<1, VEC>(psum, scratch, out, C, G, RB);
+        if (SINGLE) {
+            if (tid < C) s_ab[tid] = out[tid] / (double)N;
+        } else {
+            if (tid < C) part_pq[((size_t)blockIdx.x * C + tid) * 4 + 2] = out[tid];
+            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+            cross_reduce_cols<1, VEC>(part_pq, 2, gridDim.x, C, G, RB, scratch, out);
+            if (tid < C) s_ab[tid] = out[tid] / (double)N;
+        }
+        __syncthreads();
+        T mean[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) mean[k] = neu[k] ? T(s_ab[c0 + k]) : T(0);
+        double v4[4][VEC];   // r.z, r.r, ref.ref, sum r
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = 0.0;
+        if (any_act)
+            for (int row = row0; row < N; row += rstride) {
+                const int nd = node[row];
+                const bool surf = ((unsigned)nd >> 16) != 0;
+                const size_t ib = (size_t)row * C + c0;
+                const T dinv = T(1) / T((nd >> 8) & 0xff);
+                T rv[VEC], zv[VEC];
+                vload<T, VEC, false>(rv, &r[ib]);
+                vload<T, VEC, false>(zv, &z[ib]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    if (!neu[k] && surf) continue;
+                    const T ref = zv[k] - mean[k];
+                    rv[k] -= mean[k];
+                    zv[k] = rv[k] * dinv;
+                    if (actk[k]) {
+                        v4[0][k] += (double)rv[k] * (double)zv[k];
+                        v4[1][k] += (double)rv[k] * (double)rv[k];
+                        v4[2][k] += (double)ref * (double)ref;
+                        v4[3][k] += (double)rv[k];
                     }
                 }
-                r[ib] = dir ? -kx : rhs - kx;
-                z[ib] = rhs;                          // kept for the second pass
-                p[ib] = T(0);
-                q[ib] = T(0);
-                psum[0] += (double)rhs;
+                vstore<T, VEC>(&r[ib], rv);
+                vstore<T, VEC>(&z[ib], zv);
             }
-        double mean = 0.0;
-        if (!dir) {
-            block_reduce_inst<1>(psum, scratch, out, B, RB, 0u);
-            if (SINGLE) {
-                if (tid < B) s_ab[tid] = out[tid] / (double)N;
-            } else {
-                if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4 + 2] = out[tid];
-                if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-                cross_reduce<1>(part_pq, 2, gridDim.x, B, RB, scratch, out);
-                if (tid < B) s_ab[tid] = out[tid] / (double)N;
-            }
-            __syncthreads();
-            mean = s_ab[b];
-        }
-        double v4[4] = {0.0, 0.0, 0.0, 0.0};   // r.z, r.r, rhs.rhs, sum r
-        if (act)
-            for (int row = row0; row < N; row += rstride) {
-                const int nd = node[row];
-                if (dir && ((unsigned)nd >> 16)) continue;
-                const size_t ib = (size_t)row * B + b;
-                const T rhs = z[ib] - T(mean);
-                const T ri = r[ib] - T(mean);
-                const T zi = ri / T((nd >> 8) & 0xff);
-                r[ib] = ri;
-                z[ib] = zi;
-                v4[0] += (double)ri * (double)zi;
-                v4[1] += (double)ri * (double)ri;
-                v4[2] += (double)rhs * (double)rhs;
-                v4[3] += (double)ri;
-            }
-        block_reduce_inst<4>(v4, scratch, out, B, RB, 0u);
+        block_reduce_cols<4, VEC>(v4, scratch, out, C, G, RB);
         if (!SINGLE) {
-            if (tid < B)
-                for (int k = 0; k < 4; ++k) part_rz[((size_t)blockIdx.x * B + tid) * 4 + k] = out[k * B + tid];
+            if (tid < C)
+                for (int k = 0; k < 4; ++k) part_rz[((size_t)blockIdx.x * C + tid) * 4 + k] = out[k * C + tid];
             if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
         }
     }
-    for (int k = 0;; ++k) {
-        if (!SINGLE) cross_reduce<4>(part_rz, 0, gridDim.x, B, RB, scratch, out);
-        if (tid < B) {
+    for (int it = 0;; ++it) {
+        if (!SINGLE) cross_reduce_cols<4, VEC>(part_rz, 0, gridDim.x, C, G, RB, scratch, out);
+        if (tid < C) {
+            const bool nn = (mode == tid / B);
             const double rho = out[tid];
             // Neumann: test the residual without its null-space (mean) component,
             // which rounding feeds and CG cannot remove
-            const double sr = out[3 * B + tid];
-            const double rr = dir ? out[B + tid] : fmax(out[B + tid] - sr * sr / (double)N, 0.0);
-            if (k == 0) s_tol[tid] = A.tol2 * out[2 * B + tid];
-            const int conv = !s_act[tid] || rr <= s_tol[tid] || k >= A.max_iter;
-            s_ab[tid] = (k == 0 || conv) ? 0.0 : rho / s_rhop[tid];
+            const double sr = out[3 * C + tid];
+            const double rr = nn ? fmax(out[C + tid] - sr * sr / (double)N, 0.0) : out[C + tid];
+            if (it == 0) s_tol[tid] = A.tol2 * out[2 * C + tid];
+            const int conv = !s_act[tid] || rr <= s_tol[tid] || it >= A.max_iter;
+            s_ab[tid] = (it == 0 || conv) ? 0.0 : rho / s_rhop[tid];
             s_rho[tid] = rho;
             s_flag[tid] = conv;
         }
         __syncthreads();
         if (tid == 0) {
             int all = 1;
-            for (int i = 0; i < B; ++i) all &= s_flag[i];
+            for (int i = 0; i < C; ++i) all &= s_flag[i];
             s_all = all;
         }
         __syncthreads();
         if (s_all) break;
-        const bool run = act && !s_flag[b];
-        double ppq[1] = {0.0};
-        if (run) {
-            const T beta = T(s_ab[b]);
+        bool run = false;
+        T beta[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            run |= actk[k] && !s_flag[c0 + k];
+            beta[k] = T(s_ab[c0 + k]);
+        }
+        double ppq[1][VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) ppq[0][k] = 0.0;
+        if (run)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
-                if (dir && ((unsigned)nd >> 16)) continue;
-                const size_t ib = (size_t)row * B + b;
-                const T w = row_k<T, CG, false>(col, pkA, rowptr[row], rowptr[row + 1], z, B, b, T(0));
-                const T pi = z[ib] + beta * p[ib];
-                const T qi = w + beta * q[ib];
-                p[ib] = pi;
-                q[ib] = qi;
-                ppq[0] += (double)pi * (double)qi;
+                const bool surf = ((unsigned)nd >> 16) != 0;
+                const size_t ib = (size_t)row * C + c0;
+                T zi[VEC], w[VEC], pv[VEC], qv[VEC];
+                vload<T, VEC, false>(zi, &z[ib]);
+                row_kv<T, VEC, CG, false>(col, pkA, rowptr[row], rowptr[row + 1], z, C, c0, zi, w);
+                vload<T, VEC, false>(pv, &p[ib]);
+                vload<T, VEC, false>(qv, &q[ib]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    pv[k] = zi[k] + beta[k] * pv[k];
+                    qv[k] = (!neu[k] && surf) ? T(0) : w[k] + beta[k] * qv[k];
+                    ppq[0][k] += (double)pv[k] * (double)qv[k];
+                }
+                vstore<T, VEC>(&p[ib], pv);
+                vstore<T, VEC>(&q[ib], qv);
             }
-        }
-        block_reduce_inst<1>(ppq, scratch, out, B, RB, 0u);
+        block_reduce_cols<1, VEC>(ppq, scratch, out, C, G, RB);
         if (!SINGLE) {
-            if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4] = out[tid];
+            if (tid < C) part_pq[((size_t)blockIdx.x * C + tid) * 4] = out[tid];
             if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-            cross_reduce<1>(part_pq, 0, gridDim.x, B, RB, scratch, out);
+            cross_reduce_cols<1, VEC>(part_pq, 0, gridDim.x, C, G, RB, scratch, out);
         }
-        if (tid < B) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
+        if (tid < C) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
         __syncthreads();
-        double v4[4] = {0.0, 0.0, 0.0, 0.0};
-        if (run) {
-            const T alpha = T(s_ab[b]);
+        T alpha[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) alpha[k] = T(s_ab[c0 + k]);
+        double v4[4][VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = 0.0;
+        if (run)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
-                if (dir && ((unsigned)nd >> 16)) continue;
-                const size_t ib = (size_t)row * B + b;
-                const T xi = x[ib] + alpha * p[ib];
-                const T ri = r[ib] - alpha * q[ib];
-                const T zi = ri / T((nd >> 8) & 0xff);
-                x[ib] = xi;
-                r[ib] = ri;
-                z[ib] = zi;
-                v4[0] += (double)ri * (double)zi;
-                v4[1] += (double)ri * (double)ri;
-                v4[3] += (double)ri;
+                const size_t ib = (size_t)row * C + c0;
+                const T dinv = T(1) / T((nd >> 8) & 0xff);
+                T xv[VEC], rv[VEC], pv[VEC], qv[VEC], zv[VEC];
+                vload<T, VEC, false>(xv, &x[ib]);
+                vload<T, VEC, false>(rv, &r[ib]);
+                vload<T, VEC, false>(pv, &p[ib]);
+                vload<T, VEC, false>(qv, &q[ib]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    xv[k] += alpha[k] * pv[k];
+                    rv[k] -= alpha[k] * qv[k];
+                    zv[k] = rv[k] * dinv;
+                    v4[0][k] += (double)rv[k] * (double)zv[k];
+                    v4[1][k] += (double)rv[k] * (double)rv[k];
+                    v4[3][k] += (double)rv[k];
+                }
+                vstore<T, VEC>(&x[ib], xv);
+                vstore<T, VEC>(&r[ib], rv);
+                vstore<T, VEC>(&z[ib], zv);
             }
-        }
-        block_reduce_inst<4>(v4, scratch, out, B, RB, 0u);
+        block_reduce_cols<4, VEC>(v4, scratch, out, C, G, RB);
         if (!SINGLE) {
-            if (tid < B)
+            if (tid < C)
                 for (int kk = 0; kk < 4; ++kk)
-                    if (kk != 2) part_rz[((size_t)blockIdx.x * B + tid) * 4 + kk] = out[kk * B + tid];
+                    if (kk != 2) part_rz[((size_t)blockIdx.x * C + tid) * 4 + kk] = out[kk * C + tid];
             if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
         } else {
             __syncthreads();
         }
-        if (tid < B) {
+        if (tid < C) {
             s_rhop[tid] = s_rho[tid];
             if (!s_flag[tid]) s_it[tid] += 1;
         }
     }
     if (blockIdx.x == 0) {
-        for (int i = tid; i < B; i += bd) {
-            if (dir) A.V.st[i].cg2 += s_it[i];
-            else A.V.st[i].cg1 += s_it[i];
+        for (int i = tid; i < C; i += bd) {
+            const bool nn = (mode == i / B);
+            if (nn) atomicAdd((unsigned long long*)&A.V.st[i % B].cg1, (unsigned long long)s_it[i]);
+            else atomicAdd((unsigned long long*)&A.V.st[i % B].cg2, (unsigned long long)s_it[i]);
         }
         if (tid == 0 && A.sweeps) {
             int kmax = 0;
-            for (int i = 0; i < B; ++i) kmax = max(kmax, s_it[i]);
-            A.sweeps[dir ? 1 : 0] += (unsigned long long)kmax;
+            for (int i = 0; i < C; ++i) kmax = max(kmax, s_it[i]);
+            A.sweeps[mode] += (unsigned long long)kmax;
         }
     }
-    if (dir) return;
-    // gauge: remove the V-weighted mean; gather the surface values
-    {
-        double pv[1] = {0.0};
-        if (act)
-            for (int row = row0; row < N; row += rstride)
-                pv[0] += (double)(node[row] & 0xff) * (double)x[(size_t)row * B + b];
-        block_reduce_inst<1>(pv, scratch, out, B, RB, 0u);
-        if (!SINGLE) {
-            if (tid < B) part_pq[((size_t)blockIdx.x * B + tid) * 4 + 1] = out[tid];
-            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-            cross_reduce<1>(part_pq, 1, gridDim.x, B, RB, scratch, out);
+    // epilogue: Neumann systems are gauged to zero V-weighted mean; stage 1 then
+    // hands the surface values to the BEM products: u1_S (forward) and
+    // t = b_S - K_SI w (adjoint; w vanishes on the surface, so K_SI w = (K w)_S).
+    double pv[1][VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) pv[0][k] = 0.0;
+    if (any_act)
+        for (int row = row0; row < N; row += rstride) {
+            const double vi = (double)(node[row] & 0xff);
+            T xv[VEC];
+            vload<T, VEC, false>(xv, &x[(size_t)row * C + c0]);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k)
+                if (neu[k]) pv[0][k] += vi * (double)xv[k];
         }
-        if (tid < B) s_ab[tid] = out[tid] / A.M.vsum;
-        __syncthreads();
-        if (act) {
-            const T mean = T(s_ab[b]);
-            for (int row = row0; row < N; row += rstride) {
-                const size_t ib = (size_t)row * B + b;
-                const T xi = x[ib] - mean;
-                x[ib] = xi;
-                const int bp = (int)((unsigned)node[row] >> 16);
-                if (bp) A.V.ub1[(size_t)(bp - 1) * B + b] = xi;
+    block_reduce_cols<1, VEC>(pv, scratch, out, C, G, RB);
+    if (!SINGLE) {
+        if (tid < C) part_pq[((size_t)blockIdx.x * C + tid) * 4 + 1] = out[tid];
+        if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
+        cross_reduce_cols<1, VEC>(part_pq, 1, gridDim.x, C, G, RB, scratch, out);
+    }
+    if (tid < C) s_ab[tid] = out[tid] / A.M.vsum;
+    __syncthreads();
+    if (any_act)
+        for (int row = row0; row < N; row += rstride) {
+            const size_t ib = (size_t)row * C + c0;
+            const int bp = (int)((unsigned)node[row] >> 16);
+            const int e0 = rowptr[row], e1 = rowptr[row + 1];
+            T xv[VEC];
+            vload<T, VEC, false>(xv, &x[ib]);
+            bool need_kw = false;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                if (neu[k]) {
+                    xv[k] -= T(s_ab[c0 + k]);
+                    if (mode == 0 && bp) A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] = xv[k];
+                } else if (mode == 0 && bp) {
+                    need_kw = true;
+                }
+            }
+            vstore<T, VEC>(&x[ib], xv);
+            if (need_kw) {
+                T kw[VEC];
+                row_kv<T, VEC, CG, false>(col, pkA, e0, e1, x, C, c0, xv, kw);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k)
+                    if (!neu[k] && actk[k])
+                        A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] =
+                            T(rhs_b(col, pkA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k])) - kw[k];
             }
         }
-    }
 }
 
-size_t pcg_part_elems(int num_sms, int B) { return (size_t)2 * num_sms * B * 4; }
+size_t pcg_part_elems(int num_sms, int B) { return (size_t)2 * num_sms * (2 * B) * 4; }
+
+template <typename T, bool SINGLE, int VEC>
+static cudaError_t launch_pcg(const Launch& L, const MeshView& M, PcgArgs<T>& a, int C) {
+    const int bd = SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS;
+    const int G = C / VEC, RB = bd / G;
+    const int nrow_red = (G <= 32 && (32 % G) == 0) ? (bd >> 5) : RB;
+    const size_t smem = sizeof(double) * (4 * (size_t)nrow_red * C + 8 * (size_t)C) + sizeof(int) * 4 * C;
+    static bool attr_set = false;
+    static int occ = 0;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_pcg<T, SINGLE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (!SINGLE) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, SINGLE, VEC>, bd, 200 * 1024);
+            if (occ < 1) occ = 1;
+            if (occ > 1) occ = 1;   // the partials buffer holds one block per SM
+        }
+        attr_set = true;
+    }
+    void* args[] = {&a};
+    if (SINGLE) return cudaLaunchKernel((void*)k_pcg<T, SINGLE, VEC>, dim3(1), dim3(bd), args, smem, L.stream);
+    int nblk = (M.N + RB - 1) / RB;
+    const int maxblk = occ * L.num_sms;
+    if (nblk > maxblk) nblk = maxblk;
+    cudaMemsetAsync(L.bar, 0, sizeof(unsigned), L.stream);
+    return cudaLaunchCooperativeKernel((void*)k_pcg<T, SINGLE, VEC>, dim3(nblk), dim3(bd), args, smem, L.stream);
+}
 
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
               int* iters_dev) {
     (void)iters_dev;
-    const int B = V.B;
+    const int C = 2 * V.B;
     PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps};
-    void* args[] = {&a};
+    const bool single = (long long)M.N * C <= SINGLE_CTA_MAX_WORK;
+    const bool vec4 = (sizeof(T) == 4) && (C % 4 == 0);
     cudaError_t e;
-    if ((long long)M.N * B <= SINGLE_CTA_MAX_WORK) {
-        const size_t smem = sizeof(double) * (4 * PCG_SINGLE_THREADS + 8 * B) + sizeof(int) * 4 * B;
-        static bool attr_set[2] = {false, false};
-        if (!attr_set[sizeof(T) == 8]) {
-            cudaFuncSetAttribute(k_pcg<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-            attr_set[sizeof(T) == 8] = true;
-        }
-        e = cudaLaunchKernel((void*)k_pcg<T, true>, dim3(1), dim3(PCG_SINGLE_THREADS), args, smem, L.stream);
-    } else {
-        const int RB = PCG_THREADS / B;
-        const size_t smem = sizeof(double) * (4 * PCG_THREADS + 8 * B) + sizeof(int) * 4 * B;
-        static int occ_cache[2] = {0, 0};
-        int& occ = occ_cache[sizeof(T) == 8];
-        if (!occ) {
-            cudaFuncSetAttribute(k_pcg<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, false>, PCG_THREADS, 64 * 1024);
-            if (occ < 1) occ = 1;
-            if (occ > 1) occ = 1;
-        }
-        int nblk = (M.N + RB - 1) / RB;
-        const int maxblk = occ * L.num_sms;
-        if (nblk > maxblk) nblk = maxblk;
-        cudaMemsetAsync(L.bar, 0, sizeof(unsigned), L.stream);
-        e = cudaLaunchCooperativeKernel((void*)k_pcg<T, false>, dim3(nblk), dim3(PCG_THREADS), args, smem, L.stream);
-    }
+    if (single) e = vec4 ? launch_pcg<T, true, (sizeof(T) == 4 ? 4 : 2)>(L, M, a, C) : launch_pcg<T, true, 2>(L, M, a, C);
+    else e = vec4 ? launch_pcg<T, false, (sizeof(T) == 4 ? 4 : 2)>(L, M, a, C) : launch_pcg<T, false, 2>(L, M, a, C);
     *L.launches += 1;
     return e == cudaSuccess ? 0 : (int)e;
 }
 
-// ---- BEM product -------------------------------------------------------------------
+// ---- BEM products: forward u2_S = B u1_S, adjoint c_S = B^T t_S ------------------------
+// Columns 0..B-1 of the [nb][2B] surface arrays belong to the forward chain,
+// columns B..2B-1 to the adjoint chain.
+
+// y[row*inc] = sum_j A[row][j] x[j*inc]; one warp per row
 template <typename T>
-__global__ void k_gemv(const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y, int nb) {
+__global__ void k_gemv(const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y, int nb, int inc) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int row = warp; row < nb; row += nw) {
         const T* a = A + (size_t)row * nb;
         double acc = 0.0;
-        for (int j = lane; j < nb; j += 32) acc += (double)(a[j] * x[j]);
+        for (int j = lane; j < nb; j += 32) acc += (double)a[j] * (double)x[(size_t)j * inc];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) y[row] = T(acc);
+        if (lane == 0) y[(size_t)row * inc] = T(acc);
     }
 }
 
-// Y[nb][B] = A[nb][nb] X[nb][B]; 64x64 tiles, 256 threads, 4x4 outputs each.
+// part[s][j] = sum_{i in chunk s} A[i][j] x[i*inc]: column-parallel, coalesced rows
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(const T* __restrict__ A, const T* __restrict__ X, T* __restrict__ Y,
-                                              int nb, int B) {
+__global__ void k_gemv_t_part(const T* __restrict__ A, const T* __restrict__ x, double* __restrict__ part, int nb,
+                              int inc, int rows_per_chunk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = blockIdx.y * rows_per_chunk, i1 = min(nb, i0 + rows_per_chunk);
+    if (j >= nb) return;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) acc += (double)A[(size_t)i * nb + j] * (double)x[(size_t)i * inc];
+    part[(size_t)blockIdx.y * nb + j] = acc;
+}
+
+template <typename T>
+__global__ void k_sum_parts(const double* __restrict__ part, int S, int nb, T* __restrict__ y, int inc) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb) return;
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) acc += part[(size_t)s * nb + j];
+    y[(size_t)j * inc] = T(acc);
+}
+
+// Y[:, 0:ncols] = op(A) X[:, 0:ncols] with row strides ldx, ldy; 64x64 tiles,
+// 256 threads, 4x4 outputs each.  TRANS: op(A) = A^T.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_gemm(const T* __restrict__ A, const T* __restrict__ X, int ldx,
+                                              T* __restrict__ Y, int ldy, int nb, int ncols) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ T As[BK][BM + 4];
     __shared__ T Xs[BK][BN + 4];
@@ -462,14 +669,17 @@ __global__ void __launch_bounds__(256) k_gemm(const T* __restrict__ A, const T* 
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     for (int k0 = 0; k0 < nb; k0 += BK) {
         for (int l = tid; l < BM * BK; l += 256) {
-            const int mm = l / BK, kk = l % BK;
+            int mm, kk;
+            if (TRANS) { kk = l / BM; mm = l % BM; } else { mm = l / BK; kk = l % BK; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < nb && gk < nb) ? A[(size_t)gm * nb + gk] : T(0);
+            T v = T(0);
+            if (gm < nb && gk < nb) v = TRANS ? A[(size_t)gk * nb + gm] : A[(size_t)gm * nb + gk];
+            As[kk][mm] = v;
         }
         for (int l = tid; l < BK * BN; l += 256) {
             const int kk = l / BN, nn = l % BN;
             const int gk = k0 + kk, gn = n0 + nn;
-            Xs[kk][nn] = (gk < nb && gn < B) ? X[(size_t)gk * B + gn] : T(0);
+            Xs[kk][nn] = (gk < nb && gn < ncols) ? X[(size_t)gk * ldx + gn] : T(0);
         }
         __syncthreads();
 #pragma unroll
@@ -485,7 +695,7 @@ __global__ void __launch_bounds__(256) k_gemm(const T* __restrict__ A, const T* 
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
             const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
-            if (gm < nb && gn < B) Y[(size_t)gm * B + gn] = acc[i][j];
+            if (gm < nb && gn < ncols) Y[(size_t)gm * ldy + gn] = acc[i][j];
         }
 }
 
@@ -493,19 +703,34 @@ template <typename T> __host__ __device__ inline const T* bem_ptr(const MeshView
 template <> __host__ __device__ inline const double* bem_ptr<double>(const MeshView& M) { return M.B64; }
 template <> __host__ __device__ inline const float* bem_ptr<float>(const MeshView& M) { return M.B32; }
 
+int bem_chunks(int nb, int num_sms) {
+    const int colblocks = (nb + 255) / 256;
+    int S = (2 * num_sms + colblocks - 1) / colblocks;
+    if (S > 32) S = 32;
+    if (S < 1) S = 1;
+    return S;
+}
+
 template <typename T>
 void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V) {
     const T* Bm = bem_ptr<T>(M);
-    if (V.B == 1) {
-        const int warps = M.nb;
-        int blocks = (warps * 32 + 255) / 256;
+    const int B = V.B, C = 2 * B, nb = M.nb;
+    if (B == 1) {
+        int blocks = (nb * 32 + 255) / 256;
         if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
-        k_gemv<T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub1, V.ub2, M.nb);
+        k_gemv<T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub_in, V.ub_out, nb, C);
+        const int S = bem_chunks(nb, L.num_sms);
+        const int rpc = (nb + S - 1) / S;
+        k_gemv_t_part<T><<<dim3((nb + 255) / 256, S), 256, 0, L.stream>>>(Bm, V.ub_in + 1, (double*)V.bem_part, nb,
+                                                                         C, rpc);
+        k_sum_parts<T><<<(nb + 255) / 256, 256, 0, L.stream>>>((const double*)V.bem_part, S, nb, V.ub_out + 1, C);
+        *L.launches += 3;
     } else {
-        dim3 grid((M.nb + 63) / 64, (V.B + 63) / 64);
-        k_gemm<T><<<grid, 256, 0, L.stream>>>(Bm, V.ub1, V.ub2, M.nb, V.B);
+        dim3 grid((nb + 63) / 64, (B + 63) / 64);
+        k_gemm<T, false><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in, C, V.ub_out, C, nb, B);
+        k_gemm<T, true><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in + B, C, V.ub_out + B, C, nb, B);
+        *L.launches += 2;
     }
-    *L.launches += 1;
 }
 
 // ---- effective field, gradient, energies and step dot products -----------------------
@@ -535,8 +760,8 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
         const InstConst ic = V.ic[b];
         const double* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
         const double* mb = V.m + (size_t)cur * N * 3 * B;
-        double* Ht = V.H + (size_t)(1 - cur) * N * 3 * B;
-        const double* Hb = V.H + (size_t)cur * N * 3 * B;
+        double* Gt = V.H + (size_t)(1 - cur) * N * 3 * B;        // grad phi at the trial point
+        const double* Gb = V.H + (size_t)cur * N * 3 * B;   // grad phi at the base point
         for (int row = blockIdx.x * RB + rl; row < N; row += gridDim.x * RB) {
             const int nd = M.node[row];
             const double vi = (double)(nd & 0xff);
@@ -553,8 +778,11 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
                 ex1 += k * T(mt[j3 + B] - my);
                 ex2 += k * T(mt[j3 + 2 * B] - mz);
                 if (demag) {
+                    // (forward + adjoint)/2: the potential whose lumped gradient is the
+                    // exact gradient of the stray-field energy
                     const int wb = __ldg(&M.pkB[e]);
-                    const T u = V.u1[(size_t)j * B + b] + V.u2[(size_t)j * B + b];
+                    const size_t jc = (size_t)j * 2 * B + b;
+                    const T u = T(0.5) * (V.U1[jc] + V.U2[jc] + V.U2[jc + B]);
                     hd0 += T(sbyte(wb, 0)) * u;
                     hd1 += T(sbyte(wb, 1)) * u;
                     hd2 += T(sbyte(wb, 2)) * u;
@@ -566,12 +794,13 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
             const double hd[3] = {-(double)hd0 / vi, -(double)hd1 / vi, -(double)hd2 / vi};
             double h[3];
             for (int c = 0; c < 3; ++c) h[c] = -4.0 * ic.lam * kx[c] / vi + ic.Q * ma * ic.a[c] + ic.hz[c] + hd[c];
-            // H = -m x grad phi = (V/12) m x h ;  g = m x H
+            // grad phi = -(V/12) h ;  H = -m x grad phi = (V/12) m x h ;  g = m x H
+            const double gr[3] = {-vi / 12.0 * h[0], -vi / 12.0 * h[1], -vi / 12.0 * h[2]};
             const double mh[3] = {m[1] * h[2] - m[2] * h[1], m[2] * h[0] - m[0] * h[2], m[0] * h[1] - m[1] * h[0]};
             const double Hv[3] = {vi / 12.0 * mh[0], vi / 12.0 * mh[1], vi / 12.0 * mh[2]};
-            Ht[i3] = Hv[0];
-            Ht[i3 + B] = Hv[1];
-            Ht[i3 + 2 * B] = Hv[2];
+            Gt[i3] = gr[0];
+            Gt[i3 + B] = gr[1];
+            Gt[i3 + 2 * B] = gr[2];
             if (V.hout) {
                 V.hout[i3] = h[0];
                 V.hout[i3 + B] = h[1];
@@ -580,9 +809,13 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
             const double g[3] = {m[1] * Hv[2] - m[2] * Hv[1], m[2] * Hv[0] - m[0] * Hv[2],
                                  m[0] * Hv[1] - m[1] * Hv[0]};
             const double bm[3] = {mb[i3], mb[i3 + B], mb[i3 + 2 * B]};
-            const double bH[3] = {Hb[i3], Hb[i3 + B], Hb[i3 + 2 * B]};
-            const double gb[3] = {bm[1] * bH[2] - bm[2] * bH[1], bm[2] * bH[0] - bm[0] * bH[2],
-                                  bm[0] * bH[1] - bm[1] * bH[0]};
+            const double bg[3] = {Gb[i3], Gb[i3 + B], Gb[i3 + 2 * B]};
+            // g_b = m_b x (-m_b x grad_b) = grad_b - (m_b . grad_b) m_b  (|m_b| = 1)
+            const double bmg = bm[0] * bg[0] + bm[1] * bg[1] + bm[2] * bg[2];
+            const double gb[3] = {bg[0] - bmg * bm[0], bg[1] - bmg * bm[1], bg[2] - bmg * bm[2]};
+            // E is quadratic in m, so E_t - E_b = (grad_t + grad_b) . (m_t - m_b) / 2 exactly
+            acc[Q_DE] += 0.5 * ((gr[0] + bg[0]) * (m[0] - bm[0]) + (gr[1] + bg[1]) * (m[1] - bm[1]) +
+                                (gr[2] + bg[2]) * (m[2] - bm[2]));
             const double mxa[3] = {m[1] * ic.a[2] - m[2] * ic.a[1], m[2] * ic.a[0] - m[0] * ic.a[2],
                                    m[0] * ic.a[1] - m[1] * ic.a[0]};
             acc[Q_EEX] += ic.lam / 6.0 * (m[0] * kx[0] + m[1] * kx[1] + m[2] * kx[2]);
@@ -657,9 +890,13 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     if (lane != 0) return;
     InstState& s = st[b];
     if (s.phase == PH_DONE) return;
-    const double E = ((v[Q_EEX] + v[Q_EAN]) + v[Q_EZ]) + v[Q_ED];
+    const double Edirect = ((v[Q_EEX] + v[Q_EAN]) + v[Q_EZ]) + v[Q_ED];
+    // Decisions use E(base) + (E(trial) - E(base)) with the difference from the
+    // gradients (exact for the quadratic energy): its rounding scales with the
+    // step, not with |E|, so tiny decreases near the minimum stay resolvable.
+    const double E = s.phase == PH_INIT ? Edirect : s.Eacc + v[Q_DE];
     s.evals += 1;
-    if (v[Q_BAD] > 0.0 || !isfinite(E)) {
+    if (v[Q_BAD] > 0.0 || !isfinite(E) || !isfinite(Edirect)) {
         s.status = 4;   // LBM_E_NAN
         s.phase = PH_DONE;
         return;
@@ -694,7 +931,8 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     // accepted: the trial becomes the base point
     const bool init = s.phase == PH_INIT;
     s.cur ^= 1;
-    s.E = E;
+    s.E = Edirect;
+    s.Eacc = E;
     s.terms[0] = v[Q_EEX];
     s.terms[1] = v[Q_EAN];
     s.terms[2] = v[Q_EZ];
@@ -730,7 +968,7 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     if (conv) { s.status = 0; s.phase = PH_DONE; return; }
     if (s.iters >= so.max_iter) { s.status = 3; s.phase = PH_DONE; return; }
     const double ss = v[Q_SS], sy = v[Q_SY], yy = v[Q_YY];
-    double tau = s.tau;
+    double tau = 1.0 / v[Q_HMAX];   // s.y <= 0: restart with the first-step trial
     if (sy > 0.0) {
         const double t1 = ss / sy, t2 = sy / yy;
         const int ma = so.m_alpha < MALPHA_MAX ? so.m_alpha : MALPHA_MAX;
@@ -784,10 +1022,12 @@ __global__ void k_trial(int N, BatchView<T> V) {
             continue;
         }
         // x = [(1 - |w|^2) m - 2 m x w + 2 (m.w) w] / (1 + |w|^2),  w = tau H / 2
-        const double* Hb = V.H + (size_t)cur * N * 3 * B;
+        const double* Gb = V.H + (size_t)cur * N * 3 * B;   // grad phi at the base point
         const double ht = 0.5 * V.st[b].tau;
         const double m0 = mb[i3], m1 = mb[i3 + B], m2 = mb[i3 + 2 * B];
-        const double w0 = ht * Hb[i3], w1 = ht * Hb[i3 + B], w2 = ht * Hb[i3 + 2 * B];
+        const double g0 = Gb[i3], g1 = Gb[i3 + B], g2 = Gb[i3 + 2 * B];
+        // w = (tau/2) H with H = -m x grad phi
+        const double w0 = -ht * (m1 * g2 - m2 * g1), w1 = -ht * (m2 * g0 - m0 * g2), w2 = -ht * (m0 * g1 - m1 * g0);
         const double ww = w0 * w0 + w1 * w1 + w2 * w2;
         const double mw = m0 * w0 + m1 * w1 + m2 * w2;
         const double c0 = m1 * w2 - m2 * w1, c1 = m2 * w0 - m0 * w2, c2 = m0 * w1 - m1 * w0;
@@ -863,8 +1103,8 @@ __global__ void k_unpack_field(int N, BatchView<T> V, double* __restrict__ h, do
         if (h)
             for (int c = 0; c < 3; ++c) h[((size_t)b * N + i) * 3 + c] = Js * V.hout[(i * 3 + c) * B + b];
         if (u) {
-            u[((size_t)b * 2 + 0) * N + i] = cell * (double)V.u1[t];
-            u[((size_t)b * 2 + 1) * N + i] = cell * (double)V.u2[t];
+            u[((size_t)b * 2 + 0) * N + i] = cell * (double)V.U1[i * 2 * B + b];
+            u[((size_t)b * 2 + 1) * N + i] = cell * (double)V.U2[i * 2 * B + b];
         }
     }
 }
