@@ -23,6 +23,9 @@ import sys
 import threading
 import time
 
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")          # the CPU oracle legs run on one core
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -110,7 +113,7 @@ def dist_init(args):
     return ws, rank, local
 
 
-def cpu_oracle_sample(insts, evals_per_solve, budget_s):
+def cpu_oracle_sample(insts, evals_per_solve_gpu, budget_s):
     """Time the FP64 oracle on one instance of the workload: field evaluations
     and steps for about `budget_s` seconds (set-up -- assembly, BEM, LU -- is
     excluded, as in the paper's CPU timings), scaled to solves/s with the
@@ -131,13 +134,18 @@ def cpu_oracle_sample(insts, evals_per_solve, budget_s):
             m = inst.m0
     dt = time.perf_counter() - t0
     per_eval = dt / max(done_evals, 1)
-    threads = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS") or "1"
-    return {"value": 1.0 / (per_eval * evals_per_solve), "unit": "solves/s", "cores": int(threads),
+    try:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "batched_n30.json")))
+        evals_per_solve = float(np.mean([r["evaluations"] for r in gold["results"]]))
+        src = "the oracle's own mean over the 64 instances"
+    except Exception:
+        evals_per_solve, src = evals_per_solve_gpu, "the GPU run"
+    return {"value": 1.0 / (per_eval * evals_per_solve), "unit": "solves/s", "cores": 1,
             "kind": "oracle",
-            "sample": (f"FP64 numpy/scipy oracle, one instance of the {N_CELLS}^3-cell workload: "
-                       f"{done_evals} energy-gradient evaluations in {dt:.1f} s "
+            "sample": (f"FP64 numpy/scipy oracle (one thread), instance 0 of the {N_CELLS}^3-cell "
+                       f"workload: {done_evals} energy-gradient evaluations in {dt:.1f} s "
                        f"({per_eval * 1e3:.1f} ms each, set-up excluded), scaled by "
-                       f"{evals_per_solve:.0f} evaluations per solve measured on the GPU")}
+                       f"{evals_per_solve:.0f} evaluations per solve ({src})")}
 
 
 def run_reference(args, ws, rank):
@@ -164,8 +172,10 @@ def run_reference(args, ws, rank):
         if s >= args.warmup:
             vals.append(dt / ev)
             total_evals += ev
-    # evaluations per solve of this workload (GPU-measured, FP64 path, mean over the batch)
-    evals_per_solve = float(os.environ.get("LBM_EVALS_PER_SOLVE", "600"))
+    # evaluations per solve of this workload: the oracle's own mean over the 64
+    # instances (tests/golden/batched_n30.json, written by the oracle)
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "batched_n30.json")))
+    evals_per_solve = float(np.mean([r["evaluations"] for r in gold["results"]]))
     per_eval = float(np.mean(vals))
     value = 1.0 / (per_eval * evals_per_solve)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
@@ -216,6 +226,7 @@ def run_ours(args, ws, rank, local):
         inst.set_m_device(m0_dev.data_ptr())
         return inst.minimise(opts)
 
+    res = []
     for _ in range(args.warmup):
         res = step()
     bad = [r["status"] for r in res if r["status"] != 0]
@@ -239,6 +250,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         evals.extend(r["evaluations"] for r in res)
+        bad.extend(r["status"] for r in res if r["status"] != 0)
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read(reset=True)
     ctx.profile_enable(False)
@@ -264,21 +276,37 @@ def run_ours(args, ws, rank, local):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the potential solves)
-    tsize = 8 if prec == lbm.LBM_FP64 else 4
-    pcg_ms = prof["pcg_neumann"]["ms"] + prof["pcg_dirichlet"]["ms"]
-    pcg_launches = prof["pcg_neumann"]["launches"] + prof["pcg_dirichlet"]["launches"]
-    it_total = prof["cg_iters"][0] + prof["cg_iters"][1]
-    pcg_bytes = it_total * pcg_bytes_per_instance_iter(N, tsize)
-    achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
+    # roofline of the dominant kernel: the potential solves (k_pcg).  Algorithmic
+    # bytes per system-iteration and row: z gather, p rw, q rw (phase A), x rw,
+    # r rw, p, q read, z write (phase B) = 12 vector words; the int8 matrix and
+    # the row tables are shared by all 2B systems and not counted.
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     kinds = {k: v for k, v in prof.items() if k not in ("cg_iters", "cg_sweeps")}
     total_kernel_ms = sum(v["ms"] for v in kinds.values())
+    pcg = {}
+    for name, idx, word in (("fp32", 0, 4), ("fp64", 1, 8)):
+        ms = kinds[f"pcg1_{name}"]["ms"] + kinds[f"pcg2_{name}"]["ms"]
+        nl = kinds[f"pcg1_{name}"]["launches"] + kinds[f"pcg2_{name}"]["launches"]
+        by = prof["cg_iters"][idx] * 12 * word * N
+        pcg[name] = dict(ms=ms, launches=nl, bytes=by)
+    dom = max(pcg, key=lambda k: pcg[k]["ms"])
+    d = pcg[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": f"k_pcg ({dom} potential solves, forward + adjoint)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                "avg_launch_ms": d["ms"] / max(d["launches"], 1),
+                "share_of_kernel_time": d["ms"] / total_kernel_ms if total_kernel_ms else None,
+                "other": {k: {"ms": round(v["ms"], 2), "GB_s": (v["bytes"] / (v["ms"] / 1e3) / 1e9
+                                                                 if v["ms"] > 0 else None)}
+                          for k, v in pcg.items()}}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(insts, statistics.mean(evals), args.cpu_sample_s)
@@ -287,8 +315,8 @@ def run_ours(args, ws, rank, local):
     if args.fp64_sample > 0 and prec != lbm.LBM_FP64:
         single = ctx.instance_create(mesh, 1, lbm.LBM_FP64)
         o64 = lbm.default_opts(lbm.LBM_FP64)
-        t_fp64 = []
-        e_err = []
+        t_fp64, e_err = [], []
+        Kd = JS_T ** 2 / (2 * 4e-7 * math.pi)
         for b in range(args.fp64_sample):
             single.set_material(JS_T, A_JM, K1_JM3, axes[b])
             single.set_field(fields[b])
@@ -298,11 +326,12 @@ def run_ours(args, ws, rank, local):
             r64 = single.minimise(o64)[0]
             t_fp64.append(time.perf_counter() - t0)
             Eref = r64["energy"][4]
-            Kd = JS_T ** 2 / (2 * 4e-7 * math.pi)
             scale = max(abs(Eref), Kd * (N_CELLS * 2e-9) ** 3)
             e_err.append(abs(final_res[b]["energy"][4] - Eref) / scale)
         fp64_arm = {"solves_per_s": 1.0 / statistics.mean(t_fp64), "instances_timed": args.fp64_sample,
-                    "max_rel_energy_err_batched_vs_fp64": max(e_err)}
+                    "ms_per_solve": 1e3 * statistics.mean(t_fp64),
+                    "speedup_of_batched_mixed": value / (1.0 / statistics.mean(t_fp64)),
+                    "max_rel_energy_err_batched_mixed_vs_fp64": max(e_err)}
         single.destroy()
 
     line = {
@@ -320,12 +349,7 @@ def run_ours(args, ws, rank, local):
         "evaluations_per_solve": statistics.mean(evals),
         "gpu_launches": launches,
         "clocks": clocks,
-        "roofline": {"bound": "hbm", "kernel": "k_pcg (potential solves)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,
-                     "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                     "bytes_per_launch": pcg_bytes / max(pcg_launches, 1),
-                     "avg_launch_ms": pcg_ms / max(pcg_launches, 1),
-                     "share_of_kernel_time": pcg_ms / total_kernel_ms if total_kernel_ms else None},
+        "roofline": roofline,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()},
         "cpu_baseline": cpu,
         "fp64_single_instance": fp64_arm,

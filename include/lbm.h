@@ -41,9 +41,11 @@ extern "C" {
 
 /* ---- precision modes ---------------------------------------------------------- */
 #define LBM_FP64      0  /* every vector, field and reduction in FP64 */
-#define LBM_MIXED     1  /* FP32 node vectors, SpMV, potential solves and BEM
-                            product; FP64 reductions (dots, energy, stop test,
-                            CG residual norms) */
+#define LBM_MIXED     1  /* FP64 state m; FP32 potential solves and BEM
+                            product until max|m x h|/Js < switch_tol, then an
+                            FP64 phase (FP32 BEM matrix, FP64 solves) to tol;
+                            FP64 reductions (dots, energy differences, stop
+                            test, CG residual norms) throughout */
 #define LBM_MIXED_TC  2  /* as LBM_MIXED, BEM product on the tensor cores
                             (3xTF32 split, FP32 accumulation) when batch > 1 */
 
@@ -99,7 +101,7 @@ typedef struct {
 
 /* Fill `o` with the defaults for `precision` (tol 1e-6, memory 20, c1 1e-4,
  * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-6 mixed,
- * switch_tol 1e-4, cg_tol_polish 1e-13). */
+ * switch_tol 1e-4, cg_tol_polish 1e-10). */
 void lbm_default_opts(lbm_solve_opts* o, int32_t precision);
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t
@@ -175,15 +177,18 @@ int lbm_launch_count(lbm_ctx* ctx, int64_t* count);
 
 /* Per-kind device time of the minimiser's kernels, measured with CUDA events
  * recorded on the context's stream around every launch while enabled.
- * Kinds: 0 trial update (Eq. 8), 1 Neumann potential solve, 2 BEM product,
- * 3 Dirichlet potential solve, 4 field/energy/dot products, 5 step decision. */
+ * Kinds: 0 trial update (Eq. 8), 1 potential solves stage 1 (FP32),
+ * 2 BEM products, 3 potential solves stage 2 (FP32), 4 field/energy/dot
+ * products, 5 step decision, 6 and 7 stages 1 and 2 in FP64. */
 #define LBM_PROF_KINDS 8
 typedef struct {
     int64_t launches[LBM_PROF_KINDS];
     double  ms[LBM_PROF_KINDS];
-    int64_t cg_iters[2];       /* potential-solve iterations summed over instances */
-    int64_t cg_sweeps[2];      /* potential-solve iterations of the whole batch (each
-                                  sweep advances every unconverged instance) */
+    int64_t cg_iters[2];       /* potential-solve iterations summed over all systems
+                                  (forward and adjoint of every instance): FP32, FP64 */
+    int64_t cg_sweeps[4];      /* potential-solve iterations of the whole batch (each
+                                  sweep advances every unconverged system): stage 1
+                                  FP32, stage 2 FP32, stage 1 FP64, stage 2 FP64 */
 } lbm_profile_stats;
 int lbm_profile_enable(lbm_ctx* ctx, int32_t on);
 int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);

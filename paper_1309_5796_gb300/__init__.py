@@ -39,10 +39,11 @@ class SolveOpts(C.Structure):
 
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8), ("cg_iters", C.c_int64 * 2),
-                ("cg_sweeps", C.c_int64 * 2)]
+                ("cg_sweeps", C.c_int64 * 4)]
 
 
-PROFILE_KINDS = ("trial_update", "pcg_neumann", "bem_product", "pcg_dirichlet", "field", "decide")
+PROFILE_KINDS = ("trial_update", "pcg1_fp32", "bem_product", "pcg2_fp32", "field", "decide",
+                 "pcg1_fp64", "pcg2_fp64")
 
 
 class Result(C.Structure):
@@ -214,7 +215,7 @@ class Context:
         out = {k: dict(launches=int(s.launches[i]), ms=float(s.ms[i]))
                for i, k in enumerate(PROFILE_KINDS)}
         out["cg_iters"] = [int(s.cg_iters[0]), int(s.cg_iters[1])]
-        out["cg_sweeps"] = [int(s.cg_sweeps[0]), int(s.cg_sweeps[1])]
+        out["cg_sweeps"] = [int(s.cg_sweeps[k]) for k in range(4)]
         return out
 
 

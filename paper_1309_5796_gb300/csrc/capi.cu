@@ -47,6 +47,8 @@ struct Mesh {
     double cell = 0;
     int *rowptr = nullptr, *col = nullptr, *pkA = nullptr, *pkB = nullptr, *node = nullptr, *bidx = nullptr;
     int *tris = nullptr, *inc_ptr = nullptr, *inc_slot = nullptr;
+    int *kptr = nullptr, *kent = nullptr;
+    int nnzK = 0;
     double* B64 = nullptr;
     float* B32 = nullptr;
     size_t bytes = 0;
@@ -54,6 +56,7 @@ struct Mesh {
         MeshView v;
         v.n = n; v.N = N; v.nb = nb; v.nnz = nnz; v.F = F;
         v.rowptr = rowptr; v.col = col; v.pkA = pkA; v.pkB = pkB; v.node = node; v.bidx = bidx;
+        v.kptr = kptr; v.kent = kent;
         v.B64 = B64; v.B32 = B32;
         v.vsum = 24.0 * (double)n * n * n;
         v.cell = cell;
@@ -71,6 +74,7 @@ struct Inst {
     double* staged = nullptr;      // B*N*3 doubles (host <-> device layout conversion)
     double* staged_u = nullptr;    // B*2*N doubles
     Inst* polish = nullptr;        // FP64 shadow batch finishing mixed-precision runs
+    bool bem32 = false;            // BEM product with the FP32 matrix (FP64 phase of mixed runs)
     std::vector<lbm_material> mats;
     std::vector<double> h;         // B*3 tesla
     size_t bytes = 0;
@@ -100,8 +104,9 @@ struct lbm_ctx {
     int64_t next_id = 1;
     std::map<int64_t, Mesh*> meshes;
     std::map<int64_t, Inst*> insts;
-    unsigned long long* sweeps = nullptr;   // device [2]
-    Launch launch() { return Launch{stream, num_sms, bar, err, &launches, sweeps}; }
+    unsigned long long* sweeps = nullptr;   // device [4]
+    double* fin = nullptr;                  // device [4096] grid-reduction results
+    Launch launch() { return Launch{stream, num_sms, bar, err, &launches, sweeps, fin}; }
 };
 
 namespace {
@@ -224,7 +229,7 @@ Inst* get_inst(lbm_ctx* ctx, lbm_inst h) {
 
 void free_mesh(Mesh* m) {
     void* ptrs[] = {m->rowptr, m->col, m->pkA, m->pkB, m->node, m->bidx, m->tris, m->inc_ptr, m->inc_slot,
-                    m->B64, m->B32};
+                    m->kptr, m->kent, m->B64, m->B32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -287,22 +292,23 @@ int check_opts(const lbm_solve_opts& o) {
 
 // One field evaluation of every active instance at its trial point.
 template <typename T>
-int eval_trial(lbm_ctx* ctx, const Mesh& M, const BatchView<T>& V, const lbm_solve_opts& o) {
+int eval_trial(lbm_ctx* ctx, const Mesh& M, const Inst& I, const BatchView<T>& V, const lbm_solve_opts& o) {
     Launch L = ctx->launch();
     MeshView mv = M.view();
     if (o.demag) {
         int e;
+        const int k64 = sizeof(T) == 8 ? 5 : 0;
         {
-            ProfScope ps(ctx, 1);
+            ProfScope ps(ctx, 1 + k64);
             e = pcg_solve<T>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, nullptr);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
         {
             ProfScope ps(ctx, 2);
-            bem_product<T>(L, mv, V);
+            bem_product<T>(L, mv, V, I.bem32);
         }
         {
-            ProfScope ps(ctx, 3);
+            ProfScope ps(ctx, 3 + (k64 ? 4 : 0));
             e = pcg_solve<T>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, nullptr);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
@@ -353,7 +359,7 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
                 ProfScope ps(ctx, 0);
                 trial_update<T>(L, mv, V);
             }
-            int e = eval_trial<T>(ctx, M, V, oo);
+            int e = eval_trial<T>(ctx, M, *I, V, oo);
             if (e) return e;
             ProfScope ps(ctx, 5);
             decide<T>(L, mv, V, so, nblk_field);
@@ -393,10 +399,7 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
         }
     }
     if (ctx->prof)
-        for (int b = 0; b < I->B; ++b) {
-            ctx->prof_cg[0] += hs[b].cg1;
-            ctx->prof_cg[1] += hs[b].cg2;
-        }
+        for (int b = 0; b < I->B; ++b) ctx->prof_cg[sizeof(T) == 8 ? 1 : 0] += hs[b].cg1 + hs[b].cg2;
     if (states_out) *states_out = hs;
     (void)rc;
     return LBM_OK;
@@ -429,6 +432,7 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
             P->B = I->B;
             P->precision = LBM_FP64;
             P->tsize = 8;
+            P->bem32 = true;
             const size_t vb = vec_bytes(M, I->B, 8), pe = part_elems(ctx, I->B);
             if (cudaMalloc(&P->vec, vb) != cudaSuccess || cudaMalloc(&P->part, pe * sizeof(double)) != cudaSuccess ||
                 cudaMalloc(&P->st, sizeof(InstState) * B) != cudaSuccess ||
@@ -503,7 +507,7 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->demag = 1;
     o->check_every = 16;
     o->switch_tol = 1e-4;
-    o->cg_tol_polish = 1e-13;
+    o->cg_tol_polish = 1e-10;
     if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
@@ -538,7 +542,7 @@ int lbm_create(lbm_ctx** out, int32_t device, void* stream) {
     }
     cudaMemset(c->bar, 0, 64);
     cudaMemset(c->err, 0, 64);
-    if (cudaMalloc(&c->sweeps, 64) != cudaSuccess) {
+    if (cudaMalloc(&c->sweeps, 64) != cudaSuccess || cudaMalloc(&c->fin, sizeof(double) * 4096) != cudaSuccess) {
         delete c;
         return fail(LBM_E_OOM, "context allocation failed");
     }
@@ -558,6 +562,7 @@ int lbm_destroy(lbm_ctx* ctx) {
     cudaFree(ctx->bar);
     cudaFree(ctx->err);
     cudaFree(ctx->sweeps);
+    cudaFree(ctx->fin);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LBM_OK;
@@ -615,7 +620,15 @@ int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
     CKM(cudaMalloc(&M->bidx, sizeof(int) * M->nb));
     launch_assemble(n, M->rowptr, bpos, M->col, M->pkA, M->pkB, M->node, st);
     launch_boundary_ids(N, bflag, bpos, M->bidx, st);
-    ctx->launches += 2;
+    CKM(cudaMalloc(&M->kptr, sizeof(int) * (N + 1)));
+    launch_kcsr_count(N, M->rowptr, M->pkA, cnt, st);
+    launch_scan(cnt, M->kptr, N, st);
+    CKM(cudaMemcpyAsync(&tot[0], M->kptr + N, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKM(cudaStreamSynchronize(st));
+    M->nnzK = tot[0];
+    CKM(cudaMalloc(&M->kent, sizeof(int) * M->nnzK));
+    launch_kcsr_fill(N, M->rowptr, M->col, M->pkA, M->kptr, M->kent, st);
+    ctx->launches += 5;
     std::vector<int> hb(M->nb), tris, incp, incs;
     CKM(cudaMemcpyAsync(hb.data(), M->bidx, sizeof(int) * M->nb, cudaMemcpyDeviceToHost, st));
     CKM(cudaStreamSynchronize(st));
@@ -644,8 +657,8 @@ int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
     cleanup();
     cnt = bflag = bpos = nullptr;
 #undef CKM
-    M->bytes = sizeof(int) * ((size_t)2 * N + 1 + 3 * (size_t)M->nnz + M->nb + tris.size() + incp.size() +
-                              incs.size()) + 12 * nb2;
+    M->bytes = sizeof(int) * ((size_t)3 * N + 2 + 3 * (size_t)M->nnz + M->nnzK + M->nb + tris.size() +
+                              incp.size() + incs.size()) + 12 * nb2;
     const int64_t id = ctx->next_id++;
     ctx->meshes[id] = M;
     *out = id;
@@ -843,10 +856,9 @@ int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset) {
     }
     out->cg_iters[0] = ctx->prof_cg[0];
     out->cg_iters[1] = ctx->prof_cg[1];
-    unsigned long long sw[2];
+    unsigned long long sw[4];
     CK(cudaMemcpy(sw, ctx->sweeps, sizeof sw, cudaMemcpyDeviceToHost));
-    out->cg_sweeps[0] = (int64_t)sw[0];
-    out->cg_sweeps[1] = (int64_t)sw[1];
+    for (int k = 0; k < 4; ++k) out->cg_sweeps[k] = (int64_t)sw[k];
     if (reset) {
         CK(cudaMemsetAsync(ctx->sweeps, 0, sizeof sw, ctx->stream));
         for (int k = 0; k < LBM_PROF_KINDS; ++k) {

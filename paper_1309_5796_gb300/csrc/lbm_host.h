@@ -18,6 +18,9 @@ void launch_scan(const int* in, int* out, int count, cudaStream_t st);
 void launch_assemble(int n, const int* rowptr, const int* bpos, int* col, int* pkA, int* pkB, int* node,
                      cudaStream_t st);
 void launch_boundary_ids(int N, const int* bflag, const int* bpos, int* bidx, cudaStream_t st);
+void launch_kcsr_count(int N, const int* rowptr, const int* pkA, int* cnt, cudaStream_t st);
+void launch_kcsr_fill(int N, const int* rowptr, const int* col, const int* pkA, const int* kptr, int* kent,
+                      cudaStream_t st);
 void launch_tets(int n, int* tets, cudaStream_t st);
 void launch_bem_assemble(int n, int nb, int F, const int* bidx, const int* tris, const int* inc_ptr,
                          const int* inc_slot, double* scratch, int nblocks, double* B64, float* B32,
@@ -31,6 +34,8 @@ struct MeshView {
     const int* pkA;      // nnz; int8 x4 {Kint, Gint_x, Gint_y, Gint_z}
     const int* pkB;      // nnz; int8 x4 {Gint^T_x, Gint^T_y, Gint^T_z, 0}
     const int* node;     // N;   Vint | Kint_ii << 8 | (boundary position + 1) << 16
+    const int* kptr;     // N+1; stiffness-only CSR (nonzero Kint entries)
+    const int* kent;     // nnzK; (column << 8) | (Kint & 0xff)
     const int* bidx;     // nb;  boundary node ids, ascending
     const double* B64;   // nb x nb row-major
     const float* B32;    // nb x nb row-major
@@ -65,14 +70,15 @@ struct Launch {
     unsigned* bar;     // grid-barrier counter (device)
     int* err;          // device error word
     int64_t* launches; // host counter of kernel launches
-    unsigned long long* sweeps;  // device counters [2]: batched PCG iterations (Neumann, Dirichlet)
+    unsigned long long* sweeps;  // device counters [4]: batched PCG iterations per stage and precision
+    double* fin;                 // device scratch for grid reductions (>= 4 * 512 doubles)
 };
 
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
               int* iters_dev);
 template <typename T>
-void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V);
+void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V, bool bem32);
 template <typename T>
 void field_eval(const Launch& L, const MeshView& M, const BatchView<T>& V, int demag);
 template <typename T>

@@ -166,6 +166,27 @@ __global__ void k_assemble(int n, const int* rowptr, const int* bpos, int* col, 
     }
 }
 
+// Stiffness-only CSR for the potential solves: the nonzero Kint entries of each
+// row (7 for an interior Kuhn node, whose face- and body-diagonal couplings
+// vanish), packed as (column << 8) | (Kint & 0xff).
+__global__ void k_kcsr_count(int N, const int* rowptr, const int* pkA, int* cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) c += (pkA[e] & 0xff) != 0;
+        cnt[i] = c;
+    }
+}
+
+__global__ void k_kcsr_fill(int N, const int* rowptr, const int* col, const int* pkA, const int* kptr, int* kent) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int o = kptr[i];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int k = pkA[e] & 0xff;
+            if (k) kent[o++] = (int)(((unsigned)(col[e] & 0x7fffffff) << 8) | (unsigned)k);
+        }
+    }
+}
+
 __global__ void k_boundary_ids(int N, const int* bflag, const int* bpos, int* bidx) {
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
         if (bflag[id]) bidx[bpos[id]] = id;
@@ -354,6 +375,13 @@ void launch_assemble(int n, const int* rowptr, const int* bpos, int* col, int* p
                      cudaStream_t st) {
     const int N = (n + 1) * (n + 1) * (n + 1);
     k_assemble<<<(N + 127) / 128, 128, 0, st>>>(n, rowptr, bpos, col, pkA, pkB, node);
+}
+void launch_kcsr_count(int N, const int* rowptr, const int* pkA, int* cnt, cudaStream_t st) {
+    k_kcsr_count<<<(N + 255) / 256, 256, 0, st>>>(N, rowptr, pkA, cnt);
+}
+void launch_kcsr_fill(int N, const int* rowptr, const int* col, const int* pkA, const int* kptr, int* kent,
+                      cudaStream_t st) {
+    k_kcsr_fill<<<(N + 255) / 256, 256, 0, st>>>(N, rowptr, col, pkA, kptr, kent);
 }
 void launch_boundary_ids(int N, const int* bflag, const int* bpos, int* bidx, cudaStream_t st) {
     k_boundary_ids<<<(N + 255) / 256, 256, 0, st>>>(N, bflag, bpos, bidx);

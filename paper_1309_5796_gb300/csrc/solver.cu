@@ -164,24 +164,30 @@ __device__ __forceinline__ void vstore(T* p, const T (&d)[VEC]) {
     *reinterpret_cast<V*>(p) = x;
 }
 
+constexpr int MAXK = 8;   // stiffness entries served by the unrolled gather (interior Kuhn rows: 7)
+
 // acc[k] = sum_j K_ij (v_j - v_i) (DIFF) or sum_j K_ij v_j for VEC consecutive
-// columns of one CSR row; the row's column indices, then all its vector loads,
-// are issued before any arithmetic so that they are in flight together.
+// columns of one row of the stiffness-only CSR.  The packed entries are read
+// first -- one load per lane and a warp broadcast when the whole warp works on
+// this row (warp_row) -- then every vector gather of the row is issued before
+// any arithmetic.  warp_row requires the full warp to take part.
 template <typename T, int VEC, bool CG, bool DIFF>
-__device__ __forceinline__ void row_kv(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
-                                       const T* v, int C, int c0, const T (&vi)[VEC], T (&acc)[VEC]) {
-    int cj[MAXR], kj[MAXR];
+__device__ __forceinline__ void row_kv(const int* __restrict__ kent, int e0, int e1, const T* v, int C, int c0,
+                                       const T (&vi)[VEC], T (&acc)[VEC], bool warp_row) {
+    int w[MAXK];
+    if (warp_row) {
+        const int lane = threadIdx.x & 31;
+        const int mine = (lane < MAXK && e0 + lane < e1) ? __ldg(&kent[e0 + lane]) : 0;
 #pragma unroll
-    for (int t = 0; t < MAXR; ++t) {
-        const int e = e0 + t;
-        const bool ok = e < e1;
-        cj[t] = ok ? (__ldg(&col[e]) & 0x7fffffff) : -1;
-        kj[t] = ok ? sbyte(__ldg(&pkA[e]), 0) : 0;
+        for (int t = 0; t < MAXK; ++t) w[t] = __shfl_sync(0xffffffffu, mine, t);
+    } else {
+#pragma unroll
+        for (int t = 0; t < MAXK; ++t) w[t] = (e0 + t < e1) ? __ldg(&kent[e0 + t]) : 0;
     }
-    T vj[MAXR][VEC];
+    T vj[MAXK][VEC];
 #pragma unroll
-    for (int t = 0; t < MAXR; ++t) {
-        if (cj[t] >= 0) vload<T, VEC, CG>(vj[t], &v[(size_t)cj[t] * C + c0]);
+    for (int t = 0; t < MAXK; ++t) {
+        if (w[t] != 0) vload<T, VEC, CG>(vj[t], &v[(size_t)((unsigned)w[t] >> 8) * C + c0]);
         else
 #pragma unroll
             for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
@@ -189,14 +195,17 @@ __device__ __forceinline__ void row_kv(const int* __restrict__ col, const int* _
 #pragma unroll
     for (int k = 0; k < VEC; ++k) acc[k] = T(0);
 #pragma unroll
-    for (int t = 0; t < MAXR; ++t)
+    for (int t = 0; t < MAXK; ++t) {
+        const T kk = T(sbyte(w[t], 0));
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] += T(kj[t]) * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
-    for (int e = e0 + MAXR; e < e1; ++e) {
+        for (int k = 0; k < VEC; ++k) acc[k] += kk * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
+    }
+    for (int e = e0 + MAXK; e < e1; ++e) {
+        const int ww = __ldg(&kent[e]);
         T x[VEC];
-        vload<T, VEC, CG>(x, &v[(size_t)(col[e] & 0x7fffffff) * C + c0]);
+        vload<T, VEC, CG>(x, &v[(size_t)((unsigned)ww >> 8) * C + c0]);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] += T(sbyte(pkA[e], 0)) * (DIFF ? (x[k] - vi[k]) : x[k]);
+        for (int k = 0; k < VEC; ++k) acc[k] += T(sbyte(ww, 0)) * (DIFF ? (x[k] - vi[k]) : x[k]);
     }
 }
 
@@ -210,6 +219,7 @@ struct PcgArgs {
     unsigned* bar;
     int* err;
     unsigned long long* sweeps;
+    double* fin;
 };
 
 template <bool SINGLE>
@@ -222,16 +232,42 @@ __device__ __forceinline__ bool pcg_sync(unsigned* bar, unsigned& epoch, int* er
     }
 }
 
+// Grid-wide totals of per-block partials part[blk][C][4] (quantities
+// q0..q0+NQV-1) into out[q*C + c] of every block: after a barrier one warp of
+// the grid sums each (column, quantity) over the blocks (lanes stride the
+// blocks, then a fixed xor tree) into fin; after a second barrier every block
+// copies fin.  Fixed order, so all blocks and all runs get the same bits.
+template <int NQV>
+__device__ __forceinline__ bool grid_reduce(const double* part, int q0, int C, double* fin, double* out,
+                                            unsigned* bar, unsigned& epoch, int* err) {
+    if (!grid_sync(bar, gridDim.x, epoch, err)) return false;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int gw = blockIdx.x * nw + (threadIdx.x >> 5), tw = gridDim.x * nw;
+    const int P = C * NQV;
+    for (int pidx = gw; pidx < P; pidx += tw) {
+        const int c = pidx / NQV, q = pidx % NQV;
+        double acc = 0.0;
+        for (int blk = lane; blk < (int)gridDim.x; blk += 32) acc += __ldcg(&part[((size_t)blk * C + c) * 4 + q0 + q]);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) fin[pidx] = acc;
+    }
+    if (!grid_sync(bar, gridDim.x, epoch, err)) return false;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) out[(t % NQV) * C + t / NQV] = __ldcg(&fin[t]);
+    __syncthreads();
+    return true;
+}
+
 // b_i = (1/4) sum_j Gint_ij . m_j (the divergence right-hand side) at the trial point
+template <typename T>
 __device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
                                         const double* meval, int B, int b) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int e = e0; e < e1; ++e) {
         const int w = __ldg(&pkA[e]);
         const size_t mj = (size_t)(__ldg(&col[e]) & 0x7fffffff) * 3 * B + b;
-        acc += sbyte(w, 1) * meval[mj] + sbyte(w, 2) * meval[mj + B] + sbyte(w, 3) * meval[mj + 2 * B];
+        acc += T(sbyte(w, 1)) * T(meval[mj]) + T(sbyte(w, 2)) * T(meval[mj + B]) + T(sbyte(w, 3)) * T(meval[mj + 2 * B]);
     }
-    return 0.25 * acc;
+    return 0.25 * (double)acc;
 }
 
 // Jacobi-PCG on Kint for the 2B systems of one stage of the forward and adjoint
@@ -258,7 +294,8 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     const bool lane = tid < RB * G;
     const int g = tid % G, rl = tid / G, c0 = g * VEC;
     const int mode = A.mode;
-    // shared memory: reduction scratch, then per-column state
+    // a warp works on one row when the column groups of a row fill whole warps
+    const bool warp_row = (G % 32) == 0;
     const int nrow_red = (G <= 32 && (32 % G) == 0) ? (bd >> 5) : RB;
     double* scratch = sm;                               // [4][nrow_red][C]
     double* out = scratch + 4 * nrow_red * C;           // [4][C]
@@ -280,7 +317,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     }
     __syncthreads();
     const int N = A.M.N;
-    int bk[VEC];            // instance of each owned column
+    int bk[VEC];
     bool neu[VEC], actk[VEC];
     bool any_act = false;
 #pragma unroll
@@ -291,19 +328,35 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
         actk[k] = lane && s_act[c];
         any_act |= actk[k];
     }
+    // row loops are entered by whole warps when warp_row (the gather broadcasts)
+    const bool do_rows = warp_row ? (__any_sync(0xffffffffu, any_act) != 0) : any_act;
     const int row0 = blockIdx.x * RB + rl, rstride = gridDim.x * RB;
     const int* __restrict__ rowptr = A.M.rowptr;
     const int* __restrict__ col = A.M.col;
     const int* __restrict__ pkA = A.M.pkA;
     const int* __restrict__ node = A.M.node;
+    const int* __restrict__ kptr = A.M.kptr;
+    const int* __restrict__ kent = A.M.kent;
     T* __restrict__ x = mode ? A.V.U2 : A.V.U1;
     T* __restrict__ r = A.V.r;
     T* __restrict__ z = A.V.z;
     T* __restrict__ p = A.V.p;
     T* __restrict__ q = A.V.q;
-    double* part_rz = A.V.part;
-    double* part_pq = A.V.part + (size_t)gridDim.x * C * 4;
+    double* part = A.V.part;
     unsigned epoch = 0;
+
+    // partials of this block -> totals in `out` (a grid reduction unless SINGLE)
+    auto reduce = [&](auto& vals, int q0) -> bool {
+        constexpr int NQV = sizeof(vals) / sizeof(vals[0]);
+        block_reduce_cols<NQV, VEC>(vals, scratch, out, C, G, RB);
+        if constexpr (SINGLE) {
+            return true;
+        } else {
+            if (tid < C)
+                for (int k = 0; k < NQV; ++k) part[((size_t)blockIdx.x * C + tid) * 4 + q0 + k] = out[k * C + tid];
+            return grid_reduce<NQV>(part, q0, C, A.fin, out, A.bar, epoch, A.err);
+        }
+    };
 
     // Dirichlet systems: surface values (stage 1 adjoint: zero; stage 2 forward: B u1_S)
     if (any_act)
@@ -320,29 +373,30 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
         double psum[1][VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) psum[0][k] = 0.0;
-        if (any_act)
+        if (do_rows)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 const int bp = (int)((unsigned)nd >> 16);
                 const size_t ib = (size_t)row * C + c0;
-                const int e0 = rowptr[row], e1 = rowptr[row + 1];
                 T xi[VEC], kx[VEC], rv[VEC], zv[VEC];
                 vload<T, VEC, false>(xi, &x[ib]);
-                row_kv<T, VEC, CG, true>(col, pkA, e0, e1, x, C, c0, xi, kx);
+                row_kv<T, VEC, CG, true>(kent, kptr[row], kptr[row + 1], x, C, c0, xi, kx, warp_row);
+                const int e0 = rowptr[row], e1 = rowptr[row + 1];
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     if (!neu[k] && bp) { rv[k] = T(0); zv[k] = T(0); continue; }
                     // f: the right-hand side (b in every system but the stage-2 forward one)
                     double f = 0.0;
-                    if (!(mode == 1 && !neu[k]))
-                        f = rhs_b(col, pkA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k]);
+                    if (!(mode == 1 && !neu[k]) && actk[k])
+                        f = rhs_b<T>(col, pkA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k]);
                     if (mode == 1 && neu[k] && bp) f += (double)A.V.ub_out[(size_t)(bp - 1) * C + c0 + k];
                     double ref = f;   // norm reference: f (Neumann), f - K_IS x_S (Dirichlet)
                     if (!neu[k])
-                        for (int e = e0; e < e1; ++e) {
-                            const int cc = col[e];
-                            if (cc < 0) ref -= (double)sbyte(pkA[e], 0) *
-                                               (double)ld_vec<T, CG>(&x[(size_t)(cc & 0x7fffffff) * C + c0 + k]);
+                        for (int e = kptr[row]; e < kptr[row + 1]; ++e) {
+                            const int ww = kent[e];
+                            const int j = (int)((unsigned)ww >> 8);
+                            if ((unsigned)node[j] >> 16)
+                                ref -= (double)sbyte(ww, 0) * (double)ld_vec<T, CG>(&x[(size_t)j * C + c0 + k]);
                         }
                     rv[k] = T(f) - kx[k];
                     zv[k] = T(ref);                       // kept for the second pass
@@ -355,15 +409,8 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 vstore<T, VEC>(&q[ib], zero);
             }
         // Neumann: consistent right-hand side (sum zero)
-        block_reduce_cols<1, VEC>(psum, scratch, out, C, G, RB);
-        if (SINGLE) {
-            if (tid < C) s_ab[tid] = out[tid] / (double)N;
-        } else {
-            if (tid < C) part_pq[((size_t)blockIdx.x * C + tid) * 4 + 2] = out[tid];
-            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-            cross_reduce_cols<1, VEC>(part_pq, 2, gridDim.x, C, G, RB, scratch, out);
-            if (tid < C) s_ab[tid] = out[tid] / (double)N;
-        }
+        if (!reduce(psum, 2)) return;
+        if (tid < C) s_ab[tid] = out[tid] / (double)N;
         __syncthreads();
         T mean[VEC];
 #pragma unroll
@@ -396,15 +443,10 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 vstore<T, VEC>(&r[ib], rv);
                 vstore<T, VEC>(&z[ib], zv);
             }
-        block_reduce_cols<4, VEC>(v4, scratch, out, C, G, RB);
-        if (!SINGLE) {
-            if (tid < C)
-                for (int k = 0; k < 4; ++k) part_rz[((size_t)blockIdx.x * C + tid) * 4 + k] = out[k * C + tid];
-            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-        }
+        if (!reduce(v4, 0)) return;
     }
     for (int it = 0;; ++it) {
-        if (!SINGLE) cross_reduce_cols<4, VEC>(part_rz, 0, gridDim.x, C, G, RB, scratch, out);
+        // `out` holds the totals of r.z, r.r, (ref.ref), sum r of the last pass
         if (tid < C) {
             const bool nn = (mode == tid / B);
             const double rho = out[tid];
@@ -433,42 +475,42 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
             run |= actk[k] && !s_flag[c0 + k];
             beta[k] = T(s_ab[c0 + k]);
         }
+        const bool run_rows = warp_row ? (__any_sync(0xffffffffu, run) != 0) : run;
         double ppq[1][VEC];
+        T tpq[VEC];   // per-thread partial sums in T; block and grid sums in FP64
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) ppq[0][k] = 0.0;
-        if (run)
+        for (int k = 0; k < VEC; ++k) tpq[k] = T(0);
+        if (run_rows)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 const bool surf = ((unsigned)nd >> 16) != 0;
                 const size_t ib = (size_t)row * C + c0;
                 T zi[VEC], w[VEC], pv[VEC], qv[VEC];
                 vload<T, VEC, false>(zi, &z[ib]);
-                row_kv<T, VEC, CG, false>(col, pkA, rowptr[row], rowptr[row + 1], z, C, c0, zi, w);
+                row_kv<T, VEC, CG, false>(kent, kptr[row], kptr[row + 1], z, C, c0, zi, w, warp_row);
                 vload<T, VEC, false>(pv, &p[ib]);
                 vload<T, VEC, false>(qv, &q[ib]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     pv[k] = zi[k] + beta[k] * pv[k];
                     qv[k] = (!neu[k] && surf) ? T(0) : w[k] + beta[k] * qv[k];
-                    ppq[0][k] += (double)pv[k] * (double)qv[k];
+                    tpq[k] += pv[k] * qv[k];
                 }
                 vstore<T, VEC>(&p[ib], pv);
                 vstore<T, VEC>(&q[ib], qv);
             }
-        block_reduce_cols<1, VEC>(ppq, scratch, out, C, G, RB);
-        if (!SINGLE) {
-            if (tid < C) part_pq[((size_t)blockIdx.x * C + tid) * 4] = out[tid];
-            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-            cross_reduce_cols<1, VEC>(part_pq, 0, gridDim.x, C, G, RB, scratch, out);
-        }
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) ppq[0][k] = (double)tpq[k];
+        if (!reduce(ppq, 0)) return;
         if (tid < C) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
         __syncthreads();
         T alpha[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) alpha[k] = T(s_ab[c0 + k]);
         double v4[4][VEC];
+        T t0[VEC], t1[VEC], t3[VEC];   // per-thread partial sums in T; block and grid sums in FP64
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = 0.0;
+        for (int k = 0; k < VEC; ++k) t0[k] = t1[k] = t3[k] = T(0);
         if (run)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
@@ -484,27 +526,31 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                     xv[k] += alpha[k] * pv[k];
                     rv[k] -= alpha[k] * qv[k];
                     zv[k] = rv[k] * dinv;
-                    v4[0][k] += (double)rv[k] * (double)zv[k];
-                    v4[1][k] += (double)rv[k] * (double)rv[k];
-                    v4[3][k] += (double)rv[k];
+                    t0[k] += rv[k] * zv[k];
+                    t1[k] += rv[k] * rv[k];
+                    t3[k] += rv[k];
                 }
                 vstore<T, VEC>(&x[ib], xv);
                 vstore<T, VEC>(&r[ib], rv);
                 vstore<T, VEC>(&z[ib], zv);
             }
-        block_reduce_cols<4, VEC>(v4, scratch, out, C, G, RB);
-        if (!SINGLE) {
-            if (tid < C)
-                for (int kk = 0; kk < 4; ++kk)
-                    if (kk != 2) part_rz[((size_t)blockIdx.x * C + tid) * 4 + kk] = out[kk * C + tid];
-            if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-        } else {
-            __syncthreads();
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            v4[0][k] = (double)t0[k];
+            v4[1][k] = (double)t1[k];
+            v4[2][k] = 0.0;
+            v4[3][k] = (double)t3[k];
         }
+        // quantity 2 (ref.ref) is carried over from the prologue in `out`
+        double keep2[1];
+        if (tid < C) keep2[0] = out[2 * C + tid];
+        if (!reduce(v4, 0)) return;
         if (tid < C) {
             s_rhop[tid] = s_rho[tid];
             if (!s_flag[tid]) s_it[tid] += 1;
+            out[2 * C + tid] = keep2[0];
         }
+        __syncthreads();
     }
     if (blockIdx.x == 0) {
         for (int i = tid; i < C; i += bd) {
@@ -515,7 +561,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
         if (tid == 0 && A.sweeps) {
             int kmax = 0;
             for (int i = 0; i < C; ++i) kmax = max(kmax, s_it[i]);
-            A.sweeps[mode] += (unsigned long long)kmax;
+            A.sweeps[mode + (sizeof(T) == 8 ? 2 : 0)] += (unsigned long long)kmax;
         }
     }
     // epilogue: Neumann systems are gauged to zero V-weighted mean; stage 1 then
@@ -533,41 +579,35 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
             for (int k = 0; k < VEC; ++k)
                 if (neu[k]) pv[0][k] += vi * (double)xv[k];
         }
-    block_reduce_cols<1, VEC>(pv, scratch, out, C, G, RB);
-    if (!SINGLE) {
-        if (tid < C) part_pq[((size_t)blockIdx.x * C + tid) * 4 + 1] = out[tid];
-        if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-        cross_reduce_cols<1, VEC>(part_pq, 1, gridDim.x, C, G, RB, scratch, out);
-    }
+    if (!reduce(pv, 1)) return;
     if (tid < C) s_ab[tid] = out[tid] / A.M.vsum;
     __syncthreads();
-    if (any_act)
+    if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;   // every block has read `out` of x
+    bool need_kw = false;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) need_kw |= (mode == 0 && !neu[k] && actk[k]);
+    const bool kw_rows = warp_row ? (__any_sync(0xffffffffu, need_kw) != 0) : need_kw;
+    if (do_rows)
         for (int row = row0; row < N; row += rstride) {
             const size_t ib = (size_t)row * C + c0;
             const int bp = (int)((unsigned)node[row] >> 16);
-            const int e0 = rowptr[row], e1 = rowptr[row + 1];
             T xv[VEC];
             vload<T, VEC, false>(xv, &x[ib]);
-            bool need_kw = false;
+            T kw[VEC];
+            if (kw_rows && bp) row_kv<T, VEC, CG, false>(kent, kptr[row], kptr[row + 1], x, C, c0, xv, kw, warp_row);
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
+                if (!actk[k]) continue;
                 if (neu[k]) {
                     xv[k] -= T(s_ab[c0 + k]);
                     if (mode == 0 && bp) A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] = xv[k];
                 } else if (mode == 0 && bp) {
-                    need_kw = true;
+                    A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] =
+                        T(rhs_b<T>(col, pkA, rowptr[row], rowptr[row + 1],
+                                A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k])) - kw[k];
                 }
             }
             vstore<T, VEC>(&x[ib], xv);
-            if (need_kw) {
-                T kw[VEC];
-                row_kv<T, VEC, CG, false>(col, pkA, e0, e1, x, C, c0, xv, kw);
-#pragma unroll
-                for (int k = 0; k < VEC; ++k)
-                    if (!neu[k] && actk[k])
-                        A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] =
-                            T(rhs_b(col, pkA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k])) - kw[k];
-            }
         }
 }
 
@@ -604,7 +644,7 @@ int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mod
               int* iters_dev) {
     (void)iters_dev;
     const int C = 2 * V.B;
-    PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps};
+    PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps, L.fin};
     const bool single = (long long)M.N * C <= SINGLE_CTA_MAX_WORK;
     const bool vec4 = (sizeof(T) == 4) && (C % 4 == 0);
     cudaError_t e;
@@ -619,12 +659,12 @@ int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mod
 // columns B..2B-1 to the adjoint chain.
 
 // y[row*inc] = sum_j A[row][j] x[j*inc]; one warp per row
-template <typename T>
-__global__ void k_gemv(const T* __restrict__ A, const T* __restrict__ x, T* __restrict__ y, int nb, int inc) {
+template <typename TA, typename T>
+__global__ void k_gemv(const TA* __restrict__ A, const T* __restrict__ x, T* __restrict__ y, int nb, int inc) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int row = warp; row < nb; row += nw) {
-        const T* a = A + (size_t)row * nb;
+        const TA* a = A + (size_t)row * nb;
         double acc = 0.0;
         for (int j = lane; j < nb; j += 32) acc += (double)a[j] * (double)x[(size_t)j * inc];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -633,8 +673,8 @@ __global__ void k_gemv(const T* __restrict__ A, const T* __restrict__ x, T* __re
 }
 
 // part[s][j] = sum_{i in chunk s} A[i][j] x[i*inc]: column-parallel, coalesced rows
-template <typename T>
-__global__ void k_gemv_t_part(const T* __restrict__ A, const T* __restrict__ x, double* __restrict__ part, int nb,
+template <typename TA, typename T>
+__global__ void k_gemv_t_part(const TA* __restrict__ A, const T* __restrict__ x, double* __restrict__ part, int nb,
                               int inc, int rows_per_chunk) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i0 = blockIdx.y * rows_per_chunk, i1 = min(nb, i0 + rows_per_chunk);
@@ -655,36 +695,37 @@ __global__ void k_sum_parts(const double* __restrict__ part, int S, int nb, T* _
 }
 
 // Y[:, 0:ncols] = op(A) X[:, 0:ncols] with row strides ldx, ldy; 64x64 tiles,
-// 256 threads, 4x4 outputs each.  TRANS: op(A) = A^T.
-template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_gemm(const T* __restrict__ A, const T* __restrict__ X, int ldx,
+// 256 threads, 4x4 outputs each.  TRANS: op(A) = A^T.  Arithmetic in the
+// matrix type TA (vectors of type T are converted on load and store).
+template <typename TA, typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_gemm(const TA* __restrict__ A, const T* __restrict__ X, int ldx,
                                               T* __restrict__ Y, int ldy, int nb, int ncols) {
     constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ T As[BK][BM + 4];
-    __shared__ T Xs[BK][BN + 4];
+    __shared__ TA As[BK][BM + 4];
+    __shared__ TA Xs[BK][BN + 4];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    T acc[4][4];
+    TA acc[4][4];
     for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int j = 0; j < 4; ++j) acc[i][j] = TA(0);
     for (int k0 = 0; k0 < nb; k0 += BK) {
         for (int l = tid; l < BM * BK; l += 256) {
             int mm, kk;
             if (TRANS) { kk = l / BM; mm = l % BM; } else { mm = l / BK; kk = l % BK; }
             const int gm = m0 + mm, gk = k0 + kk;
-            T v = T(0);
+            TA v = TA(0);
             if (gm < nb && gk < nb) v = TRANS ? A[(size_t)gk * nb + gm] : A[(size_t)gm * nb + gk];
             As[kk][mm] = v;
         }
         for (int l = tid; l < BK * BN; l += 256) {
             const int kk = l / BN, nn = l % BN;
             const int gk = k0 + kk, gn = n0 + nn;
-            Xs[kk][nn] = (gk < nb && gn < ncols) ? X[(size_t)gk * ldx + gn] : T(0);
+            Xs[kk][nn] = (gk < nb && gn < ncols) ? TA(X[(size_t)gk * ldx + gn]) : TA(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            T a[4], xv[4];
+            TA a[4], xv[4];
             for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
             for (int j = 0; j < 4; ++j) xv[j] = Xs[kk][tx * 4 + j];
             for (int i = 0; i < 4; ++i)
@@ -695,7 +736,7 @@ __global__ void __launch_bounds__(256) k_gemm(const T* __restrict__ A, const T* 
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
             const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
-            if (gm < nb && gn < ncols) Y[(size_t)gm * ldy + gn] = acc[i][j];
+            if (gm < nb && gn < ncols) Y[(size_t)gm * ldy + gn] = T(acc[i][j]);
         }
 }
 
@@ -711,26 +752,33 @@ int bem_chunks(int nb, int num_sms) {
     return S;
 }
 
-template <typename T>
-void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V) {
-    const T* Bm = bem_ptr<T>(M);
+template <typename TA, typename T>
+static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const BatchView<T>& V) {
     const int B = V.B, C = 2 * B, nb = M.nb;
     if (B == 1) {
         int blocks = (nb * 32 + 255) / 256;
         if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
-        k_gemv<T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub_in, V.ub_out, nb, C);
+        k_gemv<TA, T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub_in, V.ub_out, nb, C);
         const int S = bem_chunks(nb, L.num_sms);
         const int rpc = (nb + S - 1) / S;
-        k_gemv_t_part<T><<<dim3((nb + 255) / 256, S), 256, 0, L.stream>>>(Bm, V.ub_in + 1, (double*)V.bem_part, nb,
-                                                                         C, rpc);
+        k_gemv_t_part<TA, T><<<dim3((nb + 255) / 256, S), 256, 0, L.stream>>>(Bm, V.ub_in + 1, (double*)V.bem_part,
+                                                                             nb, C, rpc);
         k_sum_parts<T><<<(nb + 255) / 256, 256, 0, L.stream>>>((const double*)V.bem_part, S, nb, V.ub_out + 1, C);
         *L.launches += 3;
     } else {
         dim3 grid((nb + 63) / 64, (B + 63) / 64);
-        k_gemm<T, false><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in, C, V.ub_out, C, nb, B);
-        k_gemm<T, true><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in + B, C, V.ub_out + B, C, nb, B);
+        k_gemm<TA, T, false><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in, C, V.ub_out, C, nb, B);
+        k_gemm<TA, T, true><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in + B, C, V.ub_out + B, C, nb, B);
         *L.launches += 2;
     }
+}
+
+// bem32: use the FP32 copy of B (a fixed operator, so energy and gradient stay
+// consistent) even for FP64 vectors -- the FP64 phase of a mixed-precision run.
+template <typename T>
+void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V, bool bem32) {
+    if (sizeof(T) == 4 || bem32) bem_launch<float, T>(L, M.B32, M, V);
+    else bem_launch<double, T>(L, M.B64, M, V);
 }
 
 // ---- effective field, gradient, energies and step dot products -----------------------
@@ -1127,7 +1175,7 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
 
 #define LBM_INSTANTIATE(T)                                                                               \
     template int pcg_solve<T>(const Launch&, const MeshView&, const BatchView<T>&, int, double, int, int*); \
-    template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&);                     \
+    template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&, bool);               \
     template void field_eval<T>(const Launch&, const MeshView&, const BatchView<T>&, int);                 \
     template void trial_update<T>(const Launch&, const MeshView&, const BatchView<T>&);                    \
     template void decide<T>(const Launch&, const MeshView&, const BatchView<T>&, const StepOpts&, int);    \
