@@ -49,6 +49,10 @@ def parse():
                     help="instances of the plain-FP64 single-instance comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--workload", default="batched", choices=["batched", "served"],
+                    help="batched: 64 same-mesh instances (default); served: Poisson request stream")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--rate", type=float, default=0.0, help="arrivals/s (0: 0.8 x calibrated capacity)")
     return ap.parse_args()
 
 
@@ -359,11 +363,69 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_served(args, ws, rank, local):
+    """Served stream: Poisson arrivals of minimisation requests on cubes of
+    10^3..50^3 cells (random field and tilt), continuous batching in the
+    library's server; p50/p99 latency (submit -> result) and solves/s."""
+    import torch
+    import paper_1309_5796_gb300 as lbm
+    from synth.inputs import served_stream
+    torch.cuda.set_device(local)
+    ctx = lbm.Context(local)
+    ctx.serve_start(slots=16, chunk=8)
+    rate = args.rate
+    calib = None
+    if rate <= 0:
+        # closed-loop burst of 48 requests of the same distribution -> capacity
+        burst = served_stream(48, 1.0, seed=55)
+        t0 = time.perf_counter()
+        ts = [ctx.submit(r.inst.n, 2e-9, JS_T, A_JM, K1_JM3, r.inst.axis, r.inst.h_ext, r.inst.m0)
+              for r in burst]
+        for t in ts:
+            ctx.wait(t, None, timeout_s=900)
+        cap = len(burst) / (time.perf_counter() - t0)
+        rate = 0.8 * cap
+        calib = {"burst_requests": len(burst), "capacity_solves_per_s": cap}
+    reqs = served_stream(args.requests, rate, seed=5)
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launch_count()
+    t_start = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        delay = r.arrival_s - (time.perf_counter() - t_start)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(ctx.submit(r.inst.n, 2e-9, JS_T, A_JM, K1_JM3, r.inst.axis, r.inst.h_ext, r.inst.m0))
+    results = [ctx.wait(t, None, timeout_s=1800)[0] for t in tickets]
+    makespan = time.perf_counter() - t_start
+    clocks = sampler.stop()
+    stats = ctx.serve_stats()
+    launches = ctx.launch_count() - launches0
+    ctx.serve_stop()
+    lat = np.array([r["wall_ms"] for r in results])
+    ok = sum(r["status"] == 0 for r in results)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": ok / makespan, "unit": "solves/s", "n_gpus": ws, "steps": 1,
+            "warmup": 0, "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"served stream: {args.requests} Poisson requests at {rate:.2f}/s, "
+                                   "cubes of 10^3..50^3 cells, mixed precision, 16 slots per cube size",
+                       "rate_per_s": rate, "calibration": calib},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "completed_ok": ok, "stats": stats, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "served":
+        run_served(args, ws, rank, local)
         return
     run_ours(args, ws, rank, local)
 

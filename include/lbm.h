@@ -38,6 +38,7 @@ extern "C" {
 #define LBM_E_TIMEOUT        5   /* a device-side wait ran out of time (kernel returned) */
 #define LBM_E_LINESEARCH     6   /* the step-halving line search gave up */
 #define LBM_E_CUDA           7   /* CUDA runtime error */
+#define LBM_E_PENDING        8   /* lbm_poll: the request has not finished yet */
 
 /* ---- precision modes ---------------------------------------------------------- */
 #define LBM_FP64      0  /* every vector, field and reduction in FP64 */
@@ -192,6 +193,51 @@ typedef struct {
 } lbm_profile_stats;
 int lbm_profile_enable(lbm_ctx* ctx, int32_t on);
 int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);
+
+/* ---- serving: continuous batching of minimisation requests ---------------------
+ * A worker thread of the context owns the device while serving.  Requests
+ * (a cube size, material, applied field and initial m) are admitted into free
+ * slots of a per-cube-size group when device memory allows (groups are created
+ * on demand and idle groups are evicted under memory pressure); every group
+ * advances its active slots `chunk` iterations at a time on its own stream, so
+ * the work of different groups overlaps on the device; finished slots are
+ * retired and refilled from the queue.  Mixed-precision requests run their FP32
+ * phase in an FP32 batch and move, on reaching switch_tol, to the group's FP64
+ * batch (Sec. 2.2-2.3 iteration, same results as lbm_minimise).  Between
+ * lbm_serve_start and lbm_serve_stop no other call may use the context except
+ * lbm_submit, lbm_poll, lbm_wait, lbm_serve_stats and lbm_last_error. */
+typedef int64_t lbm_ticket;
+
+typedef struct {
+    int32_t      n;          /* cells per side of the cube (1..96) */
+    double       cell_m;     /* cell edge (m) */
+    lbm_material mat;
+    double       h[3];       /* applied field mu0*H (T) */
+    const double* m0;        /* [N*3] initial m, host; copied by lbm_submit */
+    int32_t      precision;  /* LBM_FP64 or LBM_MIXED */
+} lbm_request;
+
+typedef struct {
+    int32_t slots;           /* batch width of each group (default 16) */
+    int32_t chunk;           /* iterations issued per group between polls (default 8) */
+    int32_t max_pcg_blocks;  /* cooperative grid cap per group (default SMs/4) */
+    double  mem_reserve;     /* fraction of device memory kept free (default 0.05) */
+    lbm_solve_opts opt;      /* solve options of every request */
+} lbm_serve_opts;
+
+void lbm_default_serve_opts(lbm_serve_opts* o);
+int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt /* NULL: defaults */);
+/* Queue a request; returns immediately with its ticket. */
+int lbm_submit(lbm_ctx* ctx, const lbm_request* req, lbm_ticket* out);
+/* LBM_OK and the result (res->wall_ms = submit-to-completion latency) when the
+ * request finished, LBM_E_PENDING otherwise.  m_out (nullable): [N*3]. */
+int lbm_poll(lbm_ctx* ctx, lbm_ticket t, lbm_result* res, double* m_out);
+/* Block until the request finished (bounded by timeout_s; LBM_E_TIMEOUT after). */
+int lbm_wait(lbm_ctx* ctx, lbm_ticket t, double timeout_s, lbm_result* res, double* m_out);
+/* stats[0..7] = submitted, admitted, completed, pending, active slots, groups,
+ * admission stalls (memory), groups evicted. */
+int lbm_serve_stats(lbm_ctx* ctx, int64_t stats[8]);
+int lbm_serve_stop(lbm_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -18,10 +18,10 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
 
 LBM_OK, LBM_E_INVALID, LBM_E_OOM, LBM_E_NOT_CONVERGED = 0, 1, 2, 3
-LBM_E_NAN, LBM_E_TIMEOUT, LBM_E_LINESEARCH, LBM_E_CUDA = 4, 5, 6, 7
+LBM_E_NAN, LBM_E_TIMEOUT, LBM_E_LINESEARCH, LBM_E_CUDA, LBM_E_PENDING = 4, 5, 6, 7, 8
 LBM_FP64, LBM_MIXED, LBM_MIXED_TC = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NOT_CONVERGED", 4: "NAN", 5: "TIMEOUT",
-                6: "LINESEARCH", 7: "CUDA"}
+                6: "LINESEARCH", 7: "CUDA", 8: "PENDING"}
 
 
 class Material(C.Structure):
@@ -59,6 +59,16 @@ class Result(C.Structure):
                     gg=self.gg, mean_m=list(self.mean_m), wall_ms=self.wall_ms)
 
 
+class Request(C.Structure):
+    _fields_ = [("n", C.c_int32), ("cell_m", C.c_double), ("mat", Material), ("h", C.c_double * 3),
+                ("m0", C.POINTER(C.c_double)), ("precision", C.c_int32)]
+
+
+class ServeOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("chunk", C.c_int32), ("max_pcg_blocks", C.c_int32),
+                ("mem_reserve", C.c_double), ("opt", SolveOpts)]
+
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _DP = C.POINTER(C.c_double)
@@ -89,6 +99,13 @@ SIGNATURES = [
     ("lbm_set_m_device", C.c_int, [_P, _I64, C.c_void_p]),
     ("lbm_profile_enable", C.c_int, [_P, C.c_int32]),
     ("lbm_profile_read", C.c_int, [_P, C.POINTER(ProfileStats), C.c_int32]),
+    ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
+    ("lbm_serve_start", C.c_int, [_P, C.POINTER(ServeOpts)]),
+    ("lbm_submit", C.c_int, [_P, C.POINTER(Request), C.POINTER(_I64)]),
+    ("lbm_poll", C.c_int, [_P, _I64, C.POINTER(Result), _DP]),
+    ("lbm_wait", C.c_int, [_P, _I64, C.c_double, C.POINTER(Result), _DP]),
+    ("lbm_serve_stats", C.c_int, [_P, C.POINTER(_I64)]),
+    ("lbm_serve_stop", C.c_int, [_P]),
 ]
 
 _lib = None
@@ -200,6 +217,56 @@ class Context:
         h = _I64()
         _check(lib().lbm_instance_create(self._h, mesh, batch, precision, C.byref(h)))
         return Instance(self, h.value, mesh, batch, precision)
+
+    # -- serving (continuous batching) ---------------------------------------
+    def serve_start(self, **kw):
+        o = ServeOpts()
+        lib().lbm_default_serve_opts(C.byref(o))
+        for k, v in kw.items():
+            if k == "opt":
+                o.opt = v
+            else:
+                setattr(o, k, v)
+        _check(lib().lbm_serve_start(self._h, C.byref(o)))
+
+    def submit(self, n, cell_m, Js, A, K1, axis, h, m0, precision=LBM_MIXED) -> int:
+        m0 = np.ascontiguousarray(np.asarray(m0, np.float64))
+        r = Request()
+        r.n, r.cell_m, r.precision = n, cell_m, precision
+        r.mat.Js, r.mat.A, r.mat.K1 = Js, A, K1
+        for d in range(3):
+            r.mat.axis[d] = axis[d]
+            r.h[d] = h[d]
+        r.m0 = _dptr(m0)
+        t = _I64()
+        _check(lib().lbm_submit(self._h, C.byref(r), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, N: int | None = None):
+        """(result dict, m) when finished, None while pending."""
+        res = Result()
+        m = np.empty((N, 3)) if N else None
+        rc = lib().lbm_poll(self._h, ticket, C.byref(res), _dptr(m))
+        if rc == LBM_E_PENDING:
+            return None
+        _check(rc)
+        return res.as_dict(), m
+
+    def wait(self, ticket: int, N: int | None = None, timeout_s: float = 600.0):
+        res = Result()
+        m = np.empty((N, 3)) if N else None
+        _check(lib().lbm_wait(self._h, ticket, timeout_s, C.byref(res), _dptr(m)))
+        return res.as_dict(), m
+
+    def serve_stats(self) -> dict:
+        st = (_I64 * 8)()
+        _check(lib().lbm_serve_stats(self._h, st))
+        keys = ("submitted", "admitted", "completed", "pending", "active_slots", "groups", "stalls",
+                "evicted")
+        return {k: int(st[i]) for i, k in enumerate(keys)}
+
+    def serve_stop(self):
+        _check(lib().lbm_serve_stop(self._h))
 
     def launch_count(self) -> int:
         c = _I64()

@@ -9,8 +9,13 @@
 #include <string.h>
 
 #include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -51,6 +56,7 @@ struct Mesh {
     int nnzK = 0;
     double* B64 = nullptr;
     float* B32 = nullptr;
+    float *tcA = nullptr, *tcAT = nullptr;   // padded FP32 B and B^T for the tensor-core path (lazy)
     size_t bytes = 0;
     MeshView view() const {
         MeshView v;
@@ -75,6 +81,9 @@ struct Inst {
     double* staged_u = nullptr;    // B*2*N doubles
     Inst* polish = nullptr;        // FP64 shadow batch finishing mixed-precision runs
     bool bem32 = false;            // BEM product with the FP32 matrix (FP64 phase of mixed runs)
+    bool use_tc = false;           // BEM products on the tensor cores (LBM_MIXED_TC, 2 <= batch <= 64)
+    float* tc_scratch = nullptr;
+    bool owns_tc_scratch = true;
     std::vector<lbm_material> mats;
     std::vector<double> h;         // B*3 tesla
     size_t bytes = 0;
@@ -87,7 +96,10 @@ struct ProfEvent {
     cudaEvent_t a, b;
 };
 
+namespace { struct Server; }
+
 struct lbm_ctx {
+    Server* server = nullptr;
     int device = 0;
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -106,7 +118,7 @@ struct lbm_ctx {
     std::map<int64_t, Inst*> insts;
     unsigned long long* sweeps = nullptr;   // device [4]
     double* fin = nullptr;                  // device [4096] grid-reduction results
-    Launch launch() { return Launch{stream, num_sms, bar, err, &launches, sweeps, fin}; }
+    Launch launch() { return Launch{stream, num_sms, bar, err, &launches, sweeps, fin, 0}; }
 };
 
 namespace {
@@ -122,21 +134,23 @@ cudaEvent_t pool_get(lbm_ctx* ctx) {
     return e;
 }
 
-// Brackets one launch of `kind` with events on the context's stream.
+// Brackets one launch of `kind` with events on the launching stream (the
+// context's stream; launches on other streams are not profiled).
 struct ProfScope {
     lbm_ctx* ctx;
     int kind;
+    cudaStream_t st;
     cudaEvent_t a = nullptr;
-    ProfScope(lbm_ctx* c, int k) : ctx(c), kind(k) {
-        if (ctx->prof) {
+    ProfScope(lbm_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s) {
+        if (ctx->prof && st == ctx->stream) {
             a = pool_get(ctx);
-            cudaEventRecord(a, ctx->stream);
+            cudaEventRecord(a, st);
         }
     }
     ~ProfScope() {
         if (a) {
             cudaEvent_t b = pool_get(ctx);
-            cudaEventRecord(b, ctx->stream);
+            cudaEventRecord(b, st);
             ctx->ev_live.push_back(ProfEvent{kind, a, b});
         }
     }
@@ -229,7 +243,7 @@ Inst* get_inst(lbm_ctx* ctx, lbm_inst h) {
 
 void free_mesh(Mesh* m) {
     void* ptrs[] = {m->rowptr, m->col, m->pkA, m->pkB, m->node, m->bidx, m->tris, m->inc_ptr, m->inc_slot,
-                    m->kptr, m->kent, m->B64, m->B32};
+                    m->kptr, m->kent, m->B64, m->B32, m->tcA, m->tcAT};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -237,6 +251,7 @@ void free_mesh(Mesh* m) {
 
 void free_inst(Inst* I) {
     if (I->polish) free_inst(I->polish);
+    if (I->tc_scratch && I->owns_tc_scratch) cudaFree(I->tc_scratch);
     void* ptrs[] = {I->vec, I->part, I->st, I->ic, I->staged, I->staged_u};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -292,31 +307,53 @@ int check_opts(const lbm_solve_opts& o) {
 
 // One field evaluation of every active instance at its trial point.
 template <typename T>
-int eval_trial(lbm_ctx* ctx, const Mesh& M, const Inst& I, const BatchView<T>& V, const lbm_solve_opts& o) {
-    Launch L = ctx->launch();
+int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, const BatchView<T>& V,
+               const lbm_solve_opts& o) {
     MeshView mv = M.view();
     if (o.demag) {
         int e;
         const int k64 = sizeof(T) == 8 ? 5 : 0;
         {
-            ProfScope ps(ctx, 1 + k64);
+            ProfScope ps(ctx, 1 + k64, L.stream);
             e = pcg_solve<T>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, nullptr);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
         {
-            ProfScope ps(ctx, 2);
-            bem_product<T>(L, mv, V, I.bem32);
+            ProfScope ps(ctx, 2, L.stream);
+            if (I.use_tc && M.tcA && I.tc_scratch) {
+                e = bem_product_tc<T>(L, M.nb, M.tcA, M.tcAT, V.ub_in, V.ub_out, V.B, I.tc_scratch);
+                if (e) return fail(LBM_E_CUDA, "tensor-core BEM product failed (%d)", e);
+            } else {
+                bem_product<T>(L, mv, V, I.bem32);
+            }
         }
         {
-            ProfScope ps(ctx, 3 + (k64 ? 4 : 0));
+            ProfScope ps(ctx, 3 + (k64 ? 4 : 0), L.stream);
             e = pcg_solve<T>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, nullptr);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
     {
-        ProfScope ps(ctx, 4);
+        ProfScope ps(ctx, 4, L.stream);
         field_eval<T>(L, mv, V, o.demag);
     }
+    return LBM_OK;
+}
+
+// One iteration of every active instance: trial point (Eq. 8), field
+// evaluation at it, step decision (Sec. 2.3).
+template <typename T>
+int iterate_once(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, const BatchView<T>& V,
+                 const lbm_solve_opts& o, const StepOpts& so, int nblk_field) {
+    const MeshView mv = M.view();
+    {
+        ProfScope ps(ctx, 0, L.stream);
+        trial_update<T>(L, mv, V);
+    }
+    int e = eval_trial<T>(ctx, L, M, I, V, o);
+    if (e) return e;
+    ProfScope ps(ctx, 5, L.stream);
+    decide<T>(L, mv, V, so, nblk_field);
     return LBM_OK;
 }
 
@@ -355,14 +392,8 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
     while (true) {
         const int chunk = evaluate_only ? 1 : oo.check_every;
         for (int k = 0; k < chunk; ++k) {
-            {
-                ProfScope ps(ctx, 0);
-                trial_update<T>(L, mv, V);
-            }
-            int e = eval_trial<T>(ctx, M, *I, V, oo);
+            int e = iterate_once<T>(ctx, L, M, *I, V, oo, so, nblk_field);
             if (e) return e;
-            ProfScope ps(ctx, 5);
-            decide<T>(L, mv, V, so, nblk_field);
         }
         loops += chunk;
         CK(cudaGetLastError());
@@ -433,6 +464,9 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
             P->precision = LBM_FP64;
             P->tsize = 8;
             P->bem32 = true;
+            P->use_tc = I->use_tc;
+            P->tc_scratch = I->tc_scratch;   // the phases run one after the other on one stream
+            P->owns_tc_scratch = false;
             const size_t vb = vec_bytes(M, I->B, 8), pe = part_elems(ctx, I->B);
             if (cudaMalloc(&P->vec, vb) != cudaSuccess || cudaMalloc(&P->part, pe * sizeof(double)) != cudaSuccess ||
                 cudaMalloc(&P->st, sizeof(InstState) * B) != cudaSuccess ||
@@ -553,6 +587,7 @@ int lbm_create(lbm_ctx** out, int32_t device, void* stream) {
 
 int lbm_destroy(lbm_ctx* ctx) {
     if (!ctx) return LBM_OK;
+    if (ctx->server) lbm_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->insts) free_inst(kv.second);
@@ -770,6 +805,26 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
     CKI(cudaMemsetAsync(I->st, 0, sizeof(InstState) * batch, ctx->stream));
 #undef CKI
     I->bytes = vb + pe * 8 + (sizeof(InstState) + sizeof(InstConst)) * batch + 40 * batch * N;
+    if (precision == LBM_MIXED_TC && batch >= 2 && batch <= 64) {
+        // tensor-core BEM products: padded B / B^T per mesh, split/partial scratch per instance
+        const size_t pad = sizeof(float) * (size_t)M->nb * tc_ld(M->nb);
+        if (!M->tcA) {
+            if (cudaMalloc(&M->tcA, pad) != cudaSuccess || cudaMalloc(&M->tcAT, pad) != cudaSuccess) {
+                if (M->tcA) cudaFree(M->tcA);
+                M->tcA = M->tcAT = nullptr;
+                free_inst(I);
+                return fail(LBM_E_OOM, "tensor-core copies of the BEM matrix");
+            }
+            Launch L = ctx->launch();
+            tc_prepare(L, M->B32, M->nb, M->tcA, M->tcAT);
+            M->bytes += 2 * pad;
+        }
+        if (cudaMalloc(&I->tc_scratch, sizeof(float) * tc_scratch_floats(M->nb, batch, ctx->num_sms)) != cudaSuccess) {
+            free_inst(I);
+            return fail(LBM_E_OOM, "tensor-core scratch");
+        }
+        I->use_tc = true;
+    }
     lbm_material nd = {1.61, 7.7e-12, 4.3e6, {0.0, 0.0, 1.0}};
     I->mats.assign(batch, nd);
     I->h.assign(3 * batch, 0.0);
@@ -929,6 +984,531 @@ int lbm_hysteresis(lbm_ctx* ctx, lbm_inst inst, const double dir[3], const doubl
             if (res) res[(size_t)k * I->B + b] = r[b];
         }
     }
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Serving: continuous batching of minimisation requests.
+// ============================================================================
+namespace {
+
+__global__ void k_slot_reset(InstState* st, int b, int phase) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    InstState& s = st[b];
+    s.phase = phase;
+    s.status = phase == PH_DONE ? 0 : 3;
+    s.cur = 0;
+    s.iters = s.evals = s.line_searches = s.backtracks = 0;
+    s.nhist = s.hpos = s.ntau2 = 0;
+    s.cg1 = s.cg2 = 0;
+}
+
+__global__ void k_slots_done(InstState* st, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) { st[b].phase = PH_DONE; st[b].status = 0; st[b].cur = 0; }
+}
+
+// m of slot b (buffer 0) from a node-major [N][3] array
+__global__ void k_slot_pack_m(const double* __restrict__ src, double* __restrict__ m, int N, int B, int b) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * N; t += gridDim.x * blockDim.x)
+        m[(size_t)t * B + b] = src[t];
+}
+
+__global__ void k_slot_unpack_m(const double* __restrict__ m, const InstState* st, int N, int B, int b,
+                                double* __restrict__ out) {
+    const size_t off = (size_t)st[b].cur * N * 3 * B;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * N; t += gridDim.x * blockDim.x)
+        out[t] = m[off + (size_t)t * B + b];
+}
+
+// zero the forward and adjoint potential columns of slot b (cold start)
+template <typename T>
+__global__ void k_slot_zero_pot(T* U1, T* U2, int N, int B, int b) {
+    const int C = 2 * B;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        U1[(size_t)i * C + b] = T(0);
+        U1[(size_t)i * C + B + b] = T(0);
+        U2[(size_t)i * C + b] = T(0);
+        U2[(size_t)i * C + B + b] = T(0);
+    }
+}
+
+// move slot bs of an FP32 batch to slot bd of an FP64 batch: m (base point)
+// and the forward/adjoint potentials (widened), the FP64 phase's warm start
+__global__ void k_slot_move(const double* __restrict__ ms, const InstState* sts, int Bs, int bs,
+                            const float* __restrict__ U1s, const float* __restrict__ U2s, double* __restrict__ md,
+                            int Bd, int bd, double* __restrict__ U1d, double* __restrict__ U2d, int N) {
+    const size_t off = (size_t)sts[bs].cur * N * 3 * Bs;
+    const int Cs = 2 * Bs, Cd = 2 * Bd;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * N; t += gridDim.x * blockDim.x)
+        md[(size_t)t * Bd + bd] = ms[off + (size_t)t * Bs + bs];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        U1d[(size_t)i * Cd + bd] = (double)U1s[(size_t)i * Cs + bs];
+        U1d[(size_t)i * Cd + Bd + bd] = (double)U1s[(size_t)i * Cs + Bs + bs];
+        U2d[(size_t)i * Cd + bd] = (double)U2s[(size_t)i * Cs + bs];
+        U2d[(size_t)i * Cd + Bd + bd] = (double)U2s[(size_t)i * Cs + Bs + bs];
+    }
+}
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Ticket {
+    lbm_request req{};
+    std::vector<double> m0, m_out;
+    lbm_result res{};
+    InstState s32{};
+    bool has32 = false;
+    int state = 0;            // 0 pending, 1 active, 2 done
+    double t_submit = 0, t_done = 0;
+};
+
+struct Group {
+    int n = 0;
+    double cell = 0;
+    int64_t mesh_id = 0, i32_id = 0, i64_id = 0;
+    Inst *I32 = nullptr, *I64 = nullptr;
+    cudaStream_t stream = nullptr;
+    unsigned* bar = nullptr;
+    int* err = nullptr;
+    double* fin = nullptr;
+    unsigned long long* sweeps = nullptr;
+    double* staged = nullptr;          // [N*3] device staging of one slot
+    std::vector<int64_t> t32, t64;     // ticket of each slot (-1: free)
+    std::vector<InstState> h32, h64;   // states read back each poll
+    std::vector<char> fresh32, fresh64;
+    double last_used = 0;
+    size_t bytes = 0;
+    int occupied() const {
+        int k = 0;
+        for (auto t : t32) k += t >= 0;
+        for (auto t : t64) k += t >= 0;
+        return k;
+    }
+};
+
+struct Server {
+    lbm_ctx* ctx = nullptr;
+    lbm_serve_opts opt{};
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    int worker_rc = LBM_OK;
+    std::string worker_err;
+    std::deque<int64_t> pending;
+    std::map<int64_t, std::unique_ptr<Ticket>> tickets;   // stable storage; map guarded by mu
+    int64_t next_ticket = 1;
+    std::map<int, Group*> groups;
+    int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_stalls = 0, n_evicted = 0;
+    std::vector<double> pinned_m;      // host staging
+};
+
+Launch group_launch(lbm_ctx* ctx, Group& G, int max_blocks) {
+    return Launch{G.stream, ctx->num_sms, G.bar, G.err, &ctx->launches, G.sweeps, G.fin, max_blocks};
+}
+
+void group_free(lbm_ctx* ctx, Group* G) {
+    if (G->stream) cudaStreamSynchronize(G->stream);
+    if (G->i32_id) lbm_instance_destroy(ctx, G->i32_id);
+    if (G->i64_id) lbm_instance_destroy(ctx, G->i64_id);
+    if (G->mesh_id) lbm_mesh_destroy(ctx, G->mesh_id);
+    void* ptrs[] = {G->bar, G->err, G->fin, G->sweeps, G->staged};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (G->stream) cudaStreamDestroy(G->stream);
+    delete G;
+}
+
+size_t group_estimate(int n, int slots) {
+    const size_t N = (size_t)(n + 1) * (n + 1) * (n + 1);
+    const size_t nb = N - (size_t)(n > 1 ? (n - 1) * (n - 1) * (n - 1) : 0);
+    const size_t mesh = 12 * nb * nb + 100 * N;
+    const size_t per_slot = 8 * (2 * N * 3 * 2 + 3 * N) * 2 + (4 + 8) * (12 * N + 4 * nb) + 40 * N;
+    return mesh + per_slot * slots + ((size_t)64 << 20);
+}
+
+// Create (or reuse) the group of cube size n, evicting idle groups when the
+// device lacks memory.  Returns nullptr when the request must wait.
+Group* group_get(Server& S, int n, double cell) {
+    auto it = S.groups.find(n);
+    if (it != S.groups.end()) return it->second;
+    lbm_ctx* ctx = S.ctx;
+    const size_t need = group_estimate(n, S.opt.slots);
+    for (;;) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        if (fr > need + (size_t)(S.opt.mem_reserve * (double)tot)) break;
+        Group* victim = nullptr;
+        for (auto& kv : S.groups)
+            if (kv.second->occupied() == 0 && (!victim || kv.second->last_used < victim->last_used)) victim = kv.second;
+        if (!victim) return nullptr;
+        S.groups.erase(victim->n);
+        group_free(ctx, victim);
+        S.n_evicted += 1;
+    }
+    Group* G = new Group();
+    G->n = n;
+    G->cell = cell;
+    const int B = S.opt.slots;
+    auto bad = [&](int rc) {
+        (void)rc;
+        group_free(ctx, G);
+        return (Group*)nullptr;
+    };
+    if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess) return bad(0);
+    if (cudaMalloc(&G->bar, 64) != cudaSuccess || cudaMalloc(&G->err, 64) != cudaSuccess ||
+        cudaMalloc(&G->fin, sizeof(double) * 4096) != cudaSuccess || cudaMalloc(&G->sweeps, 64) != cudaSuccess)
+        return bad(0);
+    cudaMemset(G->bar, 0, 64);
+    cudaMemset(G->err, 0, 64);
+    cudaMemset(G->sweeps, 0, 64);
+    if (lbm_mesh_cube(ctx, cell, n, &G->mesh_id) != LBM_OK) return bad(0);
+    if (lbm_instance_create(ctx, G->mesh_id, B, LBM_MIXED, &G->i32_id) != LBM_OK) return bad(0);
+    if (lbm_instance_create(ctx, G->mesh_id, B, LBM_FP64, &G->i64_id) != LBM_OK) return bad(0);
+    G->I32 = ctx->insts[G->i32_id];
+    G->I64 = ctx->insts[G->i64_id];
+    G->I64->bem32 = true;      // the FP64 phase of mixed requests
+    const int N = ctx->meshes[G->mesh_id]->N;
+    if (cudaMalloc(&G->staged, sizeof(double) * 3 * N) != cudaSuccess) return bad(0);
+    k_slots_done<<<(B + 127) / 128, 128, 0, ctx->stream>>>(G->I32->st, B);
+    k_slots_done<<<(B + 127) / 128, 128, 0, ctx->stream>>>(G->I64->st, B);
+    ctx->launches += 2;
+    cudaStreamSynchronize(ctx->stream);
+    G->t32.assign(B, -1);
+    G->t64.assign(B, -1);
+    G->h32.assign(B, InstState{});
+    G->h64.assign(B, InstState{});
+    G->fresh32.assign(B, 0);
+    G->fresh64.assign(B, 0);
+    G->bytes = need;
+    S.groups[n] = G;
+    return G;
+}
+
+void set_slot_consts(Inst* I, int b, const lbm_material& mat, const double h[3], double cell, cudaStream_t st) {
+    I->mats[b] = mat;
+    for (int d = 0; d < 3; ++d) I->h[3 * b + d] = h[d];
+    const double Kd = mat.Js * mat.Js / (2.0 * MU0);
+    double an = sqrt(mat.axis[0] * mat.axis[0] + mat.axis[1] * mat.axis[1] + mat.axis[2] * mat.axis[2]);
+    if (!(an > 0)) an = 1.0;
+    InstConst c;
+    c.lam = mat.A / (Kd * cell * cell);
+    c.Q = mat.K1 / Kd;
+    for (int d = 0; d < 3; ++d) {
+        c.a[d] = mat.axis[d] / an;
+        c.hz[d] = h[d] / mat.Js;
+    }
+    c.Eunit = Kd * cell * cell * cell;
+    c.Js = mat.Js;
+    cudaMemcpyAsync(I->ic + b, &c, sizeof c, cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);   // c is a stack value
+}
+
+// Put ticket t into a free slot of the FP32 (mixed) or FP64 batch of G.
+bool admit(Server& S, Group& G, int64_t t, Ticket& T) {
+    lbm_ctx* ctx = S.ctx;
+    const bool fp64 = T.req.precision == LBM_FP64;
+    std::vector<int64_t>& slots = fp64 ? G.t64 : G.t32;
+    int b = -1;
+    for (int k = 0; k < (int)slots.size(); ++k)
+        if (slots[k] < 0) { b = k; break; }
+    if (b < 0) return false;
+    Inst* I = fp64 ? G.I64 : G.I32;
+    Mesh& M = *ctx->meshes[G.mesh_id];
+    const int N = M.N, B = I->B;
+    cudaMemcpyAsync(G.staged, T.m0.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, G.stream);
+    k_slot_reset<<<1, 1, 0, G.stream>>>(I->st, b, PH_INIT);
+    k_slot_pack_m<<<64, 256, 0, G.stream>>>(G.staged, (double*)I->vec, N, B, b);
+    if (fp64) {
+        const VecLayout L = vec_layout(M, B, 8);
+        k_slot_zero_pot<double><<<64, 256, 0, G.stream>>>((double*)((char*)I->vec + L.U1),
+                                                          (double*)((char*)I->vec + L.U2), N, B, b);
+    } else {
+        const VecLayout L = vec_layout(M, B, 4);
+        k_slot_zero_pot<float><<<64, 256, 0, G.stream>>>((float*)((char*)I->vec + L.U1),
+                                                         (float*)((char*)I->vec + L.U2), N, B, b);
+    }
+    ctx->launches += 3;
+    set_slot_consts(I, b, T.req.mat, T.req.h, G.cell, G.stream);
+    slots[b] = t;
+    (fp64 ? G.fresh64 : G.fresh32)[b] = 1;
+    return true;
+}
+
+void complete(Server& S, Group& G, int b, const InstState& s, Ticket& T) {
+    lbm_ctx* ctx = S.ctx;
+    Mesh& M = *ctx->meshes[G.mesh_id];
+    const int N = M.N;
+    T.m_out.resize(3 * (size_t)N);
+    double* d_out = G.staged;
+    k_slot_unpack_m<<<64, 256, 0, G.stream>>>((const double*)G.I64->vec, G.I64->st, N, G.I64->B, b, d_out);
+    ctx->launches += 1;
+    cudaMemcpyAsync(T.m_out.data(), d_out, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, G.stream);
+    cudaStreamSynchronize(G.stream);
+    InstConst c;
+    cudaMemcpy(&c, G.I64->ic + b, sizeof c, cudaMemcpyDeviceToHost);
+    T.t_done = now_s();
+    fill_result(s, c, T.res, 1e3 * (T.t_done - T.t_submit));
+    if (T.has32) {
+        T.res.iterations += T.s32.iters;
+        T.res.evaluations += T.s32.evals;
+        T.res.line_searches += T.s32.line_searches;
+        T.res.cg_iters1 += T.s32.cg1;
+        T.res.cg_iters2 += T.s32.cg2;
+    }
+    T.state = 2;
+    S.n_completed += 1;
+}
+
+void fail_ticket(Server& S, Ticket& T, int status) {
+    T.t_done = now_s();
+    memset(&T.res, 0, sizeof T.res);
+    T.res.status = status;
+    T.res.wall_ms = 1e3 * (T.t_done - T.t_submit);
+    T.state = 2;
+    S.n_completed += 1;
+}
+
+void serve_loop(Server* Sp) {
+    Server& S = *Sp;
+    lbm_ctx* ctx = S.ctx;
+    cudaSetDevice(ctx->device);
+    const lbm_solve_opts o = S.opt.opt;
+    lbm_solve_opts o1 = o;
+    o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;
+    lbm_solve_opts o2 = o;
+    o2.cg_tol = o.cg_tol_polish;
+    const StepOpts so1 = step_opts(o1), so2 = step_opts(o2);
+    lbm_solve_opts o64 = o;        // plain FP64 requests
+    for (;;) {
+        // ---- admission (the queue lock is not held while meshes are built) ---
+        std::vector<std::pair<int64_t, Ticket*>> todo;
+        {
+            std::unique_lock<std::mutex> lk(S.mu);
+            if (S.stop) break;
+            bool busy = false;
+            for (auto& kv : S.groups) busy |= kv.second->occupied() > 0;
+            if (!busy && S.pending.empty())
+                S.cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            if (S.stop) break;
+            for (int64_t t : S.pending) todo.emplace_back(t, S.tickets[t].get());
+            S.pending.clear();
+        }
+        std::vector<int64_t> keep, admitted;
+        int64_t stalls = 0;
+        for (auto& it : todo) {
+            Group* G = group_get(S, it.second->req.n, it.second->req.cell_m);
+            if (!G) { stalls += 1; keep.push_back(it.first); continue; }
+            if (admit(S, *G, it.first, *it.second)) admitted.push_back(it.first);
+            else keep.push_back(it.first);
+        }
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            for (auto it = keep.rbegin(); it != keep.rend(); ++it) S.pending.push_front(*it);
+            for (int64_t t : admitted) S.tickets[t]->state = 1;
+            S.n_admitted += (int64_t)admitted.size();
+            S.n_stalls += stalls;
+        }
+        // ---- issue a chunk of iterations per group (each on its stream) ------
+        std::vector<Group*> active;
+        for (auto& kv : S.groups)
+            if (kv.second->occupied() > 0) active.push_back(kv.second);
+        const int maxb = S.opt.max_pcg_blocks;
+        for (Group* G : active) {
+            Launch L = group_launch(ctx, *G, maxb);
+            Mesh& M = *ctx->meshes[G->mesh_id];
+            G->last_used = now_s();
+            bool any32 = false, any64 = false;
+            for (int b = 0; b < (int)G->t32.size(); ++b) any32 |= G->t32[b] >= 0 && (G->fresh32[b] || G->h32[b].phase != PH_DONE);
+            for (int b = 0; b < (int)G->t64.size(); ++b) any64 |= G->t64[b] >= 0 && (G->fresh64[b] || G->h64[b].phase != PH_DONE);
+            for (int k = 0; k < S.opt.chunk; ++k) {
+                if (any32) {
+                    BatchView<float> V = batch_view<float>(ctx, M, *G->I32, false);
+                    iterate_once<float>(ctx, L, M, *G->I32, V, o1, so1, field_blocks(L, M.view(), G->I32->B));
+                }
+                if (any64) {
+                    BatchView<double> V = batch_view<double>(ctx, M, *G->I64, false);
+                    // FP64 batch: mixed requests finish with the polish options,
+                    // plain FP64 requests share them except for the BEM matrix
+                    iterate_once<double>(ctx, L, M, *G->I64, V, o2, so2, field_blocks(L, M.view(), G->I64->B));
+                }
+            }
+            cudaMemcpyAsync(G->h32.data(), G->I32->st, sizeof(InstState) * G->t32.size(), cudaMemcpyDeviceToHost, G->stream);
+            cudaMemcpyAsync(G->h64.data(), G->I64->st, sizeof(InstState) * G->t64.size(), cudaMemcpyDeviceToHost, G->stream);
+        }
+        // ---- retire and move -----------------------------------------------
+        std::lock_guard<std::mutex> lk(S.mu);
+        for (Group* G : active) {
+            cudaError_t e = cudaStreamSynchronize(G->stream);
+            int errw = 0;
+            cudaMemcpy(&errw, G->err, sizeof errw, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess || errw) {
+                S.worker_rc = e != cudaSuccess ? LBM_E_CUDA : LBM_E_TIMEOUT;
+                S.worker_err = e != cudaSuccess ? cudaGetErrorString(e) : "device wait ran out of time";
+                cudaMemset(G->err, 0, sizeof(int));
+            }
+            std::fill(G->fresh32.begin(), G->fresh32.end(), 0);
+            std::fill(G->fresh64.begin(), G->fresh64.end(), 0);
+            Mesh& M = *ctx->meshes[G->mesh_id];
+            for (int b = 0; b < (int)G->t64.size(); ++b) {
+                const int64_t t = G->t64[b];
+                if (t < 0 || G->h64[b].phase != PH_DONE) continue;
+                complete(S, *G, b, G->h64[b], *S.tickets[t]);
+                G->t64[b] = -1;
+            }
+            for (int b = 0; b < (int)G->t32.size(); ++b) {
+                const int64_t t = G->t32[b];
+                if (t < 0 || G->h32[b].phase != PH_DONE) continue;
+                Ticket& T = *S.tickets[t];
+                if (G->h32[b].status == 4) {   // non-finite: no FP64 phase
+                    fail_ticket(S, T, LBM_E_NAN);
+                    G->t32[b] = -1;
+                    continue;
+                }
+                int d = -1;
+                for (int k = 0; k < (int)G->t64.size(); ++k)
+                    if (G->t64[k] < 0) { d = k; break; }
+                if (d < 0) continue;      // parked until an FP64 slot frees up
+                const VecLayout L32 = vec_layout(M, G->I32->B, 4), L64 = vec_layout(M, G->I64->B, 8);
+                k_slot_reset<<<1, 1, 0, G->stream>>>(G->I64->st, d, PH_INIT);
+                k_slot_move<<<64, 256, 0, G->stream>>>(
+                    (const double*)G->I32->vec, G->I32->st, G->I32->B, b,
+                    (const float*)((const char*)G->I32->vec + L32.U1), (const float*)((const char*)G->I32->vec + L32.U2),
+                    (double*)G->I64->vec, G->I64->B, d, (double*)((char*)G->I64->vec + L64.U1),
+                    (double*)((char*)G->I64->vec + L64.U2), M.N);
+                ctx->launches += 2;
+                set_slot_consts(G->I64, d, G->I32->mats[b], &G->I32->h[3 * b], G->cell, G->stream);
+                T.s32 = G->h32[b];
+                T.has32 = true;
+                G->t64[d] = t;
+                G->fresh64[d] = 1;
+                G->t32[b] = -1;
+                k_slot_reset<<<1, 1, 0, G->stream>>>(G->I32->st, b, PH_DONE);
+                ctx->launches += 1;
+            }
+            cudaStreamSynchronize(G->stream);
+        }
+        (void)o64;
+        S.cv_done.notify_all();
+    }
+    S.cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_serve_opts(lbm_serve_opts* o) {
+    memset(o, 0, sizeof *o);
+    o->slots = 16;
+    o->chunk = 8;
+    o->max_pcg_blocks = 0;
+    o->mem_reserve = 0.05;
+    lbm_default_opts(&o->opt, LBM_MIXED);
+}
+
+int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt) {
+    if (!ctx) return fail(LBM_E_INVALID, "null context");
+    if (ctx->server) return fail(LBM_E_INVALID, "already serving");
+    Server* S = new Server();
+    S->ctx = ctx;
+    if (opt) S->opt = *opt; else lbm_default_serve_opts(&S->opt);
+    if (S->opt.slots < 1 || S->opt.slots > 256 || S->opt.chunk < 1) {
+        delete S;
+        return fail(LBM_E_INVALID, "invalid serve options");
+    }
+    if (S->opt.max_pcg_blocks <= 0) S->opt.max_pcg_blocks = ctx->num_sms / 4 > 0 ? ctx->num_sms / 4 : 1;
+    int rc = check_opts(S->opt.opt);
+    if (rc) { delete S; return rc; }
+    ctx->server = S;
+    S->worker = std::thread(serve_loop, S);
+    return LBM_OK;
+}
+
+int lbm_submit(lbm_ctx* ctx, const lbm_request* req, lbm_ticket* out) {
+    if (!ctx || !ctx->server || !req || !out || !req->m0) return fail(LBM_E_INVALID, "bad argument or not serving");
+    if (req->n < 1 || req->n > 96 || !(req->cell_m > 0) || !(req->mat.Js > 0) ||
+        (req->precision != LBM_FP64 && req->precision != LBM_MIXED))
+        return fail(LBM_E_INVALID, "invalid request");
+    Server& S = *ctx->server;
+    const size_t N = (size_t)(req->n + 1) * (req->n + 1) * (req->n + 1);
+    const double t0 = now_s();
+    std::unique_ptr<Ticket> T(new Ticket());
+    T->req = *req;
+    T->m0.assign(req->m0, req->m0 + 3 * N);
+    T->req.m0 = nullptr;
+    T->t_submit = t0;
+    std::lock_guard<std::mutex> lk(S.mu);
+    const int64_t t = S.next_ticket++;
+    S.tickets[t] = std::move(T);
+    S.pending.push_back(t);
+    S.n_submitted += 1;
+    *out = t;
+    S.cv_work.notify_one();
+    return LBM_OK;
+}
+
+int lbm_poll(lbm_ctx* ctx, lbm_ticket t, lbm_result* res, double* m_out) {
+    if (!ctx || !ctx->server) return fail(LBM_E_INVALID, "not serving");
+    Server& S = *ctx->server;
+    std::lock_guard<std::mutex> lk(S.mu);
+    auto it = S.tickets.find(t);
+    if (it == S.tickets.end()) return fail(LBM_E_INVALID, "unknown ticket");
+    if (S.worker_rc != LBM_OK) return fail(S.worker_rc, "serving failed: %s", S.worker_err.c_str());
+    const Ticket& T = *it->second;
+    if (T.state != 2) return LBM_E_PENDING;
+    if (res) *res = T.res;
+    if (m_out && !T.m_out.empty()) memcpy(m_out, T.m_out.data(), sizeof(double) * T.m_out.size());
+    return LBM_OK;
+}
+
+int lbm_wait(lbm_ctx* ctx, lbm_ticket t, double timeout_s, lbm_result* res, double* m_out) {
+    if (!ctx || !ctx->server) return fail(LBM_E_INVALID, "not serving");
+    Server& S = *ctx->server;
+    const double t_end = now_s() + timeout_s;
+    for (;;) {
+        int rc = lbm_poll(ctx, t, res, m_out);
+        if (rc != LBM_E_PENDING) return rc;
+        if (now_s() > t_end) return fail(LBM_E_TIMEOUT, "request %lld not finished", (long long)t);
+        std::unique_lock<std::mutex> lk(S.mu);
+        S.cv_done.wait_for(lk, std::chrono::milliseconds(5));
+    }
+}
+
+int lbm_serve_stats(lbm_ctx* ctx, int64_t stats[8]) {
+    if (!ctx || !ctx->server || !stats) return fail(LBM_E_INVALID, "not serving");
+    Server& S = *ctx->server;
+    std::lock_guard<std::mutex> lk(S.mu);
+    int64_t act = 0;
+    for (auto& kv : S.groups) act += kv.second->occupied();
+    stats[0] = S.n_submitted;
+    stats[1] = S.n_admitted;
+    stats[2] = S.n_completed;
+    stats[3] = (int64_t)S.pending.size();
+    stats[4] = act;
+    stats[5] = (int64_t)S.groups.size();
+    stats[6] = S.n_stalls;
+    stats[7] = S.n_evicted;
+    return LBM_OK;
+}
+
+int lbm_serve_stop(lbm_ctx* ctx) {
+    if (!ctx || !ctx->server) return fail(LBM_E_INVALID, "not serving");
+    Server* S = ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (auto& kv : S->groups) group_free(ctx, kv.second);
+    S->groups.clear();
+    ctx->server = nullptr;
+    delete S;
     return LBM_OK;
 }
 

@@ -72,6 +72,7 @@ struct Launch {
     int64_t* launches; // host counter of kernel launches
     unsigned long long* sweeps;  // device counters [4]: batched PCG iterations per stage and precision
     double* fin;                 // device scratch for grid reductions (>= 4 * 512 doubles)
+    int max_blocks;              // cap on the cooperative PCG grid (0: one block per SM)
 };
 
 template <typename T>
@@ -93,6 +94,14 @@ template <typename T>
 void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, double* staged_h,
                   double* staged_u);
 void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0);
+
+// ---- tensor-core BEM products (tc_gemm.cu) ------------------------------------------
+int tc_ld(int nb);
+size_t tc_scratch_floats(int nb, int B, int num_sms);
+void tc_prepare(const Launch& L, const float* B32, int nb, float* A, float* AT);
+template <typename T>
+int bem_product_tc(const Launch& L, int nb, const float* A32, const float* A32T, const T* ub_in, T* ub_out, int B,
+                   float* scratch);
 int field_blocks(const Launch& L, const MeshView& M, int B);
 size_t pcg_part_elems(int num_sms, int B);
 

@@ -633,7 +633,8 @@ static cudaError_t launch_pcg(const Launch& L, const MeshView& M, PcgArgs<T>& a,
     void* args[] = {&a};
     if (SINGLE) return cudaLaunchKernel((void*)k_pcg<T, SINGLE, VEC>, dim3(1), dim3(bd), args, smem, L.stream);
     int nblk = (M.N + RB - 1) / RB;
-    const int maxblk = occ * L.num_sms;
+    int maxblk = occ * L.num_sms;
+    if (L.max_blocks > 0 && L.max_blocks < maxblk) maxblk = L.max_blocks;
     if (nblk > maxblk) nblk = maxblk;
     cudaMemsetAsync(L.bar, 0, sizeof(unsigned), L.stream);
     return cudaLaunchCooperativeKernel((void*)k_pcg<T, SINGLE, VEC>, dim3(nblk), dim3(bd), args, smem, L.stream);

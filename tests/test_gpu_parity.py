@@ -255,3 +255,61 @@ def test_uniform_state_zero_exchange_on_gpu(ctx):
     assert res[0]["energy"][0] == 0.0
     inst.destroy()
     ctx.mesh_destroy(mesh)
+
+
+def _golden(name):
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", name)))
+
+
+@pytest.mark.parametrize("prec", [lbm.LBM_FP64, lbm.LBM_MIXED])
+def test_sweep_config2_vs_oracle(ctx, prec):
+    """40 nm cube, axis tilted 1 degree, +8 -> -8 T in 0.1 T steps (161 warm-started
+    points): per-point energies within 1e-6 relative of the oracle's sweep and the
+    same switching field (within one field step)."""
+    from oracle.micromag import MU0
+    from synth.inputs import sweep_case
+    g = _golden("sweep_n20.json")
+    c = sweep_case(20, seed=2)
+    assert np.allclose(c["axis"], g["axis"], atol=0) and np.allclose(c["fields"], g["fields"], atol=0)
+    mesh = ctx.mesh_cube(2e-9, 20)
+    inst = ctx.instance_create(mesh, 1, prec)
+    inst.set_material(JS_T, A_JM, K1_JM3, c["axis"])
+    inst.set_m(c["m0"])
+    mpar, energy, res = inst.hysteresis(c["direction"], c["fields"], lbm.default_opts(prec))
+    inst.destroy()
+    ctx.mesh_destroy(mesh)
+    assert all(r["status"] == lbm.LBM_OK for r in res)
+    Kd = JS_T ** 2 / (2 * MU0)
+    scale = np.maximum(np.abs(g["energy"]), Kd * (20 * 2e-9) ** 3)
+    assert np.max(np.abs(energy[:, 0] - g["energy"]) / scale) < 1e-6
+    f = np.array(c["fields"])
+    def switch(mp):
+        return [f[k] for k in range(1, len(f)) if np.sign(mp[k]) != np.sign(mp[k - 1])]
+    sw_gpu, sw_ora = switch(mpar[:, 0]), switch(np.array(g["m_par"]))
+    assert len(sw_gpu) == len(sw_ora) == 1
+    assert abs(sw_gpu[0] - sw_ora[0]) <= 0.1 + 1e-9
+
+
+def test_batched_config4_vs_oracle(ctx):
+    """The benchmark's workload in its launch configuration (64 instances on the
+    30^3-cell cube, mixed precision): every instance converges and its energy is
+    within 1e-6 relative of the oracle's (golden, written by the oracle)."""
+    from oracle.micromag import MU0
+    from synth.inputs import batched_case
+    g = _golden("batched_n30.json")["results"]
+    insts = batched_case(30, 64, seed=4)
+    mesh = ctx.mesh_cube(2e-9, 30)
+    inst = ctx.instance_create(mesh, 64, lbm.LBM_MIXED)
+    inst.set_material(JS_T, A_JM, K1_JM3, np.stack([i.axis for i in insts]))
+    inst.set_field(np.stack([i.h_ext for i in insts]))
+    inst.set_m(np.stack([i.m0 for i in insts]))
+    res = inst.minimise(lbm.default_opts(lbm.LBM_MIXED))
+    inst.destroy()
+    ctx.mesh_destroy(mesh)
+    Kd = JS_T ** 2 / (2 * MU0)
+    for b, (r, o) in enumerate(zip(res, g)):
+        assert r["status"] == lbm.LBM_OK and r["torque"] < 1e-6, b
+        scale = max(abs(o["E"]), Kd * (30 * 2e-9) ** 3)
+        assert abs(r["energy"][4] - o["E"]) / scale < 1e-6, (b, r["energy"][4], o["E"])
