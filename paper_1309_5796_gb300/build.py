@@ -71,7 +71,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
-        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcuda"])
+        run([nvcc, *ARCH, "-shared", "-o", LIB, *objs])
     return LIB
 
 
