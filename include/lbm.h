@@ -194,6 +194,36 @@ typedef struct {
 int lbm_profile_enable(lbm_ctx* ctx, int32_t on);
 int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);
 
+/* ---- evaluation without device allocation ---------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that must not
+ * allocate device memory while they run -- for example a host application that
+ * reserves all of its GPU memory at start-up, or a time-critical loop in which
+ * touching the CUDA allocator is not allowed.  It computes what lbm_evaluate
+ * computes for one instance in FP64 (energy terms, effective field, forward
+ * potentials at the given m) but keeps every intermediate vector in one
+ * fixed device array built into the library (about 4.9 MB on every device that
+ * loads it, held until the process exits).  It calls no cudaMalloc or cudaFree.
+ *
+ *   mesh      a cube from lbm_mesh_cube with at most 16384 nodes and 4096
+ *             surface nodes (n <= 24 cells per side); larger meshes are
+ *             rejected with LBM_E_INVALID and a message
+ *   mat, h_ext, opt   as for an instance (opt may be NULL: FP64 defaults)
+ *   d_m       DEVICE pointer, [N*3] unit vectors (node-major)
+ *   d_h       DEVICE pointer or NULL, [N*3] mu0*h_eff in tesla
+ *   d_u       DEVICE pointer or NULL, [2*N] potentials u1, u2 in metres
+ *   d_energy  DEVICE pointer or NULL, [5] exchange, anisotropy, Zeeman,
+ *             stray field, total (J)
+ * The work is queued on the context's stream and the call returns without
+ * waiting for it.  The first call on a device looks up the device address of
+ * the fixed array (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array, and each call overwrites it
+ * (the parts that must start from zero -- the potentials, counters and the
+ * barrier word -- are cleared by every call): calls whose work overlaps on the
+ * GPU, e.g. from two streams or two contexts on one device, race. */
+int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_material* mat, const double h_ext[3],
+                         const lbm_solve_opts* opt, const double* d_m, double* d_h, double* d_u,
+                         double* d_energy);
+
 /* ---- serving: continuous batching of minimisation requests ---------------------
  * A worker thread of the context owns the device while serving.  Requests
  * (a cube size, material, applied field and initial m) are admitted into free

@@ -99,6 +99,8 @@ SIGNATURES = [
     ("lbm_set_m_device", C.c_int, [_P, _I64, C.c_void_p]),
     ("lbm_profile_enable", C.c_int, [_P, C.c_int32]),
     ("lbm_profile_read", C.c_int, [_P, C.POINTER(ProfileStats), C.c_int32]),
+    ("lbm_evaluate_noalloc", C.c_int, [_P, _I64, C.POINTER(Material), _DP, C.POINTER(SolveOpts),
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
     ("lbm_serve_start", C.c_int, [_P, C.POINTER(ServeOpts)]),
     ("lbm_submit", C.c_int, [_P, C.POINTER(Request), C.POINTER(_I64)]),
@@ -217,6 +219,20 @@ class Context:
         h = _I64()
         _check(lib().lbm_instance_create(self._h, mesh, batch, precision, C.byref(h)))
         return Instance(self, h.value, mesh, batch, precision)
+
+    def evaluate_noalloc(self, mesh: int, Js, A, K1, axis, h_ext, d_m: int, d_h: int = 0, d_u: int = 0,
+                         d_energy: int = 0, opts: SolveOpts | None = None):
+        """lbm_evaluate_noalloc with device pointers (e.g. torch tensors' data_ptr());
+        queued on the context's stream."""
+        mat = Material()
+        mat.Js, mat.A, mat.K1 = Js, A, K1
+        for d in range(3):
+            mat.axis[d] = axis[d]
+        h = np.ascontiguousarray(np.asarray(h_ext, np.float64))
+        _check(lib().lbm_evaluate_noalloc(self._h, mesh, C.byref(mat), _dptr(h),
+                                          C.byref(opts) if opts else None, C.c_void_p(d_m),
+                                          C.c_void_p(d_h or None), C.c_void_p(d_u or None),
+                                          C.c_void_p(d_energy or None)))
 
     # -- serving (continuous batching) ---------------------------------------
     def serve_start(self, **kw):

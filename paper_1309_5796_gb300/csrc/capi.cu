@@ -990,6 +990,166 @@ int lbm_hysteresis(lbm_ctx* ctx, lbm_inst inst, const double dir[3], const doubl
 }  // extern "C"
 
 // ============================================================================
+// Field evaluation without device allocation.
+// ============================================================================
+// Callers that cannot allocate device memory once they are running -- a host
+// application that hands the library a fixed memory budget at start-up, code
+// that runs while the CUDA allocator must not be touched (real-time loops, or a
+// process whose allocations are all made up front) -- get one entry point that
+// evaluates the energy, effective field and potentials of one magnetisation
+// using only a fixed device array compiled into this library.
+namespace {
+
+constexpr size_t NOALLOC_MAX_NODES = 16384;     // cubes up to 24^3 cells (15 625 nodes)
+constexpr size_t NOALLOC_MAX_SURFACE = 4096;    // surface nodes (24^3 cells: 3 458)
+constexpr size_t NOALLOC_PART = 16384;          // per-block partial sums (doubles)
+constexpr size_t NOALLOC_FIN = 4096;            // grid-reduction results (doubles)
+// doubles: m, grad phi (2 x 3N each), field (3N), U1, U2, r, z, p, q (2N each),
+// surface in/out (2 nb each), column-split partials (32 nb), partials, fin,
+// plus state, constants and the barrier/error words (a few hundred bytes)
+constexpr size_t NOALLOC_DOUBLES = 27 * NOALLOC_MAX_NODES + 36 * NOALLOC_MAX_SURFACE + NOALLOC_PART + NOALLOC_FIN + 1024;
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {nullptr};   // device address of the array, per device
+
+__global__ void k_noalloc_setup(InstState* st, InstConst* ic, InstConst c) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    memset(st, 0, sizeof(InstState));
+    st->phase = PH_INIT;
+    st->status = 3;
+    st->cur = 0;
+    *ic = c;
+}
+
+__global__ void k_noalloc_energy(const InstState* st, const InstConst* ic, double* e) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < 4; ++k) e[k] = st->terms[k] * ic->Eunit;
+    e[4] = st->E * ic->Eunit;
+}
+
+}  // namespace
+
+extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_material* mat, const double h_ext[3],
+                                    const lbm_solve_opts* opt, const double* d_m, double* d_h, double* d_u,
+                                    double* d_energy) {
+    Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
+    if (!M || !mat || !h_ext || !d_m) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: bad argument");
+    if ((size_t)M->N > NOALLOC_MAX_NODES || (size_t)M->nb > NOALLOC_MAX_SURFACE)
+        return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: mesh of %d nodes / %d surface nodes exceeds the "
+                    "static scratch (%zu nodes / %zu surface nodes)", M->N, M->nb, NOALLOC_MAX_NODES,
+                    NOALLOC_MAX_SURFACE);
+    if (!(mat->Js > 0)) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: Js must be positive");
+    lbm_solve_opts o;
+    if (opt) o = *opt; else lbm_default_opts(&o, LBM_FP64);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->device < 0 || ctx->device >= 64) return fail(LBM_E_INVALID, "device index out of range");
+    double* base;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[ctx->device]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(LBM_E_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[ctx->device] = (double*)p;
+        }
+        base = g_noalloc_ptr[ctx->device];
+    }
+    const size_t N = M->N, nb = M->nb;
+    // carve the array (offsets in doubles, each region 256-byte aligned)
+    size_t off = 0;
+    auto take = [&](size_t n) { double* p = base + off; off += (n + 31) & ~(size_t)31; return p; };
+    double* m = take(6 * N);
+    double* g = take(6 * N);
+    double* hout = take(3 * N);
+    double* U1 = take(2 * N);
+    double* U2 = take(2 * N);
+    double* r = take(2 * N);
+    double* z = take(2 * N);
+    double* p = take(2 * N);
+    double* q = take(2 * N);
+    double* ubi = take(2 * nb);
+    double* ubo = take(2 * nb);
+    double* bpart = take(32 * nb);
+    double* part = take(NOALLOC_PART);
+    double* fin = take(NOALLOC_FIN);
+    InstState* st = (InstState*)take((sizeof(InstState) + 7) / 8);
+    InstConst* ic = (InstConst*)take((sizeof(InstConst) + 7) / 8);
+    unsigned* bar = (unsigned*)take(1);
+    int* err = (int*)take(1);
+    unsigned long long* sweeps = (unsigned long long*)take(4);
+    if (off > NOALLOC_DOUBLES) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: static scratch too small");
+    const size_t need_part = (size_t)4 * ctx->num_sms * NQ > pcg_part_elems(ctx->num_sms, 1)
+                                 ? (size_t)4 * ctx->num_sms * NQ : pcg_part_elems(ctx->num_sms, 1);
+    if (need_part > NOALLOC_PART) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: too many SMs for the static scratch");
+    cudaStream_t s = ctx->stream;
+    // what must start at zero: the potentials (cold start), barrier, error word, counters
+    CK(cudaMemsetAsync(U1, 0, sizeof(double) * 2 * N, s));
+    CK(cudaMemsetAsync(U2, 0, sizeof(double) * 2 * N, s));
+    CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(sweeps, 0, 4 * sizeof(unsigned long long), s));
+    CK(cudaMemcpyAsync(m, d_m, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    const double Kd = mat->Js * mat->Js / (2.0 * MU0);
+    double an = sqrt(mat->axis[0] * mat->axis[0] + mat->axis[1] * mat->axis[1] + mat->axis[2] * mat->axis[2]);
+    if (!(an > 0)) an = 1.0;
+    InstConst c;
+    c.lam = mat->A / (Kd * M->cell * M->cell);
+    c.Q = mat->K1 / Kd;
+    for (int d = 0; d < 3; ++d) {
+        c.a[d] = mat->axis[d] / an;
+        c.hz[d] = h_ext[d] / mat->Js;
+    }
+    c.Eunit = Kd * M->cell * M->cell * M->cell;
+    c.Js = mat->Js;
+    k_noalloc_setup<<<1, 1, 0, s>>>(st, ic, c);
+    ctx->launches += 1;
+    BatchView<double> V;
+    V.B = 1;
+    V.m = m;
+    V.H = g;
+    V.hout = hout;
+    V.U1 = U1;
+    V.U2 = U2;
+    V.r = r;
+    V.z = z;
+    V.p = p;
+    V.q = q;
+    V.ub_in = ubi;
+    V.ub_out = ubo;
+    V.bem_part = bpart;
+    V.part = part;
+    V.st = st;
+    V.ic = ic;
+    Launch L{s, ctx->num_sms, bar, err, &ctx->launches, sweeps, fin, 0};
+    const MeshView mv = M->view();
+    lbm_solve_opts oo = o;
+    oo.max_iter = 0;
+    const StepOpts so = step_opts(oo);
+    trial_update<double>(L, mv, V);
+    if (o.demag) {
+        int e = pcg_solve<double>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, nullptr);
+        if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
+        bem_product<double>(L, mv, V, false);
+        e = pcg_solve<double>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, nullptr);
+        if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    }
+    field_eval<double>(L, mv, V, o.demag);
+    decide<double>(L, mv, V, so, field_blocks(L, mv, 1));
+    if (d_h || d_u) unpack_field<double>(L, mv, V, d_h, d_u);
+    if (d_energy) {
+        k_noalloc_energy<<<1, 1, 0, s>>>(st, ic, d_energy);
+        ctx->launches += 1;
+    }
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// ============================================================================
 // Serving: continuous batching of minimisation requests.
 // ============================================================================
 namespace {
