@@ -34,11 +34,13 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def hat_double_layer(x: np.ndarray, tri: np.ndarray) -> np.ndarray:
+def hat_double_layer(x: np.ndarray, tri: np.ndarray, exclude: np.ndarray | None = None) -> np.ndarray:
     """I[p, t, k] = int_t phi_k(y) (x_p - y).n_t / |x_p - y|^3 dS_y.
 
     x: (P, 3) targets; tri: (T, 3, 3) vertices ordered counter-clockwise seen
-    from the outside (normal (y2-y1) x (y3-y1) outward)."""
+    from the outside (normal (y2-y1) x (y3-y1) outward).  exclude: optional
+    (P, T) mask of pairs known to be coplanar (x_p a vertex of t), which give
+    0 whatever rounding does to h."""
     x = np.asarray(x, dtype=np.float64)[:, None, :]          # (P, 1, 3)
     y = np.asarray(tri, dtype=np.float64)[None, :, :, :]      # (1, T, 3, 3)
     y1, y2, y3 = y[..., 0, :], y[..., 1, :], y[..., 2, :]
@@ -58,6 +60,8 @@ def hat_double_layer(x: np.ndarray, tri: np.ndarray) -> np.ndarray:
     ys = [y1, y2, y3]
     foot = x + h[..., None] * nrm                             # (P, T, 3)
     coplanar = h == 0.0
+    if exclude is not None:
+        coplanar = coplanar | exclude
     hs = np.where(coplanar, 1.0, h)                           # avoid 0/0 in unused logs
     edge_sum = np.zeros_like(foot)
     for k in range(3):
@@ -115,6 +119,65 @@ def bem_matrix(nodes: np.ndarray, n: int, bnd: np.ndarray, tris: np.ndarray,
     for s in range(0, rows.size, chunk):
         r = rows[s:s + chunk]
         I = hat_double_layer(nodes[bnd[r]].astype(np.float64), txyz)   # (p, F, 3)
+        out[s:s + chunk] = (S.T @ I.reshape(r.size, -1).T).T / (4.0 * math.pi)
+    out[np.arange(rows.size), rows] += omega / (4.0 * math.pi) - 1.0
+    return out
+
+
+def interior_solid_angle(xyz: np.ndarray, bnd: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """Interior solid angle of a closed triangulated surface at its vertices, by
+    Girard's theorem: the cone of the incident triangles cuts a spherical
+    polygon out of the unit sphere around x_i, whose area is the sum of its
+    angles minus (m - 2) pi.  Its angle at fan edge u_b is the interior
+    dihedral angle between the two incident triangles that share the edge,
+    atan2(u_b . (w_a x w_c), w_a . w_c) in [0, 2 pi), where w_a, w_c are the
+    neighbouring fan edges projected orthogonally to u_b and (x_i, a, b),
+    (x_i, b, c) are consecutive triangles in outward counter-clockwise order.
+    2 pi on a flat face, pi on a straight edge, pi/2 at a box corner."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    out = np.empty(bnd.size)
+    nxt = {}
+    for t in np.asarray(tris):
+        for k in range(3):
+            nxt.setdefault(int(t[k]), {})[int(t[(k + 1) % 3])] = int(t[(k + 2) % 3])
+    for q, i in enumerate(np.asarray(bnd)):
+        fan = nxt[int(i)]                        # a -> b for every triangle (i, a, b)
+        m = len(fan)
+        x = xyz[i]
+        total = 0.0
+        for a, b in fan.items():
+            c = fan[b]                           # the next triangle (i, b, c)
+            u = xyz[b] - x
+            u = u / np.linalg.norm(u)
+            wa = xyz[a] - x
+            wa = wa - np.dot(wa, u) * u
+            wc = xyz[c] - x
+            wc = wc - np.dot(wc, u) * u
+            th = math.atan2(float(np.dot(u, np.cross(wa, wc))), float(np.dot(wa, wc)))
+            total += th % (2.0 * math.pi)
+        out[q] = total - (m - 2) * math.pi
+    return out
+
+
+def bem_matrix_general(nodes: np.ndarray, bnd: np.ndarray, tris: np.ndarray, rows=None,
+                       chunk: int = 128) -> np.ndarray:
+    """Dense B (len(rows) x nb) on any closed triangulated surface: as
+    bem_matrix, with the interior solid angles from interior_solid_angle and
+    the triangles incident to the collocation node excluded explicitly."""
+    nb = bnd.size
+    if rows is None:
+        rows = np.arange(nb)
+    rows = np.asarray(rows)
+    nodes = np.asarray(nodes, dtype=np.float64)
+    S = incidence(tris, bnd, nodes.shape[0])
+    txyz = nodes[tris]
+    omega = interior_solid_angle(nodes, bnd[rows], tris)
+    out = np.empty((rows.size, nb))
+    for s in range(0, rows.size, chunk):
+        r = rows[s:s + chunk]
+        ids = bnd[r]
+        excl = np.any(tris[None, :, :] == ids[:, None, None], axis=2)
+        I = hat_double_layer(nodes[ids], txyz, exclude=excl)
         out[s:s + chunk] = (S.T @ I.reshape(r.size, -1).T).T / (4.0 * math.pi)
     out[np.arange(rows.size), rows] += omega / (4.0 * math.pi) - 1.0
     return out

@@ -204,3 +204,134 @@ def cube_mesh(n: int, cell: float = 2e-9) -> CubeMesh:
     ops = assemble_int(nodes, tets)
     return CubeMesh(n=n, cell=cell, nodes=nodes, tets=tets, ops=ops,
                     bnd=boundary_nodes(nodes, n), tris=boundary_triangles(nodes, tets, n))
+
+
+# ---- general tetrahedral meshes (FP64 assembly) -----------------------------------------
+#
+# The same P1 operators on an arbitrary conforming tetrahedral mesh, assembled
+# in FP64 from the definitions above: with the cofactors c_a of a tetrahedron
+# and det = 6 x its signed volume, grad phi_a = c_a / det and vol = |det|/6, so
+#   K_ab (element)        = vol grad phi_a . grad phi_b = c_a . c_b / (6 |det|)
+#   (vol/4) grad phi_a    = sgn(det) c_a / 24
+#   V_a (element share)   = |det| / 24.
+# The surface is the set of faces that belong to one tetrahedron only.
+
+@dataclass
+class FloatOperators:
+    """FP64 FEM operators (SI units) on the element-adjacency CSR pattern."""
+    indptr: np.ndarray     # (N+1,) int64
+    indices: np.ndarray    # (nnz,) int64
+    K: np.ndarray          # (nnz,)   K_ij (m)
+    G: np.ndarray          # (nnz, 3) G_ij (m^2)
+    Gt: np.ndarray         # (nnz, 3) G_ji at the position of (i, j)
+    V: np.ndarray          # (N,)     V_i (m^3)
+
+
+def assemble_fp64(xyz: np.ndarray, tets: np.ndarray) -> FloatOperators:
+    """K, G, V of the P1 space on any conforming tetrahedral mesh (FP64)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    tets = np.asarray(tets, dtype=np.int64)
+    N = xyz.shape[0]
+    c, det = cofactors(xyz, tets)
+    if np.any(det == 0.0):
+        raise ValueError("degenerate tetrahedron")
+    rows = np.repeat(tets, 4, axis=1).ravel()
+    cols = np.tile(tets, (1, 4)).ravel()
+    kloc = (np.einsum("tad,tbd->tab", c, c) / (6.0 * np.abs(det))[:, None, None]).ravel()
+    gloc = np.repeat(c * (np.sign(det) / 24.0)[:, None, None], 4, axis=1).reshape(-1, 3)
+    Km = sp.coo_matrix((kloc, (rows, cols)), shape=(N, N)).tocsr()
+    Km.sum_duplicates()
+    Km.sort_indices()
+    G = np.empty((Km.nnz, 3))
+    Gt = np.empty((Km.nnz, 3))
+    for d in range(3):
+        Gd = sp.coo_matrix((gloc[:, d], (rows, cols)), shape=(N, N)).tocsr()
+        Gd.sum_duplicates()
+        Gd.sort_indices()
+        assert np.array_equal(Gd.indices, Km.indices)
+        G[:, d] = Gd.data
+        GdT = Gd.T.tocsr()
+        GdT.sum_duplicates()
+        GdT.sort_indices()
+        assert np.array_equal(GdT.indices, Km.indices)
+        Gt[:, d] = GdT.data
+    V = np.bincount(tets.ravel(), weights=np.repeat(np.abs(det) / 24.0, 4), minlength=N)
+    return FloatOperators(Km.indptr.astype(np.int64), Km.indices.astype(np.int64), Km.data.copy(), G, Gt, V)
+
+
+def surface_faces(xyz: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    """Outward-oriented surface triangles (F, 3): the faces of exactly one
+    tetrahedron; normal (b-a) x (c-a) away from that tetrahedron's fourth
+    vertex.  Canonical form as in boundary_triangles (smallest id first, cyclic
+    order kept, rows sorted).  Raises on faces shared by more than two."""
+    tets = np.asarray(tets, dtype=np.int64)
+    faces, opp = [], []
+    for o in range(4):
+        faces.append(tets[:, [v for v in range(4) if v != o]])
+        opp.append(tets[:, o])
+    faces = np.concatenate(faces)
+    opp = np.concatenate(opp)
+    key = np.sort(faces, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    if np.any(cnt > 2):
+        raise ValueError("non-manifold mesh: a face belongs to more than two tetrahedra")
+    on = cnt[inv.ravel()] == 1
+    F, O = faces[on].copy(), opp[on]
+    X = xyz[F]
+    nrm = np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0])
+    flip = np.einsum("ij,ij->i", nrm, xyz[O] - X[:, 0]) > 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    r = np.argmin(F, axis=1)
+    F = np.stack([F[np.arange(len(F)), (r + s) % 3] for s in range(3)], axis=1)
+    order = np.lexsort((F[:, 2], F[:, 1], F[:, 0]))
+    return F[order]
+
+
+def length_unit(xyz: np.ndarray, tets: np.ndarray) -> float:
+    """The mesh's length unit L = (mean |det|)^(1/3) = (6 x mean volume)^(1/3):
+    the cell edge for a 6-tetrahedra cube split.  Reduced quantities use it
+    the way the cube meshes use their cell edge."""
+    _, det = cofactors(np.asarray(xyz, dtype=np.float64), np.asarray(tets, dtype=np.int64))
+    return float(np.cbrt(np.mean(np.abs(det))))
+
+
+@dataclass
+class TetMesh:
+    """A general mesh with the interface of CubeMesh (n = 0; cell = L)."""
+    xyz_m: np.ndarray           # (N, 3) metres
+    tets: np.ndarray            # (T, 4)
+    ops: FloatOperators
+    bnd: np.ndarray             # (nb,) surface node ids, ascending
+    tris: np.ndarray            # (F, 3) outward surface triangles
+    cell: float                 # length unit L (m)
+    n: int = 0
+
+    @property
+    def N(self) -> int:
+        return self.xyz_m.shape[0]
+
+    @property
+    def nodes(self) -> np.ndarray:
+        """Coordinates in units of L (the BEM operator is scale free)."""
+        return self.xyz_m / self.cell
+
+    def xyz(self) -> np.ndarray:
+        return self.xyz_m
+
+    def stiffness(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.ops.K, self.ops.indices, self.ops.indptr), shape=(self.N, self.N))
+
+    def coupling(self):
+        return [sp.csr_matrix((self.ops.G[:, d], self.ops.indices, self.ops.indptr), shape=(self.N, self.N))
+                for d in range(3)]
+
+    def volumes(self) -> np.ndarray:
+        return self.ops.V
+
+
+def tet_mesh(xyz: np.ndarray, tets: np.ndarray) -> TetMesh:
+    xyz = np.asarray(xyz, dtype=np.float64)
+    tets = np.asarray(tets, dtype=np.int64)
+    tris = surface_faces(xyz, tets)
+    return TetMesh(xyz_m=xyz, tets=tets, ops=assemble_fp64(xyz, tets), bnd=np.unique(tris),
+                   tris=tris, cell=length_unit(xyz, tets))

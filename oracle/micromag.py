@@ -33,6 +33,9 @@ solution of the linear systems), not the iterative solver of the GPU path.
 Minimiser units (reading of "grad phi_t", Sec. 2.1-2.3): the Euclidean gradient
 of the discrete energy in the fixed unit E0 = Kd h^3, Kd = Js^2/(2 mu0):
 grad_i phi = (dE/dm_i) / E0 = -(Js/mu0) V_i (mu0 h_i) / E0.
+General tetrahedral meshes (mesh_problem) use the same formulas with the FP64
+operators of oracle.mesh.tet_mesh, the general BEM, and h replaced by the
+mesh's length unit L.
 """
 from __future__ import annotations
 
@@ -43,8 +46,8 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .bem import bem_matrix
-from .mesh import CubeMesh, cube_mesh
+from .bem import bem_matrix, bem_matrix_general
+from .mesh import CubeMesh, TetMesh, cube_mesh, tet_mesh
 
 MU0 = 4e-7 * math.pi
 
@@ -67,6 +70,8 @@ class CubeProblem:
     def __init__(self, n: int, Js: float, A: float, K1: float, axis, cell: float = 2e-9,
                  demag: bool = True, mesh: CubeMesh | None = None, B: np.ndarray | None = None):
         self.mesh = mesh if mesh is not None else cube_mesh(n, cell)
+        if mesh is not None:
+            cell = mesh.cell            # a general mesh carries its own length unit
         self.n, self.cell = n, cell
         self.Js, self.A, self.K1 = Js, A, K1
         self.axis = np.asarray(axis, dtype=np.float64)
@@ -85,7 +90,12 @@ class CubeProblem:
         isb[self.bnd] = True
         self.interior = np.nonzero(~isb)[0]
         if demag:
-            self.B = B if B is not None else bem_matrix(self.mesh.nodes, n, self.bnd, self.mesh.tris)
+            if B is not None:
+                self.B = B
+            elif self.mesh.n == 0:
+                self.B = bem_matrix_general(self.mesh.nodes, self.bnd, self.mesh.tris)
+            else:
+                self.B = bem_matrix(self.mesh.nodes, n, self.bnd, self.mesh.tris)
             # Neumann problem: fix node 0, solve the reduced SPD system exactly
             self.lu_neu = spla.splu(self.K[1:, 1:].tocsc())
             Kd_ = self.Kcsr
@@ -161,3 +171,9 @@ class CubeProblem:
 
     def mean_m(self, m: np.ndarray) -> np.ndarray:
         return (self.V[:, None] * m).sum(axis=0) / self.V.sum()
+
+
+def mesh_problem(xyz, tets, Js: float, A: float, K1: float, axis, demag: bool = True) -> CubeProblem:
+    """The same problem on a general tetrahedral mesh (coordinates in metres)."""
+    mesh = tet_mesh(xyz, tets)
+    return CubeProblem(0, Js, A, K1, axis, mesh=mesh, demag=demag)
