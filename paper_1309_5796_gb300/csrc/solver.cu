@@ -345,16 +345,29 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     double* part = A.V.part;
     unsigned epoch = 0;
 
-    // partials of this block -> totals in `out` (a grid reduction unless SINGLE)
+    // partials of this block -> totals in `out` (a grid reduction unless SINGLE).
+    // Few partials (small batches): one barrier, then every block sums all of
+    // them; the two halves of `part` alternate so that a block writing the next
+    // partials never overwrites ones another block is still reading.  Many
+    // partials: the two-level reduction (one warp per total, two barriers).
+    const bool few = (size_t)gridDim.x * C * 4 <= (size_t)8 * bd;
+    unsigned red_idx = 0;
     auto reduce = [&](auto& vals, int q0) -> bool {
         constexpr int NQV = sizeof(vals) / sizeof(vals[0]);
         block_reduce_cols<NQV, VEC>(vals, scratch, out, C, G, RB);
         if constexpr (SINGLE) {
             return true;
         } else {
+            double* pr = part + (size_t)(red_idx & 1u) * gridDim.x * C * 4;
+            red_idx += 1;
             if (tid < C)
-                for (int k = 0; k < NQV; ++k) part[((size_t)blockIdx.x * C + tid) * 4 + q0 + k] = out[k * C + tid];
-            return grid_reduce<NQV>(part, q0, C, A.fin, out, A.bar, epoch, A.err);
+                for (int k = 0; k < NQV; ++k) pr[((size_t)blockIdx.x * C + tid) * 4 + q0 + k] = out[k * C + tid];
+            if (few) {
+                if (!grid_sync(A.bar, gridDim.x, epoch, A.err)) return false;
+                cross_reduce_cols<NQV, VEC>(pr, q0, gridDim.x, C, G, RB, scratch, out);
+                return true;
+            }
+            return grid_reduce<NQV>(pr, q0, C, A.fin, out, A.bar, epoch, A.err);
         }
     };
 
@@ -659,6 +672,27 @@ int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mod
 // Columns 0..B-1 of the [nb][2B] surface arrays belong to the forward chain,
 // columns B..2B-1 to the adjoint chain.
 
+// Per-lane accumulator of a matrix-vector product in the matrix precision: a
+// compensated (Kahan) sum for FP32 matrices, so that the product stays bound by
+// memory bandwidth rather than by GB300's FP64 units, and a plain FP64 sum for
+// FP64 matrices.
+template <typename TA> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float x) {
+        const float y = __fmaf_rn(a, x, -c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // y[row*inc] = sum_j A[row][j] x[j*inc]; one warp per row
 template <typename TA, typename T>
 __global__ void k_gemv(const TA* __restrict__ A, const T* __restrict__ x, T* __restrict__ y, int nb, int inc) {
@@ -666,10 +700,11 @@ __global__ void k_gemv(const TA* __restrict__ A, const T* __restrict__ x, T* __r
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int row = warp; row < nb; row += nw) {
         const TA* a = A + (size_t)row * nb;
-        double acc = 0.0;
-        for (int j = lane; j < nb; j += 32) acc += (double)a[j] * (double)x[(size_t)j * inc];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) y[(size_t)row * inc] = T(acc);
+        DotAcc<TA> acc;
+        for (int j = lane; j < nb; j += 32) acc.add(a[j], TA(x[(size_t)j * inc]));
+        double v = acc.value();
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) y[(size_t)row * inc] = T(v);
     }
 }
 
@@ -680,10 +715,10 @@ __global__ void k_gemv_t_part(const TA* __restrict__ A, const T* __restrict__ x,
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i0 = blockIdx.y * rows_per_chunk, i1 = min(nb, i0 + rows_per_chunk);
     if (j >= nb) return;
-    double acc = 0.0;
+    DotAcc<TA> acc;
 #pragma unroll 4
-    for (int i = i0; i < i1; ++i) acc += (double)A[(size_t)i * nb + j] * (double)x[(size_t)i * inc];
-    part[(size_t)blockIdx.y * nb + j] = acc;
+    for (int i = i0; i < i1; ++i) acc.add(A[(size_t)i * nb + j], TA(x[(size_t)i * inc]));
+    part[(size_t)blockIdx.y * nb + j] = acc.value();
 }
 
 template <typename T>
