@@ -49,6 +49,7 @@ extern "C" {
                             test, CG residual norms) throughout */
 #define LBM_MIXED_TC  2  /* as LBM_MIXED, BEM product on the tensor cores
                             (3xTF32 split, FP32 accumulation) when batch > 1 */
+#define LBM_MIXED_TF32 LBM_MIXED_TC   /* the same mode under its arithmetic's name */
 
 typedef struct lbm_ctx lbm_ctx;
 typedef int64_t lbm_mesh;   /* mesh handle (> 0) */
@@ -83,6 +84,25 @@ typedef struct {
                                stalls), then an FP64 phase finishes to tol */
     double  cg_tol_polish;  /* relative residual of the potential solves in the
                                FP64 phase of a mixed-precision run */
+    int32_t cg_mixed_iter;  /* FP64 potential solves (LBM_FP64 runs and the FP64
+                               phase of mixed runs): 1 = CG iterations in FP32 with
+                               the FP64 residual recomputed whenever they have
+                               reduced it 1e4-fold (restarted CG), the solve ending
+                               on the FP64 residual test; 0 = plain FP64 PCG.
+                               Default 1 for LBM_MIXED / LBM_MIXED_TC, 0 for
+                               LBM_FP64 */
+    int32_t bb_rule;        /* step length after the first step (Sec. 2.3): 0 the
+                               adaptive BB rule (default), 1 BB1 = s.s/s.y,
+                               2 BB2 = s.y/y.y, 3 BB1 and BB2 on alternate steps;
+                               every rule restarts from 1/max|H| when s.y <= 0 */
+    int32_t method;         /* 0 curvilinear steepest descent with BB steps and the
+                               nonmonotone line search (Sec. 2, default); 1 LaBonte's
+                               method (Sec. 1.2), all nodes at once: m_i <-
+                               normalize((1 - omega) m_i + omega h_i/|h_i|), every
+                               step accepted; omega < 1 under-, > 1 over-relaxation.
+                               Not guaranteed to converge (exchange-coupled nodes
+                               moved together oscillate unless omega is small) */
+    double  omega;          /* LaBonte relaxation factor, 0 < omega <= 2 (default 1) */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -102,7 +122,7 @@ typedef struct {
 
 /* Fill `o` with the defaults for `precision` (tol 1e-6, memory 20, c1 1e-4,
  * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-6 mixed,
- * switch_tol 1e-4, cg_tol_polish 1e-10). */
+ * switch_tol 1e-4, cg_tol_polish 1e-10, cg_mixed_iter 1 mixed / 0 FP64). */
 void lbm_default_opts(lbm_solve_opts* o, int32_t precision);
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t
@@ -119,12 +139,44 @@ const char* lbm_last_error(void);
  * lists and the dense double-layer BEM matrix (FP64 and FP32).
  * 1 <= n <= 96.  Device memory: about 12*nb^2 + 17*nnz + 40*N bytes. */
 int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out);
+
+#define LBM_UPLOAD_MAX_NODES 8000000
+#define LBM_UPLOAD_MAX_TETS  16000000
+
+/* Any conforming tetrahedral mesh (Sec. 2.1 linear tetrahedral elements; the
+ * paper's grain is such a mesh of a sphere, Sec. 3.1).
+ *   xyz   HOST [n_nodes*3] node coordinates in metres (copied; caller keeps it)
+ *   tets  HOST [n_tets*4]  node ids of each tetrahedron, any orientation (copied)
+ * The library checks the ids, rejects degenerate tetrahedra, unused nodes and
+ * faces shared by more than two tetrahedra (LBM_E_INVALID with a message), and
+ * builds: the CSR pattern of the element adjacency (columns ascending), the
+ * surface (faces of one tetrahedron, oriented outward), the surface node list
+ * (ascending ids), the P1 stiffness, divergence coupling and lumped volumes in
+ * FP64 on the device (each row summing its tetrahedra in ascending order), and
+ * the dense double-layer BEM matrix (FP64 and FP32).  Reduced units use the
+ * length unit L = (mean |6 x volume|)^(1/3) (the cell edge of a 6-tetrahedra
+ * cube split).  4 <= n_nodes <= LBM_UPLOAD_MAX_NODES, n_tets <=
+ * LBM_UPLOAD_MAX_TETS, at most 65534 surface nodes.  Device memory: about
+ * 12*nb^2 + 100*nnz + 80*N + 16*T bytes. */
+int lbm_mesh_upload(lbm_ctx* ctx, const double* xyz, int64_t n_nodes, const int32_t* tets,
+                    int64_t n_tets, lbm_mesh* out);
 int lbm_mesh_destroy(lbm_ctx* ctx, lbm_mesh mesh);
 
-/* info[0..7] = N, nb, nnz, tets, boundary triangles, device bytes, n, 0. */
+/* FP64 copies of the assembled operators of any mesh, in SI units, on the CSR
+ * pattern of lbm_mesh_export (any pointer may be NULL):
+ *   K[nnz] int grad phi_i . grad phi_j (m), G[nnz*3] sum_e (vol_e/4) grad phi_i|_e
+ *   (m^2), Gt[nnz*3] G_ji, V[N] lumped volumes (m^3), unit_m the length unit
+ *   (the cell edge of a cube mesh, L of an uploaded one). */
+int lbm_mesh_values(lbm_ctx* ctx, lbm_mesh mesh, double* K, double* G, double* Gt, double* V,
+                    double* unit_m);
+
+/* info[0..7] = N, nb, nnz, tets, boundary triangles, device bytes, n (0 for an
+ * uploaded mesh), 0. */
 int lbm_mesh_info(lbm_ctx* ctx, lbm_mesh mesh, int64_t info[8]);
 
-/* Host copies of the assembled tables (any pointer may be NULL):
+/* Host copies of the assembled tables (any pointer may be NULL; the integer
+ * tables kval, gval, gtval, vol exist for cube meshes only -- an uploaded mesh
+ * rejects them with LBM_E_INVALID, use lbm_mesh_values):
  *   tets[T*4], rowptr[N+1], col[nnz] (node ids, boundary flag removed),
  *   kval[nnz] (K in units h/6), gval[nnz*3] (G_ij in units h^2/24),
  *   gtval[nnz*3] (G_ji), vol[N] (V in units h^3/24), bnd[nb] (ascending ids),
@@ -154,6 +206,11 @@ int lbm_get_m(lbm_ctx* ctx, lbm_inst inst, double* m /* [batch*N*3] host */);
  * potentials u1, u2 in metres (U = Ms u).  res (nullable): [batch]. */
 int lbm_evaluate(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, double* h, double* u,
                  lbm_result* res);
+
+/* The Eq. (1) energy terms of every instance at its current m, with the
+ * instance precision's default solver options:
+ *   e_terms HOST [batch*5] exchange, anisotropy, Zeeman, stray field, total (J). */
+int lbm_energy(lbm_ctx* ctx, lbm_inst inst, double* e_terms);
 
 /* Minimise every instance of the batch from its current m (Sec. 2.2-2.3).
  * res: [batch].  Returns LBM_OK when the call ran; per-instance outcomes are
@@ -204,8 +261,8 @@ int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);
  * fixed device array built into the library (about 4.9 MB on every device that
  * loads it, held until the process exits).  It calls no cudaMalloc or cudaFree.
  *
- *   mesh      a cube from lbm_mesh_cube with at most 16384 nodes and 4096
- *             surface nodes (n <= 24 cells per side); larger meshes are
+ *   mesh      a mesh (lbm_mesh_cube or lbm_mesh_upload) with at most 16384
+ *             nodes and 4096 surface nodes (cubes: n <= 24); larger meshes are
  *             rejected with LBM_E_INVALID and a message
  *   mat, h_ext, opt   as for an instance (opt may be NULL: FP64 defaults)
  *   d_m       DEVICE pointer, [N*3] unit vectors (node-major)

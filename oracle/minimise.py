@@ -32,6 +32,17 @@ Readings where the paper prints no detail:
     the paper's grad h^T grad h < 1e-12 of Sec. 3.1);
   * sweep: at every field point the step memory, the energy history and the
     first-step line search start afresh.
+
+Step-rule variants (StepRule.bb): "adaptive" (above, the default), "bb1" (tau^1
+always), "bb2" (tau^2 always) and "alternate" (tau^1 and tau^2 on alternate
+steps, the plain alternation that the adaptive rule refines, Sec. 2.3); all
+restart from tau = 1/max|H| when s.y <= 0 and share the clamp.
+
+LaBonte's method (Sec. 1.2 history): every node's magnetisation is replaced
+by its normalised effective field; over- and under-relaxation rotate it part
+of the way or beyond.  Data-parallel reading used here (all nodes at once,
+relaxation factor omega):  m_i <- normalize((1 - omega) m_i + omega h_i/|h_i|),
+omega = 1 the plain replacement; no line search; stop test as above.
 """
 from __future__ import annotations
 
@@ -53,6 +64,7 @@ class StepRule:
     m_alpha: int = 3
     tau_min: float = 1e-10
     tau_max: float = 1e10
+    bb: str = "adaptive"          # "adaptive" | "bb1" | "bb2" | "alternate"
 
 
 def cayley(m: np.ndarray, H: np.ndarray, tau: float) -> np.ndarray:
@@ -75,12 +87,21 @@ def bb_steps(s: np.ndarray, y: np.ndarray):
 class BBState:
     kappa: float
     tau2: list = field(default_factory=list)
+    k: int = 0                    # BB steps taken (parity for "alternate")
 
 
 def next_bb_tau(s, y, tau_restart: float, st: BBState, rule: StepRule) -> float:
     steps = bb_steps(s, y)
+    k = st.k
+    st.k += 1
     if steps is None:
         tau = tau_restart
+    elif rule.bb == "bb1":
+        tau = steps[0]
+    elif rule.bb == "bb2":
+        tau = steps[1]
+    elif rule.bb == "alternate":
+        tau = steps[0] if k % 2 == 0 else steps[1]
     else:
         t1, t2 = steps
         st.tau2.append(t2)
@@ -176,6 +197,35 @@ def minimise(prob: CubeProblem, m0: np.ndarray, h_ext, tol: float = 1e-6, max_it
         tau = next_bb_tau(s, y, 1.0 / float(np.max(np.linalg.norm(H, axis=1))), bb, rule)
         searching, backtracks = False, 0
     return Result(m, ev.E, ev.terms, ev.torque, status, it, evals, line_searches, traj, hist)
+
+
+def labonte(prob: CubeProblem, m0: np.ndarray, h_ext, omega: float = 1.0, tol: float = 1e-6,
+            max_iter: int = 100000, record=()) -> Result:
+    """LaBonte's rotate-to-field iteration with relaxation factor omega, all
+    nodes at once: m_i <- normalize((1 - omega) m_i + omega h_i/|h_i|)."""
+    record = set(record)
+    m = np.array(m0, dtype=np.float64)
+    ev = prob.evaluate(m, h_ext)
+    evals, it, traj = 1, 0, []
+    hist = [ev.E / prob.E0]
+    status = MAX_ITER
+    while True:
+        if ev.torque < tol:
+            status = OK
+            break
+        if it >= max_iter:
+            break
+        hn = np.linalg.norm(ev.h, axis=1, keepdims=True)
+        hhat = np.where(hn > 0.0, ev.h / np.where(hn > 0.0, hn, 1.0), m)
+        x = (1.0 - omega) * m + omega * hhat
+        m = x / np.linalg.norm(x, axis=1, keepdims=True)
+        ev = prob.evaluate(m, h_ext)
+        evals += 1
+        it += 1
+        hist.append(ev.E / prob.E0)
+        if it in record:
+            traj.append((it, m.copy()))
+    return Result(m, ev.E, ev.terms, ev.torque, status, it, evals, 0, traj, hist)
 
 
 def hysteresis(prob: CubeProblem, m0: np.ndarray, direction, fields, tol: float = 1e-6,

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "liblbm.so")
 LBM_OK, LBM_E_INVALID, LBM_E_OOM, LBM_E_NOT_CONVERGED = 0, 1, 2, 3
 LBM_E_NAN, LBM_E_TIMEOUT, LBM_E_LINESEARCH, LBM_E_CUDA, LBM_E_PENDING = 4, 5, 6, 7, 8
 LBM_FP64, LBM_MIXED, LBM_MIXED_TC = 0, 1, 2
+LBM_MIXED_TF32 = LBM_MIXED_TC
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "NOT_CONVERGED", 4: "NAN", 5: "TIMEOUT",
                 6: "LINESEARCH", 7: "CUDA", 8: "PENDING"}
 
@@ -34,7 +35,8 @@ class SolveOpts(C.Structure):
                 ("max_backtracks", C.c_int32), ("memory", C.c_int32), ("kappa0", C.c_double),
                 ("m_alpha", C.c_int32), ("tau_min", C.c_double), ("tau_max", C.c_double),
                 ("demag", C.c_int32), ("check_every", C.c_int32), ("switch_tol", C.c_double),
-                ("cg_tol_polish", C.c_double)]
+                ("cg_tol_polish", C.c_double), ("cg_mixed_iter", C.c_int32), ("bb_rule", C.c_int32),
+                ("method", C.c_int32), ("omega", C.c_double)]
 
 
 class ProfileStats(C.Structure):
@@ -81,6 +83,9 @@ SIGNATURES = [
     ("lbm_destroy", C.c_int, [_P]),
     ("lbm_last_error", C.c_char_p, []),
     ("lbm_mesh_cube", C.c_int, [_P, C.c_double, C.c_int32, C.POINTER(_I64)]),
+    ("lbm_mesh_upload", C.c_int, [_P, _DP, _I64, _IP, _I64, C.POINTER(_I64)]),
+    ("lbm_mesh_values", C.c_int, [_P, _I64, _DP, _DP, _DP, _DP, _DP]),
+    ("lbm_energy", C.c_int, [_P, _I64, _DP]),
     ("lbm_mesh_destroy", C.c_int, [_P, _I64]),
     ("lbm_mesh_info", C.c_int, [_P, _I64, C.POINTER(_I64)]),
     ("lbm_mesh_export", C.c_int, [_P, _I64] + [_IP] * 9),
@@ -186,6 +191,27 @@ class Context:
         _check(lib().lbm_mesh_cube(self._h, cell_m, n, C.byref(h)))
         return h.value
 
+    def mesh_upload(self, xyz, tets) -> int:
+        """A general tetrahedral mesh: xyz (N, 3) metres, tets (T, 4) node ids."""
+        x = np.ascontiguousarray(np.asarray(xyz, np.float64))
+        t = np.ascontiguousarray(np.asarray(tets, np.int32))
+        if x.ndim != 2 or x.shape[1] != 3 or t.ndim != 2 or t.shape[1] != 4:
+            raise ValueError("xyz must be (N, 3) and tets (T, 4)")
+        h = _I64()
+        _check(lib().lbm_mesh_upload(self._h, _dptr(x), x.shape[0], _iptr(t), t.shape[0], C.byref(h)))
+        return h.value
+
+    def mesh_values(self, mesh: int) -> dict:
+        """FP64 operators in SI units: K (nnz,), G, Gt (nnz, 3), V (N,), unit (m)."""
+        i = self.mesh_info(mesh)
+        out = dict(K=np.empty(i["nnz"]), G=np.empty((i["nnz"], 3)), Gt=np.empty((i["nnz"], 3)),
+                   V=np.empty(i["N"]))
+        unit = C.c_double()
+        _check(lib().lbm_mesh_values(self._h, mesh, _dptr(out["K"]), _dptr(out["G"]), _dptr(out["Gt"]),
+                                     _dptr(out["V"]), C.byref(unit)))
+        out["unit"] = unit.value
+        return out
+
     def mesh_destroy(self, mesh: int):
         _check(lib().lbm_mesh_destroy(self._h, mesh))
 
@@ -196,6 +222,8 @@ class Context:
         return {k: int(info[i]) for i, k in enumerate(keys)}
 
     def mesh_export(self, mesh: int) -> dict:
+        """Topology and (cube meshes) the integer tables; an uploaded mesh has no
+        integer tables, so kval/gval/gtval/vol are left out for it."""
         i = self.mesh_info(mesh)
         N, nb, nnz, T, F = i["N"], i["nb"], i["nnz"], i["tets"], i["tris"]
         out = dict(tets=np.empty((T, 4), np.int32), rowptr=np.empty(N + 1, np.int32),
@@ -203,9 +231,11 @@ class Context:
                    gval=np.empty((nnz, 3), np.int32), gtval=np.empty((nnz, 3), np.int32),
                    vol=np.empty(N, np.int32), bnd=np.empty(nb, np.int32),
                    tris=np.empty((F, 3), np.int32))
-        _check(lib().lbm_mesh_export(self._h, mesh, *[_iptr(out[k]) for k in
-                                                      ("tets", "rowptr", "col", "kval", "gval",
-                                                       "gtval", "vol", "bnd", "tris")]))
+        keys = ("tets", "rowptr", "col", "kval", "gval", "gtval", "vol", "bnd", "tris")
+        if i["n"] == 0:
+            for k in ("kval", "gval", "gtval", "vol"):
+                del out[k]
+        _check(lib().lbm_mesh_export(self._h, mesh, *[_iptr(out[k]) if k in out else None for k in keys]))
         return out
 
     def bem_rows(self, mesh: int, row0: int, nrows: int) -> np.ndarray:
@@ -345,6 +375,12 @@ class Instance:
         _check(lib().lbm_evaluate(self.ctx._h, self.h, C.byref(opts) if opts else None,
                                   _dptr(h), _dptr(u), res))
         return [r.as_dict() for r in res], h, u
+
+    def energy(self) -> np.ndarray:
+        """(B, 5) exchange, anisotropy, Zeeman, stray-field and total energy (J)."""
+        out = np.empty((self.B, 5))
+        _check(lib().lbm_energy(self.ctx._h, self.h, _dptr(out)))
+        return out
 
     def minimise(self, opts: SolveOpts | None = None):
         res = (Result * self.B)()

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -57,6 +58,15 @@ struct Mesh {
     double* B64 = nullptr;
     float* B32 = nullptr;
     float *tcA = nullptr, *tcAT = nullptr;   // padded FP32 B and B^T for the tensor-core path (lazy)
+    // general meshes (lbm_mesh_upload; n == 0)
+    bool gen = false;
+    double vsum = 0.0;
+    int* tets = nullptr;                     // T*4 as uploaded (orientation kept)
+    double* xyz = nullptr;                   // N*3 in units of L
+    Dbl4 *gA64 = nullptr, *gB64 = nullptr;
+    float4 *gA32 = nullptr, *gB32 = nullptr;
+    double *gk64 = nullptr, *gV = nullptr, *gd64 = nullptr;
+    float *gk32 = nullptr, *gd32 = nullptr;
     size_t bytes = 0;
     MeshView view() const {
         MeshView v;
@@ -64,8 +74,11 @@ struct Mesh {
         v.rowptr = rowptr; v.col = col; v.pkA = pkA; v.pkB = pkB; v.node = node; v.bidx = bidx;
         v.kptr = kptr; v.kent = kent;
         v.B64 = B64; v.B32 = B32;
-        v.vsum = 24.0 * (double)n * n * n;
+        v.vsum = gen ? vsum : 24.0 * (double)n * n * n;
         v.cell = cell;
+        v.gen = gen ? 1 : 0;
+        v.gA64 = gA64; v.gA32 = gA32; v.gB64 = gB64; v.gB32 = gB32;
+        v.gk64 = gk64; v.gk32 = gk32; v.gV = gV; v.gd64 = gd64; v.gd32 = gd32;
         return v;
     }
 };
@@ -194,7 +207,7 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.q = take(tsize * N * C);
     L.ub_in = take(tsize * nb * C);
     L.ub_out = take(tsize * nb * C);
-    L.bem_part = take(8 * 32 * nb);
+    L.bem_part = take(8 * 34 * nb);   // 32 x nb partial sums + hi/lo FP32 parts of two vectors
     L.total = o;
     return L;
 }
@@ -243,7 +256,8 @@ Inst* get_inst(lbm_ctx* ctx, lbm_inst h) {
 
 void free_mesh(Mesh* m) {
     void* ptrs[] = {m->rowptr, m->col, m->pkA, m->pkB, m->node, m->bidx, m->tris, m->inc_ptr, m->inc_slot,
-                    m->kptr, m->kent, m->B64, m->B32, m->tcA, m->tcAT};
+                    m->kptr, m->kent, m->B64, m->B32, m->tcA, m->tcAT, m->tets, m->xyz, m->gA64, m->gB64,
+                    m->gA32, m->gB32, m->gk64, m->gV, m->gd64, m->gk32, m->gd32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -293,6 +307,9 @@ StepOpts step_opts(const lbm_solve_opts& o) {
     s.max_backtracks = o.max_backtracks;
     s.memory = o.memory;
     s.m_alpha = o.m_alpha;
+    s.bb_rule = o.bb_rule;
+    s.method = o.method;
+    s.omega = o.omega;
     return s;
 }
 
@@ -300,7 +317,8 @@ int check_opts(const lbm_solve_opts& o) {
     if (!(o.tol >= 0) || o.max_iter < 0 || o.memory < 1 || o.memory > HIST_MAX || o.m_alpha < 1 ||
         o.m_alpha > MALPHA_MAX || o.max_backtracks < 0 || o.cg_max_iter < 1 || !(o.cg_tol > 0) ||
         o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
-        !(o.cg_tol_polish > 0))
+        !(o.cg_tol_polish > 0) || o.bb_rule < 0 || o.bb_rule > 3 || o.method < 0 || o.method > 1 ||
+        (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)))
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -315,7 +333,7 @@ int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, cons
         const int k64 = sizeof(T) == 8 ? 5 : 0;
         {
             ProfScope ps(ctx, 1 + k64, L.stream);
-            e = pcg_solve<T>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, nullptr);
+            e = pcg_solve<T>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, o.cg_mixed_iter != 0);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
         {
@@ -329,7 +347,7 @@ int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, cons
         }
         {
             ProfScope ps(ctx, 3 + (k64 ? 4 : 0), L.stream);
-            e = pcg_solve<T>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, nullptr);
+            e = pcg_solve<T>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, o.cg_mixed_iter != 0);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
@@ -464,8 +482,12 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
             P->precision = LBM_FP64;
             P->tsize = 8;
             P->bem32 = true;
-            P->use_tc = I->use_tc;
-            P->tc_scratch = I->tc_scratch;   // the phases run one after the other on one stream
+            // The FP64 phase fixes the final accuracy: its BEM products stay on the
+            // SIMT path (FP32 matrix).  The tensor cores' FP32 accumulation is not
+            // round-to-nearest, and over the long reductions of the product
+            // (K = nb) it biases the stray-field energy by ~1e-6 relative.
+            P->use_tc = false;
+            P->tc_scratch = nullptr;
             P->owns_tc_scratch = false;
             const size_t vb = vec_bytes(M, I->B, 8), pe = part_elems(ctx, I->B);
             if (cudaMalloc(&P->vec, vb) != cudaSuccess || cudaMalloc(&P->part, pe * sizeof(double)) != cudaSuccess ||
@@ -542,6 +564,10 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->check_every = 16;
     o->switch_tol = 1e-4;
     o->cg_tol_polish = 1e-10;
+    o->cg_mixed_iter = precision == LBM_FP64 ? 0 : 1;
+    o->bb_rule = 0;
+    o->method = 0;
+    o->omega = 1.0;
     if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
@@ -682,8 +708,8 @@ int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
     if (nblocks > M->nb) nblocks = M->nb;
     double* scratch = nullptr;
     CKM(cudaMalloc(&scratch, sizeof(double) * 3 * (size_t)M->F * nblocks));
-    launch_bem_assemble(n, M->nb, M->F, M->bidx, M->tris, M->inc_ptr, M->inc_slot, scratch, nblocks, M->B64,
-                        M->B32, st);
+    launch_bem_assemble(n, M->nb, M->F, M->bidx, M->tris, M->inc_ptr, M->inc_slot, nullptr, scratch, nblocks,
+                        M->B64, M->B32, st);
     ctx->launches += 1;
     cudaError_t e = cudaStreamSynchronize(st);
     cudaFree(scratch);
@@ -697,6 +723,172 @@ int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
     const int64_t id = ctx->next_id++;
     ctx->meshes[id] = M;
     *out = id;
+    return LBM_OK;
+}
+
+int lbm_mesh_upload(lbm_ctx* ctx, const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                    lbm_mesh* out) {
+    if (!ctx || !out || !xyz || !tets) return fail(LBM_E_INVALID, "lbm_mesh_upload: null argument");
+    if (n_nodes < 4 || n_nodes > LBM_UPLOAD_MAX_NODES || n_tets < 1 || n_tets > LBM_UPLOAD_MAX_TETS)
+        return fail(LBM_E_INVALID, "lbm_mesh_upload: need 4 <= n_nodes <= %d and 1 <= n_tets <= %d",
+                    LBM_UPLOAD_MAX_NODES, LBM_UPLOAD_MAX_TETS);
+    for (int64_t k = 0; k < 3 * n_nodes; ++k)
+        if (!std::isfinite(xyz[k])) return fail(LBM_E_INVALID, "lbm_mesh_upload: non-finite coordinate");
+    const int N = (int)n_nodes, T = (int)n_tets;
+    GeneralTopology g;
+    const std::string why = host_general_topology(N, T, tets, xyz, g);
+    if (!why.empty()) return fail(LBM_E_INVALID, "lbm_mesh_upload: %s", why.c_str());
+    const int nb = (int)g.bidx.size();
+    if (nb > 65534) return fail(LBM_E_INVALID, "lbm_mesh_upload: %d surface nodes (at most 65534)", nb);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    Mesh* M = new Mesh();
+    M->gen = true;
+    M->n = 0;
+    M->N = N;
+    M->T = T;
+    M->nb = nb;
+    M->nnz = (int)g.col.size();
+    M->F = (int)g.tris.size() / 3;
+    M->cell = g.L;
+    // coordinates in units of L, surface flags on the columns, node words
+    std::vector<double> xl(3 * (size_t)N);
+    for (size_t k = 0; k < xl.size(); ++k) xl[k] = xyz[k] / g.L;
+    std::vector<int> bpos(N, 0), colf(g.col.size()), nodew(N);
+    for (int k = 0; k < nb; ++k) bpos[g.bidx[k]] = k + 1;
+    for (size_t e = 0; e < g.col.size(); ++e) colf[e] = (int)((unsigned)g.col[e] | (bpos[g.col[e]] ? 0x80000000u : 0u));
+    for (int i = 0; i < N; ++i) nodew[i] = (int)((unsigned)bpos[i] << 16);
+    double vsum = 0.0;
+    for (int t = 0; t < T; ++t) vsum += 4.0 * fabs(g.det[t]) / (g.L * g.L * g.L);
+    M->vsum = vsum;
+    std::vector<int> incp, incs;
+    host_incidence(N, g.tris, g.bidx, incp, incs);
+    int *nt_ptr = nullptr, *nt_idx = nullptr, *cnt = nullptr;
+    double* scratch = nullptr;
+    auto cleanup = [&]() {
+        if (nt_ptr) cudaFree(nt_ptr);
+        if (nt_idx) cudaFree(nt_idx);
+        if (cnt) cudaFree(cnt);
+        if (scratch) cudaFree(scratch);
+    };
+#define CKM(call)                   \
+    do {                            \
+        cudaError_t e_ = (call);    \
+        if (e_ != cudaSuccess) {    \
+            cudaStreamSynchronize(st); \
+            cleanup();              \
+            free_mesh(M);           \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+        }                           \
+    } while (0)
+    const size_t nnz = M->nnz;
+    CKM(cudaMalloc(&M->rowptr, sizeof(int) * (N + 1)));
+    CKM(cudaMalloc(&M->col, sizeof(int) * nnz));
+    CKM(cudaMalloc(&M->node, sizeof(int) * N));
+    CKM(cudaMalloc(&M->bidx, sizeof(int) * nb));
+    CKM(cudaMalloc(&M->tets, sizeof(int) * 4 * (size_t)T));
+    CKM(cudaMalloc(&M->xyz, sizeof(double) * 3 * (size_t)N));
+    CKM(cudaMalloc(&M->tris, sizeof(int) * g.tris.size()));
+    CKM(cudaMalloc(&M->inc_ptr, sizeof(int) * incp.size()));
+    CKM(cudaMalloc(&M->inc_slot, sizeof(int) * incs.size()));
+    CKM(cudaMalloc(&nt_ptr, sizeof(int) * (N + 1)));
+    CKM(cudaMalloc(&nt_idx, sizeof(int) * g.nt_idx.size()));
+    CKM(cudaMalloc(&cnt, sizeof(int) * N));
+    CKM(cudaMalloc(&M->gA64, sizeof(Dbl4) * nnz));
+    CKM(cudaMalloc(&M->gB64, sizeof(Dbl4) * nnz));
+    CKM(cudaMalloc(&M->gA32, sizeof(float4) * nnz));
+    CKM(cudaMalloc(&M->gB32, sizeof(float4) * nnz));
+    CKM(cudaMalloc(&M->gV, sizeof(double) * N));
+    CKM(cudaMalloc(&M->gd64, sizeof(double) * N));
+    CKM(cudaMalloc(&M->gd32, sizeof(float) * N));
+    CKM(cudaMalloc(&M->kptr, sizeof(int) * (N + 1)));
+    CKM(cudaMemcpyAsync(M->rowptr, g.rowptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->col, colf.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->node, nodew.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->bidx, g.bidx.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->tets, tets, sizeof(int) * 4 * (size_t)T, cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->xyz, xl.data(), sizeof(double) * xl.size(), cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->tris, g.tris.data(), sizeof(int) * g.tris.size(), cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->inc_ptr, incp.data(), sizeof(int) * incp.size(), cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(M->inc_slot, incs.data(), sizeof(int) * incs.size(), cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(nt_ptr, g.nt_ptr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+    CKM(cudaMemcpyAsync(nt_idx, g.nt_idx.data(), sizeof(int) * g.nt_idx.size(), cudaMemcpyHostToDevice, st));
+    launch_assemble_gen(N, M->xyz, M->tets, nt_ptr, nt_idx, M->rowptr, M->col, M->gA64, M->gA32, M->gB64, M->gB32,
+                        M->gV, M->gd64, M->gd32, st);
+    launch_kcsr_count_gen(N, M->rowptr, M->gA64, cnt, st);
+    launch_scan(cnt, M->kptr, N, st);
+    ctx->launches += 3;
+    int tot = 0;
+    CKM(cudaMemcpyAsync(&tot, M->kptr + N, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKM(cudaStreamSynchronize(st));
+    M->nnzK = tot;
+    CKM(cudaMalloc(&M->kent, sizeof(int) * (size_t)M->nnzK));
+    CKM(cudaMalloc(&M->gk64, sizeof(double) * (size_t)M->nnzK));
+    CKM(cudaMalloc(&M->gk32, sizeof(float) * (size_t)M->nnzK));
+    launch_kcsr_fill_gen(N, M->rowptr, M->col, M->gA64, M->kptr, M->kent, M->gk64, M->gk32, st);
+    ctx->launches += 1;
+    const size_t nb2 = (size_t)nb * nb;
+    CKM(cudaMalloc(&M->B64, sizeof(double) * nb2));
+    CKM(cudaMalloc(&M->B32, sizeof(float) * nb2));
+    int nblocks = 2 * ctx->num_sms;
+    if (nblocks > nb) nblocks = nb;
+    CKM(cudaMalloc(&scratch, sizeof(double) * 3 * (size_t)M->F * nblocks));
+    launch_bem_assemble(0, nb, M->F, M->bidx, M->tris, M->inc_ptr, M->inc_slot, M->xyz, scratch, nblocks, M->B64,
+                        M->B32, st);
+    ctx->launches += 1;
+    CKM(cudaStreamSynchronize(st));
+    CKM(cudaGetLastError());
+    cleanup();
+#undef CKM
+    M->bytes = sizeof(int) * ((size_t)3 * N + 2 + nnz + M->nnzK + nb + g.tris.size() + incp.size() + incs.size() +
+                              4 * (size_t)T) +
+               sizeof(double) * (3 * (size_t)N + 3 * (size_t)N + M->nnzK) + (32 + 32 + 16 + 16) * nnz +
+               4 * ((size_t)N + M->nnzK) + 12 * nb2;
+    const int64_t id = ctx->next_id++;
+    ctx->meshes[id] = M;
+    *out = id;
+    return LBM_OK;
+}
+
+int lbm_mesh_values(lbm_ctx* ctx, lbm_mesh mesh, double* K, double* G, double* Gt, double* V, double* unit_m) {
+    Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
+    if (!M) return fail(LBM_E_INVALID, "unknown mesh");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const double L = M->cell;
+    const double sK = L / 6.0, sG = L * L / 24.0, sV = L * L * L / 24.0;
+    if (unit_m) *unit_m = L;
+    if (M->gen) {
+        std::vector<Dbl4> a(M->nnz), b(M->nnz);
+        std::vector<double> v(M->N);
+        CK(cudaMemcpyAsync(a.data(), M->gA64, sizeof(Dbl4) * M->nnz, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b.data(), M->gB64, sizeof(Dbl4) * M->nnz, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(v.data(), M->gV, sizeof(double) * M->N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int e = 0; e < M->nnz; ++e) {
+            if (K) K[e] = sK * a[e].x;
+            if (G) { G[3 * e] = sG * a[e].y; G[3 * e + 1] = sG * a[e].z; G[3 * e + 2] = sG * a[e].w; }
+            if (Gt) { Gt[3 * e] = sG * b[e].x; Gt[3 * e + 1] = sG * b[e].y; Gt[3 * e + 2] = sG * b[e].z; }
+        }
+        if (V)
+            for (int i = 0; i < M->N; ++i) V[i] = sV * v[i];
+        return LBM_OK;
+    }
+    std::vector<int> a(M->nnz), b(M->nnz), nd(M->N);
+    CK(cudaMemcpyAsync(a.data(), M->pkA, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(b.data(), M->pkB, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(nd.data(), M->node, sizeof(int) * M->N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    auto sb = [](int w, int k) { return (double)(signed char)((w >> (8 * k)) & 0xff); };
+    for (int e = 0; e < M->nnz; ++e) {
+        if (K) K[e] = sK * sb(a[e], 0);
+        for (int d = 0; d < 3; ++d) {
+            if (G) G[3 * e + d] = sG * sb(a[e], 1 + d);
+            if (Gt) Gt[3 * e + d] = sG * sb(b[e], d);
+        }
+    }
+    if (V)
+        for (int i = 0; i < M->N; ++i) V[i] = sV * (double)(nd[i] & 0xff);
     return LBM_OK;
 }
 
@@ -731,7 +923,11 @@ int lbm_mesh_export(lbm_ctx* ctx, lbm_mesh mesh, int32_t* tets, int32_t* rowptr,
     if (!M) return fail(LBM_E_INVALID, "unknown mesh");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    if (tets) {
+    if (M->gen && (kval || gval || gtval || vol))
+        return fail(LBM_E_INVALID, "lbm_mesh_export: integer tables exist for cube meshes only (use lbm_mesh_values)");
+    if (tets && M->gen) {
+        CK(cudaMemcpyAsync(tets, M->tets, sizeof(int) * 4 * (size_t)M->T, cudaMemcpyDeviceToHost, st));
+    } else if (tets) {
         int* d = nullptr;
         CK(cudaMalloc(&d, sizeof(int) * 4 * (size_t)M->T));
         launch_tets(M->n, d, st);
@@ -746,8 +942,10 @@ int lbm_mesh_export(lbm_ctx* ctx, lbm_mesh mesh, int32_t* tets, int32_t* rowptr,
     if (tris) CK(cudaMemcpyAsync(tris, M->tris, sizeof(int) * 3 * M->F, cudaMemcpyDeviceToHost, st));
     std::vector<int> c(M->nnz), a(M->nnz), b(M->nnz), nd(M->N);
     CK(cudaMemcpyAsync(c.data(), M->col, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(a.data(), M->pkA, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(b.data(), M->pkB, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
+    if (!M->gen) {
+        CK(cudaMemcpyAsync(a.data(), M->pkA, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(b.data(), M->pkB, sizeof(int) * M->nnz, cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaMemcpyAsync(nd.data(), M->node, sizeof(int) * M->N, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     auto sb = [](int w, int k) { return (int)(signed char)((w >> (8 * k)) & 0xff); };
@@ -950,6 +1148,19 @@ int lbm_evaluate(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, double*
                          : run_minimise<float>(ctx, I, o, res, true, h, u);
 }
 
+int lbm_energy(lbm_ctx* ctx, lbm_inst inst, double* e_terms) {
+    Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
+    if (!I || !e_terms) return fail(LBM_E_INVALID, "lbm_energy: unknown instance or null output");
+    lbm_solve_opts o;
+    lbm_default_opts(&o, I->precision);
+    std::vector<lbm_result> r(I->B);
+    const int rc = lbm_evaluate(ctx, inst, &o, nullptr, nullptr, r.data());
+    if (rc != LBM_OK) return rc;
+    for (int b = 0; b < I->B; ++b)
+        for (int k = 0; k < 5; ++k) e_terms[5 * b + k] = r[b].energy[k];
+    return LBM_OK;
+}
+
 int lbm_minimise(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, lbm_result* res) {
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I) return fail(LBM_E_INVALID, "unknown instance");
@@ -1132,10 +1343,10 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     const StepOpts so = step_opts(oo);
     trial_update<double>(L, mv, V);
     if (o.demag) {
-        int e = pcg_solve<double>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, nullptr);
+        int e = pcg_solve<double>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, false);
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
         bem_product<double>(L, mv, V, false);
-        e = pcg_solve<double>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, nullptr);
+        e = pcg_solve<double>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, false);
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
     field_eval<double>(L, mv, V, o.demag);

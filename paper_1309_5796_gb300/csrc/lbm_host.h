@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "lbm_internal.cuh"
@@ -23,8 +24,26 @@ void launch_kcsr_fill(int N, const int* rowptr, const int* col, const int* pkA, 
                       cudaStream_t st);
 void launch_tets(int n, int* tets, cudaStream_t st);
 void launch_bem_assemble(int n, int nb, int F, const int* bidx, const int* tris, const int* inc_ptr,
-                         const int* inc_slot, double* scratch, int nblocks, double* B64, float* B32,
-                         cudaStream_t st);
+                         const int* inc_slot, const double* xyz, double* scratch, int nblocks, double* B64,
+                         float* B32, cudaStream_t st);
+void host_incidence(int N, const std::vector<int>& tris, const std::vector<int>& bidx, std::vector<int>& inc_ptr,
+                    std::vector<int>& inc_slot);
+
+// general tetrahedral meshes
+struct GeneralTopology {
+    std::vector<int> nt_ptr, nt_idx;   // node -> tetrahedra (ascending)
+    std::vector<int> rowptr, col;      // CSR pattern (columns ascending, no flags)
+    std::vector<int> tris, bidx;       // outward surface triangles, surface node ids (ascending)
+    std::vector<double> det;           // 6 x signed volume of every tetrahedron (input units)
+    double L = 0.0;                    // length unit (mean |det|)^(1/3)
+};
+std::string host_general_topology(int N, int T, const int* tets, const double* xyz, GeneralTopology& g);
+void launch_assemble_gen(int N, const double* xyz, const int* tets, const int* nt_ptr, const int* nt_idx,
+                         const int* rowptr, const int* col, Dbl4* A64, float4* A32, Dbl4* Bt64,
+                         float4* Bt32, double* Vn, double* d64, float* d32, cudaStream_t st);
+void launch_kcsr_count_gen(int N, const int* rowptr, const Dbl4* A64, int* cnt, cudaStream_t st);
+void launch_kcsr_fill_gen(int N, const int* rowptr, const int* col, const Dbl4* A64, const int* kptr, int* kent,
+                          double* k64, float* k32, cudaStream_t st);
 
 // ---- device view of one mesh --------------------------------------------------------
 struct MeshView {
@@ -39,8 +58,17 @@ struct MeshView {
     const int* bidx;     // nb;  boundary node ids, ascending
     const double* B64;   // nb x nb row-major
     const float* B32;    // nb x nb row-major
-    double vsum;         // sum_i Vint_i = 24 n^3
-    double cell;         // cell edge h (m)
+    double vsum;         // sum_i Vint_i = 24 n^3 (general meshes: sum of gV)
+    double cell;         // cell edge h (m); general meshes: the length unit L
+    // General meshes (gen != 0): the same tables as FP64/FP32 values in the same
+    // units (K: L/6, G: L^2/24, V: L^3/24); node[] then holds only the surface
+    // position, and kent's low byte only marks an entry.
+    int gen;
+    const Dbl4* gA64; const float4* gA32;   // nnz  {K, G_x, G_y, G_z}
+    const Dbl4* gB64; const float4* gB32;   // nnz  {G^T_x, G^T_y, G^T_z, 0}
+    const double* gk64; const float* gk32;     // nnzK values of the stiffness-only CSR
+    const double* gV;                          // N    lumped volumes
+    const double* gd64; const float* gd32;     // N    K_ii (Jacobi preconditioner)
 };
 
 // ---- device view of one instance batch (node-major, instance-minor) ------------------
@@ -77,7 +105,7 @@ struct Launch {
 
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
-              int* iters_dev);
+              bool mixed_iter);
 template <typename T>
 void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V, bool bem32);
 template <typename T>

@@ -24,12 +24,17 @@ enum {
 };
 constexpr int NQ = 16;                 // stride of the partials array
 
-enum { PH_INIT = 0, PH_SEARCH = 1, PH_BB = 2, PH_DONE = 3 };
+enum { PH_INIT = 0, PH_SEARCH = 1, PH_BB = 2, PH_DONE = 3, PH_LB = 4 };   // PH_LB: LaBonte iteration
 constexpr int HIST_MAX = 64;
 constexpr int MALPHA_MAX = 8;
 
 // Device status bits (context-wide error word).
 constexpr int DEV_ERR_TIMEOUT = 1;
+
+// Four doubles on a 32-byte boundary (general-mesh value tables).
+struct __align__(32) Dbl4 {
+    double x, y, z, w;
+};
 
 struct InstConst {
     double lam;        // A / (Kd h^2): h_ex~ = -4 lam (Kint m)_i / Vint_i
@@ -43,7 +48,9 @@ struct InstConst {
 struct StepOpts {
     double tol, grad_tol, c1, kappa0, tau_min, tau_max;
     int max_iter, max_backtracks, memory, m_alpha;
-    int stop_on_linesearch_fail;   // 1: a failed line search ends the run (status LINESEARCH)
+    int bb_rule;     // 0 adaptive, 1 BB1, 2 BB2, 3 BB1/BB2 alternation
+    int method;      // 0 curvilinear steepest descent (Sec. 2), 1 LaBonte rotate-to-field
+    double omega;    // LaBonte relaxation factor
 };
 
 struct InstState {
@@ -76,14 +83,19 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // launch; each block's thread 0 keeps its own epoch.  The wait gives up after
 // 2 s (or when another block has flagged an error), sets DEV_ERR_TIMEOUT and
 // returns false; callers then leave the kernel.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned nblocks, unsigned& epoch, int* err) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1u;
         const unsigned target = epoch * nblocks;
-        __threadfence();
-        atomicAdd(count, 1u);
+        // release: the block's writes (ordered before this by the barrier above)
+        // become visible to every block whose acquire load sees the increment
+        red_release_add(count, 1u);
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();
         unsigned spins = 0;
@@ -93,8 +105,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned nblocks, uns
                 if (globaltimer_ns() - t0 > 2000000000ull) { atomicOr(err, DEV_ERR_TIMEOUT); ok = 0; break; }
             }
         }
-        __threadfence();
-        s_ok = ok;
+        s_ok = ok;   // the acquire loads above order the other blocks' writes before the barrier below
     }
     __syncthreads();
     return s_ok != 0;

@@ -11,8 +11,14 @@
 // row is assembled by its own thread from the tetrahedra around its node, so
 // no atomics are needed and the tables are bit-reproducible.
 #include <math.h>
-#include <vector>
 #include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <string>
+#include <vector>
 
 #include "lbm_internal.cuh"
 #include "lbm_host.h"
@@ -264,26 +270,42 @@ __device__ void hat_double_layer(const double x[3], const double y[3][3], double
 // surface seen from a surface point subtends its interior solid angle), then
 // B_ij = (1/4pi) sum_{(t,k) at j} W[3t+k] + (Omega_i/4pi - 1) delta_ij in the
 // fixed order of the incidence list.
+// Coordinates come from the lattice (cube meshes, xyz == nullptr) or from xyz
+// (general meshes, units of the mesh's length unit).  A triangle that has the
+// collocation node as a vertex contains it and gives 0; with lattice
+// coordinates its h is exactly 0, with general ones it is excluded by index.
 __global__ void k_bem_assemble(int n, int nb, int F, const int* bidx, const int* tris, const int* inc_ptr,
-                               const int* inc_slot, double* scratch, double* B64, float* B32) {
+                               const int* inc_slot, const double* xyz, double* scratch, double* B64, float* B32) {
     __shared__ double s_red[256];
     const int n1 = n + 1;
     double* W = scratch + (size_t)blockIdx.x * 3 * F;
     const double inv4pi = 0.25 / 3.14159265358979323846;
+    auto coords = [&](int v, double* c) {
+        if (xyz) {
+            c[0] = xyz[3 * (size_t)v];
+            c[1] = xyz[3 * (size_t)v + 1];
+            c[2] = xyz[3 * (size_t)v + 2];
+        } else {
+            c[0] = (double)(v % n1);
+            c[1] = (double)((v / n1) % n1);
+            c[2] = (double)(v / (n1 * n1));
+        }
+    };
     for (int row = blockIdx.x; row < nb; row += gridDim.x) {
         const int id = bidx[row];
-        const double x[3] = {(double)(id % n1), (double)((id / n1) % n1), (double)(id / (n1 * n1))};
+        double x[3];
+        coords(id, x);
         double om = 0.0;
         for (int t = threadIdx.x; t < F; t += blockDim.x) {
             double y[3][3];
+            bool incident = false;
             for (int k = 0; k < 3; ++k) {
                 const int v = tris[3 * t + k];
-                y[k][0] = (double)(v % n1);
-                y[k][1] = (double)((v / n1) % n1);
-                y[k][2] = (double)(v / (n1 * n1));
+                incident |= (v == id);
+                coords(v, y[k]);
             }
-            double I[3];
-            hat_double_layer(x, y, I);
+            double I[3] = {0.0, 0.0, 0.0};
+            if (!incident) hat_double_layer(x, y, I);
             W[3 * t + 0] = I[0];
             W[3 * t + 1] = I[1];
             W[3 * t + 2] = I[2];
@@ -305,6 +327,110 @@ __global__ void k_bem_assemble(int n, int nb, int F, const int* bidx, const int*
             if (B32) B32[(size_t)row * nb + j] = (float)val;
         }
         __syncthreads();
+    }
+}
+
+// ---- general tetrahedral meshes (FP64 assembly) --------------------------------------
+// Coordinates in units of the mesh's length unit L.  With the cofactors c_a of
+// a tetrahedron and det = e1 . (e2 x e3) (6 x signed volume), the element
+// contributions in the units of the integer tables are
+//   K (units L/6):    c_a . c_b / |det|
+//   G (units L^2/24): sgn(det) c_a          (row a, every column b)
+//   G^T:              sgn(det) c_b
+//   V (units L^3/24): |det|                 (per incident tetrahedron)
+// One thread per row sums the tetrahedra around its node in ascending order.
+__global__ void k_assemble_gen(int N, const double* __restrict__ xyz, const int* __restrict__ tets,
+                               const int* __restrict__ nt_ptr, const int* __restrict__ nt_idx,
+                               const int* __restrict__ rowptr, const int* __restrict__ col, Dbl4* A64,
+                               float4* A32, Dbl4* Bt64, float4* Bt32, double* Vn, double* d64, float* d32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int e0 = rowptr[i], e1 = rowptr[i + 1];
+        for (int e = e0; e < e1; ++e) {
+            A64[e] = Dbl4{0.0, 0.0, 0.0, 0.0};
+            Bt64[e] = Dbl4{0.0, 0.0, 0.0, 0.0};
+        }
+        double V = 0.0;
+        for (int q = nt_ptr[i]; q < nt_ptr[i + 1]; ++q) {
+            const int t = nt_idx[q];
+            int v[4];
+            double P[4][3];
+            int a = -1;
+            for (int k = 0; k < 4; ++k) {
+                v[k] = tets[4 * (size_t)t + k];
+                if (v[k] == i) a = k;
+                for (int d = 0; d < 3; ++d) P[k][d] = xyz[3 * (size_t)v[k] + d];
+            }
+            double E[3][3], c[4][3];
+            for (int k = 0; k < 3; ++k)
+                for (int d = 0; d < 3; ++d) E[k][d] = P[k + 1][d] - P[0][d];
+            for (int k = 0; k < 3; ++k) {
+                const double* u = E[(k + 1) % 3];
+                const double* w = E[(k + 2) % 3];
+                c[k + 1][0] = u[1] * w[2] - u[2] * w[1];
+                c[k + 1][1] = u[2] * w[0] - u[0] * w[2];
+                c[k + 1][2] = u[0] * w[1] - u[1] * w[0];
+            }
+            for (int d = 0; d < 3; ++d) c[0][d] = -(c[1][d] + c[2][d] + c[3][d]);
+            const double det = E[0][0] * c[1][0] + E[0][1] * c[1][1] + E[0][2] * c[1][2];
+            const double ad = fabs(det), sg = det > 0.0 ? 1.0 : -1.0;
+            V += ad;
+            for (int b = 0; b < 4; ++b) {
+                // slot of column v[b] in row i (columns ascending)
+                int lo = e0, hi = e1 - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((col[mid] & 0x7fffffff) < v[b]) lo = mid + 1; else hi = mid;
+                }
+                const double kab = (c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2]) / ad;
+                Dbl4 x = A64[lo];
+                x.x += kab;
+                x.y += sg * c[a][0];
+                x.z += sg * c[a][1];
+                x.w += sg * c[a][2];
+                A64[lo] = x;
+                Dbl4 y = Bt64[lo];
+                y.x += sg * c[b][0];
+                y.y += sg * c[b][1];
+                y.z += sg * c[b][2];
+                Bt64[lo] = y;
+            }
+        }
+        Vn[i] = V;
+        for (int e = e0; e < e1; ++e) {
+            const Dbl4 x = A64[e], y = Bt64[e];
+            A32[e] = make_float4((float)x.x, (float)x.y, (float)x.z, (float)x.w);
+            Bt32[e] = make_float4((float)y.x, (float)y.y, (float)y.z, 0.f);
+            if ((col[e] & 0x7fffffff) == i) {
+                d64[i] = x.x;
+                d32[i] = (float)x.x;
+            }
+        }
+    }
+}
+
+// Stiffness-only CSR of a general mesh: the entries with K != 0, packed as
+// (column << 8) | 1 (the low byte only marks a present entry), values apart.
+__global__ void k_kcsr_count_gen(int N, const int* rowptr, const Dbl4* A64, int* cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) c += A64[e].x != 0.0;
+        cnt[i] = c;
+    }
+}
+
+__global__ void k_kcsr_fill_gen(int N, const int* rowptr, const int* col, const Dbl4* A64, const int* kptr,
+                                int* kent, double* k64, float* k32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int o = kptr[i];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const double k = A64[e].x;
+            if (k != 0.0) {
+                kent[o] = (int)(((unsigned)(col[e] & 0x7fffffff) << 8) | 1u);
+                k64[o] = k;
+                k32[o] = (float)k;
+                ++o;
+            }
+        }
     }
 }
 
@@ -353,15 +479,8 @@ static void surface_triangles(int n, std::vector<int>& tris) {
 void host_boundary_topology(int n, std::vector<int>& tris, const std::vector<int>& bidx,
                             std::vector<int>& inc_ptr, std::vector<int>& inc_slot) {
     surface_triangles(n, tris);
-    const int n1 = n + 1, N = n1 * n1 * n1, nb = (int)bidx.size(), F = (int)tris.size() / 3;
-    std::vector<int> pos(N, -1);
-    for (int k = 0; k < nb; ++k) pos[bidx[k]] = k;
-    inc_ptr.assign(nb + 1, 0);
-    for (int s = 0; s < 3 * F; ++s) inc_ptr[pos[tris[s]] + 1] += 1;
-    for (int k = 0; k < nb; ++k) inc_ptr[k + 1] += inc_ptr[k];
-    inc_slot.assign(3 * F, 0);
-    std::vector<int> fill(inc_ptr.begin(), inc_ptr.end() - 1);
-    for (int s = 0; s < 3 * F; ++s) inc_slot[fill[pos[tris[s]]]++] = s;   // ascending slots per node
+    const int n1 = n + 1;
+    host_incidence(n1 * n1 * n1, tris, bidx, inc_ptr, inc_slot);
 }
 
 void launch_row_counts(int n, int* cnt, int* bflag, cudaStream_t st) {
@@ -391,9 +510,166 @@ void launch_tets(int n, int* tets, cudaStream_t st) {
     k_tets<<<(T + 255) / 256, 256, 0, st>>>(n, tets);
 }
 void launch_bem_assemble(int n, int nb, int F, const int* bidx, const int* tris, const int* inc_ptr,
-                         const int* inc_slot, double* scratch, int nblocks, double* B64, float* B32,
-                         cudaStream_t st) {
-    k_bem_assemble<<<nblocks, 256, 0, st>>>(n, nb, F, bidx, tris, inc_ptr, inc_slot, scratch, B64, B32);
+                         const int* inc_slot, const double* xyz, double* scratch, int nblocks, double* B64,
+                         float* B32, cudaStream_t st) {
+    k_bem_assemble<<<nblocks, 256, 0, st>>>(n, nb, F, bidx, tris, inc_ptr, inc_slot, xyz, scratch, B64, B32);
+}
+void launch_assemble_gen(int N, const double* xyz, const int* tets, const int* nt_ptr, const int* nt_idx,
+                         const int* rowptr, const int* col, Dbl4* A64, float4* A32, Dbl4* Bt64,
+                         float4* Bt32, double* Vn, double* d64, float* d32, cudaStream_t st) {
+    k_assemble_gen<<<(N + 127) / 128, 128, 0, st>>>(N, xyz, tets, nt_ptr, nt_idx, rowptr, col, A64, A32, Bt64,
+                                                   Bt32, Vn, d64, d32);
+}
+void launch_kcsr_count_gen(int N, const int* rowptr, const Dbl4* A64, int* cnt, cudaStream_t st) {
+    k_kcsr_count_gen<<<(N + 255) / 256, 256, 0, st>>>(N, rowptr, A64, cnt);
+}
+void launch_kcsr_fill_gen(int N, const int* rowptr, const int* col, const Dbl4* A64, const int* kptr, int* kent,
+                          double* k64, float* k32, cudaStream_t st) {
+    k_kcsr_fill_gen<<<(N + 255) / 256, 256, 0, st>>>(N, rowptr, col, A64, kptr, kent, k64, k32);
+}
+
+// ---- general meshes: host topology ---------------------------------------------------
+// Validates the tetrahedra, builds the node -> tetrahedron incidence (ascending
+// tetrahedron ids), the CSR pattern (per row: the sorted distinct vertices of
+// the incident tetrahedra), the surface (faces of exactly one tetrahedron,
+// outward: the normal points away from the fourth vertex; smallest id first,
+// cyclic order kept, rows sorted), the surface node ids (ascending) and the
+// length unit L = (mean |det|)^(1/3).  Returns an empty string or the reason
+// the mesh is rejected.
+std::string host_general_topology(int N, int T, const int* tets, const double* xyz, GeneralTopology& g) {
+    char buf[256];
+    for (int t = 0; t < T; ++t) {
+        const int* v = tets + 4 * (size_t)t;
+        for (int k = 0; k < 4; ++k) {
+            if (v[k] < 0 || v[k] >= N) {
+                snprintf(buf, sizeof buf, "tetrahedron %d has node id %d outside [0, %d)", t, v[k], N);
+                return buf;
+            }
+            for (int l = 0; l < k; ++l)
+                if (v[l] == v[k]) {
+                    snprintf(buf, sizeof buf, "tetrahedron %d repeats node %d", t, v[k]);
+                    return buf;
+                }
+        }
+    }
+    g.nt_ptr.assign(N + 1, 0);
+    for (size_t s = 0; s < 4 * (size_t)T; ++s) g.nt_ptr[tets[s] + 1] += 1;
+    for (int i = 0; i < N; ++i) {
+        if (g.nt_ptr[i + 1] == 0) {
+            snprintf(buf, sizeof buf, "node %d belongs to no tetrahedron", i);
+            return buf;
+        }
+        g.nt_ptr[i + 1] += g.nt_ptr[i];
+    }
+    g.nt_idx.assign(4 * (size_t)T, 0);
+    {
+        std::vector<int> fill(g.nt_ptr.begin(), g.nt_ptr.end() - 1);
+        for (int t = 0; t < T; ++t)
+            for (int k = 0; k < 4; ++k) g.nt_idx[fill[tets[4 * (size_t)t + k]]++] = t;
+    }
+    // determinants and the length unit
+    double sum_ad = 0.0;
+    g.det.assign(T, 0.0);
+    for (int t = 0; t < T; ++t) {
+        const int* v = tets + 4 * (size_t)t;
+        double e[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int d = 0; d < 3; ++d) e[k][d] = xyz[3 * (size_t)v[k + 1] + d] - xyz[3 * (size_t)v[0] + d];
+        const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) +
+                           e[0][1] * (e[1][2] * e[2][0] - e[1][0] * e[2][2]) +
+                           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        if (!(det != 0.0) || !std::isfinite(det)) {
+            snprintf(buf, sizeof buf, "tetrahedron %d is degenerate (zero or non-finite volume)", t);
+            return buf;
+        }
+        g.det[t] = det;
+        sum_ad += fabs(det);
+    }
+    g.L = cbrt(sum_ad / (double)T);
+    // CSR pattern
+    g.rowptr.assign(N + 1, 0);
+    g.col.clear();
+    std::vector<int> nb;
+    for (int i = 0; i < N; ++i) {
+        nb.clear();
+        for (int q = g.nt_ptr[i]; q < g.nt_ptr[i + 1]; ++q)
+            for (int k = 0; k < 4; ++k) nb.push_back(tets[4 * (size_t)g.nt_idx[q] + k]);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        g.col.insert(g.col.end(), nb.begin(), nb.end());
+        g.rowptr[i + 1] = (int)g.col.size();
+    }
+    // surface faces
+    struct Face { int k[3]; int t, opp; int v[3]; };
+    std::vector<Face> faces(4 * (size_t)T);
+    for (int t = 0; t < T; ++t)
+        for (int o = 0; o < 4; ++o) {
+            Face& f = faces[4 * (size_t)t + o];
+            int c = 0;
+            for (int k = 0; k < 4; ++k)
+                if (k != o) f.v[c++] = tets[4 * (size_t)t + k];
+            f.k[0] = f.v[0]; f.k[1] = f.v[1]; f.k[2] = f.v[2];
+            std::sort(f.k, f.k + 3);
+            f.t = t;
+            f.opp = tets[4 * (size_t)t + o];
+        }
+    std::sort(faces.begin(), faces.end(), [](const Face& a, const Face& b) {
+        if (a.k[0] != b.k[0]) return a.k[0] < b.k[0];
+        if (a.k[1] != b.k[1]) return a.k[1] < b.k[1];
+        if (a.k[2] != b.k[2]) return a.k[2] < b.k[2];
+        return a.t < b.t;
+    });
+    std::vector<std::array<int, 3>> tris;
+    for (size_t s = 0; s < faces.size();) {
+        size_t e = s + 1;
+        while (e < faces.size() && faces[e].k[0] == faces[s].k[0] && faces[e].k[1] == faces[s].k[1] &&
+               faces[e].k[2] == faces[s].k[2])
+            ++e;
+        if (e - s > 2) {
+            snprintf(buf, sizeof buf, "face (%d, %d, %d) belongs to %d tetrahedra", faces[s].k[0], faces[s].k[1],
+                     faces[s].k[2], (int)(e - s));
+            return buf;
+        }
+        if (e - s == 1) {
+            const Face& f = faces[s];
+            const double* a = xyz + 3 * (size_t)f.v[0];
+            const double* b = xyz + 3 * (size_t)f.v[1];
+            const double* c = xyz + 3 * (size_t)f.v[2];
+            const double* o = xyz + 3 * (size_t)f.opp;
+            const double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+            const double ac[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+            const double nr[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2],
+                                  ab[0] * ac[1] - ab[1] * ac[0]};
+            const double side = nr[0] * (o[0] - a[0]) + nr[1] * (o[1] - a[1]) + nr[2] * (o[2] - a[2]);
+            std::array<int, 3> tri = {f.v[0], f.v[1], f.v[2]};
+            if (side > 0) std::swap(tri[1], tri[2]);
+            const int r = (tri[1] < tri[0] && tri[1] < tri[2]) ? 1 : (tri[2] < tri[0] && tri[2] < tri[1]) ? 2 : 0;
+            tris.push_back({tri[r], tri[(r + 1) % 3], tri[(r + 2) % 3]});
+        }
+        s = e;
+    }
+    if (tris.empty()) return "the mesh has no surface";
+    std::sort(tris.begin(), tris.end());
+    g.tris.resize(3 * tris.size());
+    for (size_t t = 0; t < tris.size(); ++t)
+        for (int k = 0; k < 3; ++k) g.tris[3 * t + k] = tris[t][k];
+    g.bidx = g.tris;
+    std::sort(g.bidx.begin(), g.bidx.end());
+    g.bidx.erase(std::unique(g.bidx.begin(), g.bidx.end()), g.bidx.end());
+    return std::string();
+}
+
+void host_incidence(int N, const std::vector<int>& tris, const std::vector<int>& bidx, std::vector<int>& inc_ptr,
+                    std::vector<int>& inc_slot) {
+    const int nb = (int)bidx.size(), F = (int)tris.size() / 3;
+    std::vector<int> pos(N, -1);
+    for (int k = 0; k < nb; ++k) pos[bidx[k]] = k;
+    inc_ptr.assign(nb + 1, 0);
+    for (int s = 0; s < 3 * F; ++s) inc_ptr[pos[tris[s]] + 1] += 1;
+    for (int k = 0; k < nb; ++k) inc_ptr[k + 1] += inc_ptr[k];
+    inc_slot.assign(3 * F, 0);
+    std::vector<int> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int s = 0; s < 3 * F; ++s) inc_slot[fill[pos[tris[s]]]++] = s;   // ascending slots per node
 }
 
 }  // namespace lbm

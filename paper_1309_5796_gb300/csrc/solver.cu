@@ -15,6 +15,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <type_traits>
+
 #include "lbm_host.h"
 
 namespace lbm {
@@ -79,11 +81,14 @@ __device__ __forceinline__ void block_reduce_inst(double (&v)[NQV], double* scra
 
 // Column sums for threads that each hold VEC consecutive columns: thread tid is
 // row lane rl = tid / G of column group g = tid % G (columns g*VEC .. +VEC-1,
-// C = G*VEC).  Fixed summation order; totals in out[q*C + c].  `scratch` holds
-// at least NQV * max(bd/32, RB) * C doubles.
-template <int NQV, int VEC>
-__device__ __forceinline__ void block_reduce_cols(double (&v)[NQV][VEC], double* scratch, double* out, int C,
-                                                  int G, int RB) {
+// C = G*VEC).  Fixed summation order; totals in out[q*C + c] (FP64).  The sums
+// inside the block are taken in R (FP32 for the per-iteration dot products of
+// the FP32 solves, whose per-thread partials are FP32 already: GB300 issues
+// FP64 at a small fraction of the FP32 rate).  `scratch` holds at least
+// NQV * max(bd/32, RB) * C values of R.
+template <int NQV, int VEC, typename R = double>
+__device__ __forceinline__ void block_reduce_cols(R (&v)[NQV][VEC], R* scratch, double* out, int C, int G,
+                                                  int RB) {
     const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, g = tid % G;
     int nrow;
     if (G <= 32 && (32 % G) == 0) {
@@ -111,9 +116,9 @@ __device__ __forceinline__ void block_reduce_cols(double (&v)[NQV][VEC], double*
     __syncthreads();
     for (int t = tid; t < NQV * C; t += bd) {
         const int q = t / C, c = t % C;
-        double acc = 0.0;
+        R acc = R(0);
         for (int r = 0; r < nrow; ++r) acc += scratch[(q * nrow + r) * C + c];
-        out[q * C + c] = acc;
+        out[q * C + c] = (double)acc;
     }
     __syncthreads();
 }
@@ -164,16 +169,77 @@ __device__ __forceinline__ void vstore(T* p, const T (&d)[VEC]) {
     *reinterpret_cast<V*>(p) = x;
 }
 
+constexpr double MP_INNER = 1e-4;   // residual reduction of one FP32 cycle of a mixed-iteration solve
+constexpr int MP_MAX_CYCLES = 16;
 constexpr int MAXK = 8;   // stiffness entries served by the unrolled gather (interior Kuhn rows: 7)
+
+// Value tables of a general mesh in the precision of the kernel.
+template <typename T> struct GenTab;
+template <> struct GenTab<float> {
+    using V4 = float4;
+    static __device__ __forceinline__ const float4* A(const MeshView& M) { return M.gA32; }
+    static __device__ __forceinline__ const float4* Bt(const MeshView& M) { return M.gB32; }
+    static __device__ __forceinline__ const float* k(const MeshView& M) { return M.gk32; }
+    static __device__ __forceinline__ const float* d(const MeshView& M) { return M.gd32; }
+};
+template <> struct GenTab<double> {
+    using V4 = Dbl4;
+    static __device__ __forceinline__ const Dbl4* A(const MeshView& M) { return M.gA64; }
+    static __device__ __forceinline__ const Dbl4* Bt(const MeshView& M) { return M.gB64; }
+    static __device__ __forceinline__ const double* k(const MeshView& M) { return M.gk64; }
+    static __device__ __forceinline__ const double* d(const MeshView& M) { return M.gd64; }
+};
 
 // acc[k] = sum_j K_ij (v_j - v_i) (DIFF) or sum_j K_ij v_j for VEC consecutive
 // columns of one row of the stiffness-only CSR.  The packed entries are read
 // first -- one load per lane and a warp broadcast when the whole warp works on
 // this row (warp_row) -- then every vector gather of the row is issued before
 // any arithmetic.  warp_row requires the full warp to take part.
-template <typename T, int VEC, bool CG, bool DIFF>
-__device__ __forceinline__ void row_kv(const int* __restrict__ kent, int e0, int e1, const T* v, int C, int c0,
-                                       const T (&vi)[VEC], T (&acc)[VEC], bool warp_row) {
+// General meshes (GEN): the values come from kval, and rows of any length are
+// served MAXK entries at a time.
+template <typename T, int VEC, bool CG, bool DIFF, bool GEN>
+__device__ __forceinline__ void row_kv(const int* __restrict__ kent, const T* __restrict__ kval, int e0, int e1,
+                                       const T* v, int C, int c0, const T (&vi)[VEC], T (&acc)[VEC],
+                                       bool warp_row) {
+    if constexpr (GEN) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc[k] = T(0);
+        for (int base = e0; base < e1; base += MAXK) {
+            int w[MAXK];
+            T kv[MAXK];
+            if (warp_row) {
+                const int lane = threadIdx.x & 31;
+                const bool has = lane < MAXK && base + lane < e1;
+                const int mine = has ? __ldg(&kent[base + lane]) : 0;
+                const T mk = has ? __ldg(&kval[base + lane]) : T(0);
+#pragma unroll
+                for (int t = 0; t < MAXK; ++t) {
+                    w[t] = __shfl_sync(0xffffffffu, mine, t);
+                    kv[t] = __shfl_sync(0xffffffffu, mk, t);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < MAXK; ++t) {
+                    const bool has = base + t < e1;
+                    w[t] = has ? __ldg(&kent[base + t]) : 0;
+                    kv[t] = has ? __ldg(&kval[base + t]) : T(0);
+                }
+            }
+            T vj[MAXK][VEC];
+#pragma unroll
+            for (int t = 0; t < MAXK; ++t) {
+                if (w[t] != 0) vload<T, VEC, CG>(vj[t], &v[(size_t)((unsigned)w[t] >> 8) * C + c0]);
+                else
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
+            }
+#pragma unroll
+            for (int t = 0; t < MAXK; ++t)
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) acc[k] += kv[t] * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
+        }
+        return;
+    }
     int w[MAXK];
     if (warp_row) {
         const int lane = threadIdx.x & 31;
@@ -258,14 +324,21 @@ __device__ __forceinline__ bool grid_reduce(const double* part, int q0, int C, d
 }
 
 // b_i = (1/4) sum_j Gint_ij . m_j (the divergence right-hand side) at the trial point
-template <typename T>
-__device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* __restrict__ pkA, int e0, int e1,
+template <typename T, bool GEN>
+__device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* __restrict__ pkA,
+                                        const typename GenTab<T>::V4* __restrict__ gA, int e0, int e1,
                                         const double* meval, int B, int b) {
     T acc = T(0);
     for (int e = e0; e < e1; ++e) {
-        const int w = __ldg(&pkA[e]);
         const size_t mj = (size_t)(__ldg(&col[e]) & 0x7fffffff) * 3 * B + b;
-        acc += T(sbyte(w, 1)) * T(meval[mj]) + T(sbyte(w, 2)) * T(meval[mj + B]) + T(sbyte(w, 3)) * T(meval[mj + 2 * B]);
+        if constexpr (GEN) {
+            const typename GenTab<T>::V4 a = gA[e];
+            acc += a.y * T(meval[mj]) + a.z * T(meval[mj + B]) + a.w * T(meval[mj + 2 * B]);
+        } else {
+            const int w = __ldg(&pkA[e]);
+            acc += T(sbyte(w, 1)) * T(meval[mj]) + T(sbyte(w, 2)) * T(meval[mj + B]) +
+                   T(sbyte(w, 3)) * T(meval[mj + 2 * B]);
+        }
     }
     return 0.25 * (double)acc;
 }
@@ -285,10 +358,11 @@ __device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* 
 // Neumann systems: the right-hand side is made consistent (mean removed), the
 // residual is tested without its mean, and the solution is gauged to zero
 // V-weighted mean.  Dirichlet systems freeze the surface rows (p = q = r = z = 0).
-template <typename T, bool SINGLE, int VEC>
+template <typename T, bool SINGLE, int VEC, bool GEN, bool MP>
 __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) k_pcg(PcgArgs<T> A) {
     extern __shared__ double sm[];
     constexpr bool CG = !SINGLE;
+    using W = typename std::conditional<MP, float, T>::type;   // precision of the iteration
     const int bd = blockDim.x, tid = threadIdx.x;
     const int B = A.V.B, C = 2 * B, G = C / VEC, RB = bd / G;
     const bool lane = tid < RB * G;
@@ -303,16 +377,19 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     double* s_rhop = s_rho + C;
     double* s_ab = s_rhop + C;
     double* s_tol = s_ab + C;
-    int* s_flag = (int*)(s_tol + C);
+    double* s_tin = s_tol + C;                          // MP: tolerance of the current cycle
+    int* s_flag = (int*)(s_tin + C);
     int* s_act = s_flag + C;
     int* s_cur = s_act + C;
     int* s_it = s_cur + C;
-    __shared__ int s_all;
+    int* s_done = s_it + C;                             // MP: true residual met the tolerance
 
     for (int i = tid; i < C; i += bd) {
         s_act[i] = A.V.st[i % B].phase != PH_DONE;
         s_cur[i] = A.V.st[i % B].cur;
         s_it[i] = 0;
+        s_done[i] = 0;
+        s_tin[i] = 0.0;
         s_rhop[i] = 1.0;
     }
     __syncthreads();
@@ -337,11 +414,16 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     const int* __restrict__ node = A.M.node;
     const int* __restrict__ kptr = A.M.kptr;
     const int* __restrict__ kent = A.M.kent;
+    const T* __restrict__ kvalT = GEN ? GenTab<T>::k(A.M) : nullptr;
+    const W* __restrict__ kvalW = GEN ? GenTab<W>::k(A.M) : nullptr;
+    const W* __restrict__ kdiagW = GEN ? GenTab<W>::d(A.M) : nullptr;
+    const typename GenTab<T>::V4* __restrict__ gA = GEN ? GenTab<T>::A(A.M) : nullptr;
     T* __restrict__ x = mode ? A.V.U2 : A.V.U1;
-    T* __restrict__ r = A.V.r;
-    T* __restrict__ z = A.V.z;
-    T* __restrict__ p = A.V.p;
-    T* __restrict__ q = A.V.q;
+    // work vectors in W (MP: FP32 values in the FP64 arrays' storage)
+    W* __restrict__ r = reinterpret_cast<W*>(A.V.r);
+    W* __restrict__ z = reinterpret_cast<W*>(A.V.z);
+    W* __restrict__ p = reinterpret_cast<W*>(A.V.p);
+    W* __restrict__ q = reinterpret_cast<W*>(A.V.q);
     double* part = A.V.part;
     unsigned epoch = 0;
 
@@ -354,7 +436,8 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     unsigned red_idx = 0;
     auto reduce = [&](auto& vals, int q0) -> bool {
         constexpr int NQV = sizeof(vals) / sizeof(vals[0]);
-        block_reduce_cols<NQV, VEC>(vals, scratch, out, C, G, RB);
+        using R = typename std::remove_reference<decltype(vals[0][0])>::type;
+        block_reduce_cols<NQV, VEC, R>(vals, reinterpret_cast<R*>(scratch), out, C, G, RB);
         if constexpr (SINGLE) {
             return true;
         } else {
@@ -382,7 +465,14 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                     x[(size_t)row * C + c0 + k] = mode ? A.V.ub_out[(size_t)(bp - 1) * C + bk[k]] : T(0);
         }
     if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
-    {   // residual of the warm start
+    // One cycle: the residual of the current x in the precision of x (T), then
+    // preconditioned CG iterations in the work precision W.  MP (FP64 x, FP32
+    // work vectors): a cycle ends when the FP32 recurrence has reduced the
+    // residual by MP_INNER (or reached the tolerance); the next cycle replaces it
+    // by the true FP64 residual and restarts CG from there, so the test that
+    // ends the solve is always taken on the FP64 residual.
+    for (int cycle = 0;; ++cycle) {
+    {   // residual of the current x
         double psum[1][VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) psum[0][k] = 0.0;
@@ -391,17 +481,19 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 const int nd = node[row];
                 const int bp = (int)((unsigned)nd >> 16);
                 const size_t ib = (size_t)row * C + c0;
-                T xi[VEC], kx[VEC], rv[VEC], zv[VEC];
+                T xi[VEC], kx[VEC];
+                W rv[VEC], zv[VEC];
                 vload<T, VEC, false>(xi, &x[ib]);
-                row_kv<T, VEC, CG, true>(kent, kptr[row], kptr[row + 1], x, C, c0, xi, kx, warp_row);
+                row_kv<T, VEC, CG, true, GEN>(kent, kvalT, kptr[row], kptr[row + 1], x, C, c0, xi, kx, warp_row);
                 const int e0 = rowptr[row], e1 = rowptr[row + 1];
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
-                    if (!neu[k] && bp) { rv[k] = T(0); zv[k] = T(0); continue; }
+                    if (!neu[k] && bp) { rv[k] = W(0); zv[k] = W(0); continue; }
                     // f: the right-hand side (b in every system but the stage-2 forward one)
                     double f = 0.0;
                     if (!(mode == 1 && !neu[k]) && actk[k])
-                        f = rhs_b<T>(col, pkA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k]);
+                        f = rhs_b<T, GEN>(col, pkA, gA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B,
+                                          bk[k]);
                     if (mode == 1 && neu[k] && bp) f += (double)A.V.ub_out[(size_t)(bp - 1) * C + c0 + k];
                     double ref = f;   // norm reference: f (Neumann), f - K_IS x_S (Dirichlet)
                     if (!neu[k])
@@ -409,25 +501,26 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                             const int ww = kent[e];
                             const int j = (int)((unsigned)ww >> 8);
                             if ((unsigned)node[j] >> 16)
-                                ref -= (double)sbyte(ww, 0) * (double)ld_vec<T, CG>(&x[(size_t)j * C + c0 + k]);
+                                ref -= (GEN ? (double)kvalT[e] : (double)sbyte(ww, 0)) *
+                                       (double)ld_vec<T, CG>(&x[(size_t)j * C + c0 + k]);
                         }
-                    rv[k] = T(f) - kx[k];
-                    zv[k] = T(ref);                       // kept for the second pass
+                    rv[k] = W(T(f) - kx[k]);
+                    zv[k] = W(ref);                       // kept for the second pass
                     if (actk[k]) psum[0][k] += f;
                 }
-                const T zero[VEC] = {};
-                vstore<T, VEC>(&r[ib], rv);
-                vstore<T, VEC>(&z[ib], zv);
-                vstore<T, VEC>(&p[ib], zero);
-                vstore<T, VEC>(&q[ib], zero);
+                const W zero[VEC] = {};
+                vstore<W, VEC>(&r[ib], rv);
+                vstore<W, VEC>(&z[ib], zv);
+                vstore<W, VEC>(&p[ib], zero);
+                vstore<W, VEC>(&q[ib], zero);
             }
         // Neumann: consistent right-hand side (sum zero)
         if (!reduce(psum, 2)) return;
         if (tid < C) s_ab[tid] = out[tid] / (double)N;
         __syncthreads();
-        T mean[VEC];
+        W mean[VEC];
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) mean[k] = neu[k] ? T(s_ab[c0 + k]) : T(0);
+        for (int k = 0; k < VEC; ++k) mean[k] = neu[k] ? W(s_ab[c0 + k]) : W(0);
         double v4[4][VEC];   // r.z, r.r, ref.ref, sum r
 #pragma unroll
         for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = 0.0;
@@ -436,14 +529,14 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 const int nd = node[row];
                 const bool surf = ((unsigned)nd >> 16) != 0;
                 const size_t ib = (size_t)row * C + c0;
-                const T dinv = T(1) / T((nd >> 8) & 0xff);
-                T rv[VEC], zv[VEC];
-                vload<T, VEC, false>(rv, &r[ib]);
-                vload<T, VEC, false>(zv, &z[ib]);
+                const W dinv = W(1) / (GEN ? kdiagW[row] : W((nd >> 8) & 0xff));
+                W rv[VEC], zv[VEC];
+                vload<W, VEC, false>(rv, &r[ib]);
+                vload<W, VEC, false>(zv, &z[ib]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     if (!neu[k] && surf) continue;
-                    const T ref = zv[k] - mean[k];
+                    const W ref = zv[k] - mean[k];
                     rv[k] -= mean[k];
                     zv[k] = rv[k] * dinv;
                     if (actk[k]) {
@@ -453,8 +546,8 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                         v4[3][k] += (double)rv[k];
                     }
                 }
-                vstore<T, VEC>(&r[ib], rv);
-                vstore<T, VEC>(&z[ib], zv);
+                vstore<W, VEC>(&r[ib], rv);
+                vstore<W, VEC>(&z[ib], zv);
             }
         if (!reduce(v4, 0)) return;
     }
@@ -467,93 +560,91 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
             // which rounding feeds and CG cannot remove
             const double sr = out[3 * C + tid];
             const double rr = nn ? fmax(out[C + tid] - sr * sr / (double)N, 0.0) : out[C + tid];
-            if (it == 0) s_tol[tid] = A.tol2 * out[2 * C + tid];
-            const int conv = !s_act[tid] || rr <= s_tol[tid] || it >= A.max_iter;
+            int conv;
+            if constexpr (MP) {
+                if (it == 0) {   // rr is the true (FP64) residual of this cycle
+                    s_tol[tid] = A.tol2 * out[2 * C + tid];
+                    s_done[tid] = !s_act[tid] || rr <= s_tol[tid] || s_it[tid] >= A.max_iter;
+                    s_tin[tid] = fmax(s_tol[tid], MP_INNER * MP_INNER * rr);
+                }
+                conv = s_done[tid] || rr <= s_tin[tid] || s_it[tid] >= A.max_iter;
+            } else {
+                if (it == 0) s_tol[tid] = A.tol2 * out[2 * C + tid];
+                conv = !s_act[tid] || rr <= s_tol[tid] || it >= A.max_iter;
+            }
             s_ab[tid] = (it == 0 || conv) ? 0.0 : rho / s_rhop[tid];
             s_rho[tid] = rho;
             s_flag[tid] = conv;
         }
-        __syncthreads();
-        if (tid == 0) {
-            int all = 1;
-            for (int i = 0; i < C; ++i) all &= s_flag[i];
-            s_all = all;
-        }
-        __syncthreads();
-        if (s_all) break;
+        // C <= blockDim.x: one flag per thread, combined by the barrier itself
+        if (__syncthreads_and(tid < C ? s_flag[tid] : 1)) break;
         bool run = false;
-        T beta[VEC];
+        W beta[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
             run |= actk[k] && !s_flag[c0 + k];
-            beta[k] = T(s_ab[c0 + k]);
+            beta[k] = W(s_ab[c0 + k]);
         }
         const bool run_rows = warp_row ? (__any_sync(0xffffffffu, run) != 0) : run;
-        double ppq[1][VEC];
-        T tpq[VEC];   // per-thread partial sums in T; block and grid sums in FP64
+        W tpq[1][VEC];   // per-thread and block partial sums in W; grid sums in FP64
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) tpq[k] = T(0);
+        for (int k = 0; k < VEC; ++k) tpq[0][k] = W(0);
         if (run_rows)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 const bool surf = ((unsigned)nd >> 16) != 0;
                 const size_t ib = (size_t)row * C + c0;
-                T zi[VEC], w[VEC], pv[VEC], qv[VEC];
-                vload<T, VEC, false>(zi, &z[ib]);
-                row_kv<T, VEC, CG, false>(kent, kptr[row], kptr[row + 1], z, C, c0, zi, w, warp_row);
-                vload<T, VEC, false>(pv, &p[ib]);
-                vload<T, VEC, false>(qv, &q[ib]);
+                W zi[VEC], w[VEC], pv[VEC], qv[VEC];
+                vload<W, VEC, false>(zi, &z[ib]);
+                row_kv<W, VEC, CG, false, GEN>(kent, kvalW, kptr[row], kptr[row + 1], z, C, c0, zi, w, warp_row);
+                vload<W, VEC, false>(pv, &p[ib]);
+                vload<W, VEC, false>(qv, &q[ib]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     pv[k] = zi[k] + beta[k] * pv[k];
-                    qv[k] = (!neu[k] && surf) ? T(0) : w[k] + beta[k] * qv[k];
-                    tpq[k] += pv[k] * qv[k];
+                    qv[k] = (!neu[k] && surf) ? W(0) : w[k] + beta[k] * qv[k];
+                    tpq[0][k] += pv[k] * qv[k];
                 }
-                vstore<T, VEC>(&p[ib], pv);
-                vstore<T, VEC>(&q[ib], qv);
+                vstore<W, VEC>(&p[ib], pv);
+                vstore<W, VEC>(&q[ib], qv);
             }
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) ppq[0][k] = (double)tpq[k];
-        if (!reduce(ppq, 0)) return;
+        if (!reduce(tpq, 0)) return;
         if (tid < C) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
         __syncthreads();
         T alpha[VEC];
+        W alphaw[VEC];
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) alpha[k] = T(s_ab[c0 + k]);
-        double v4[4][VEC];
-        T t0[VEC], t1[VEC], t3[VEC];   // per-thread partial sums in T; block and grid sums in FP64
+        for (int k = 0; k < VEC; ++k) {
+            alpha[k] = T(s_ab[c0 + k]);
+            alphaw[k] = W(s_ab[c0 + k]);
+        }
+        W v4[4][VEC];   // r.z, r.r, (unused), sum r: per-thread and block sums in W, grid sums in FP64
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) t0[k] = t1[k] = t3[k] = T(0);
+        for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = W(0);
         if (run)
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 const size_t ib = (size_t)row * C + c0;
-                const T dinv = T(1) / T((nd >> 8) & 0xff);
-                T xv[VEC], rv[VEC], pv[VEC], qv[VEC], zv[VEC];
+                const W dinv = W(1) / (GEN ? kdiagW[row] : W((nd >> 8) & 0xff));
+                T xv[VEC];
+                W rv[VEC], pv[VEC], qv[VEC], zv[VEC];
                 vload<T, VEC, false>(xv, &x[ib]);
-                vload<T, VEC, false>(rv, &r[ib]);
-                vload<T, VEC, false>(pv, &p[ib]);
-                vload<T, VEC, false>(qv, &q[ib]);
+                vload<W, VEC, false>(rv, &r[ib]);
+                vload<W, VEC, false>(pv, &p[ib]);
+                vload<W, VEC, false>(qv, &q[ib]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
-                    xv[k] += alpha[k] * pv[k];
-                    rv[k] -= alpha[k] * qv[k];
+                    xv[k] += alpha[k] * T(pv[k]);
+                    rv[k] -= alphaw[k] * qv[k];
                     zv[k] = rv[k] * dinv;
-                    t0[k] += rv[k] * zv[k];
-                    t1[k] += rv[k] * rv[k];
-                    t3[k] += rv[k];
+                    v4[0][k] += rv[k] * zv[k];
+                    v4[1][k] += rv[k] * rv[k];
+                    v4[3][k] += rv[k];
                 }
                 vstore<T, VEC>(&x[ib], xv);
-                vstore<T, VEC>(&r[ib], rv);
-                vstore<T, VEC>(&z[ib], zv);
+                vstore<W, VEC>(&r[ib], rv);
+                vstore<W, VEC>(&z[ib], zv);
             }
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-            v4[0][k] = (double)t0[k];
-            v4[1][k] = (double)t1[k];
-            v4[2][k] = 0.0;
-            v4[3][k] = (double)t3[k];
-        }
         // quantity 2 (ref.ref) is carried over from the prologue in `out`
         double keep2[1];
         if (tid < C) keep2[0] = out[2 * C + tid];
@@ -564,6 +655,14 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
             out[2 * C + tid] = keep2[0];
         }
         __syncthreads();
+    }
+    if constexpr (!MP) {
+        break;
+    } else {
+        // done when every column met the tolerance on its true residual at the
+        // start of this cycle (or ran out of iterations or cycles)
+        if (__syncthreads_and(tid < C ? s_done[tid] : 1) || cycle + 1 >= MP_MAX_CYCLES) break;
+    }
     }
     if (blockIdx.x == 0) {
         for (int i = tid; i < C; i += bd) {
@@ -585,7 +684,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     for (int k = 0; k < VEC; ++k) pv[0][k] = 0.0;
     if (any_act)
         for (int row = row0; row < N; row += rstride) {
-            const double vi = (double)(node[row] & 0xff);
+            const double vi = GEN ? A.M.gV[row] : (double)(node[row] & 0xff);
             T xv[VEC];
             vload<T, VEC, false>(xv, &x[(size_t)row * C + c0]);
 #pragma unroll
@@ -607,7 +706,8 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
             T xv[VEC];
             vload<T, VEC, false>(xv, &x[ib]);
             T kw[VEC];
-            if (kw_rows && bp) row_kv<T, VEC, CG, false>(kent, kptr[row], kptr[row + 1], x, C, c0, xv, kw, warp_row);
+            if (kw_rows && bp)
+                row_kv<T, VEC, CG, false, GEN>(kent, kvalT, kptr[row], kptr[row + 1], x, C, c0, xv, kw, warp_row);
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
                 if (!actk[k]) continue;
@@ -616,8 +716,8 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                     if (mode == 0 && bp) A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] = xv[k];
                 } else if (mode == 0 && bp) {
                     A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] =
-                        T(rhs_b<T>(col, pkA, rowptr[row], rowptr[row + 1],
-                                A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k])) - kw[k];
+                        T(rhs_b<T, GEN>(col, pkA, gA, rowptr[row], rowptr[row + 1],
+                                        A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k])) - kw[k];
                 }
             }
             vstore<T, VEC>(&x[ib], xv);
@@ -626,44 +726,58 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
 
 size_t pcg_part_elems(int num_sms, int B) { return (size_t)2 * num_sms * (2 * B) * 4; }
 
-template <typename T, bool SINGLE, int VEC>
+template <typename T, bool SINGLE, int VEC, bool GEN, bool MP>
 static cudaError_t launch_pcg(const Launch& L, const MeshView& M, PcgArgs<T>& a, int C) {
     const int bd = SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS;
     const int G = C / VEC, RB = bd / G;
     const int nrow_red = (G <= 32 && (32 % G) == 0) ? (bd >> 5) : RB;
-    const size_t smem = sizeof(double) * (4 * (size_t)nrow_red * C + 8 * (size_t)C) + sizeof(int) * 4 * C;
+    const size_t smem = sizeof(double) * (4 * (size_t)nrow_red * C + 9 * (size_t)C) + sizeof(int) * 5 * C;
     static bool attr_set = false;
     static int occ = 0;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_pcg<T, SINGLE, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_pcg<T, SINGLE, VEC, GEN, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (!SINGLE) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, SINGLE, VEC>, bd, 200 * 1024);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, SINGLE, VEC, GEN, MP>, bd, 200 * 1024);
             if (occ < 1) occ = 1;
             if (occ > 1) occ = 1;   // the partials buffer holds one block per SM
         }
         attr_set = true;
     }
     void* args[] = {&a};
-    if (SINGLE) return cudaLaunchKernel((void*)k_pcg<T, SINGLE, VEC>, dim3(1), dim3(bd), args, smem, L.stream);
+    if (SINGLE) return cudaLaunchKernel((void*)k_pcg<T, SINGLE, VEC, GEN, MP>, dim3(1), dim3(bd), args, smem, L.stream);
     int nblk = (M.N + RB - 1) / RB;
     int maxblk = occ * L.num_sms;
     if (L.max_blocks > 0 && L.max_blocks < maxblk) maxblk = L.max_blocks;
     if (nblk > maxblk) nblk = maxblk;
     cudaMemsetAsync(L.bar, 0, sizeof(unsigned), L.stream);
-    return cudaLaunchCooperativeKernel((void*)k_pcg<T, SINGLE, VEC>, dim3(nblk), dim3(bd), args, smem, L.stream);
+    return cudaLaunchCooperativeKernel((void*)k_pcg<T, SINGLE, VEC, GEN, MP>, dim3(nblk), dim3(bd), args, smem, L.stream);
 }
 
+template <typename T, bool GEN, bool MP>
+static cudaError_t dispatch_pcg(const Launch& L, const MeshView& M, PcgArgs<T>& a, int C, bool single) {
+    constexpr int V4 = sizeof(T) == 4 ? 4 : 2;
+    const bool vec4 = (sizeof(T) == 4) && (C % 4 == 0);
+    if (single) return vec4 ? launch_pcg<T, true, V4, GEN, MP>(L, M, a, C) : launch_pcg<T, true, 2, GEN, MP>(L, M, a, C);
+    return vec4 ? launch_pcg<T, false, V4, GEN, MP>(L, M, a, C) : launch_pcg<T, false, 2, GEN, MP>(L, M, a, C);
+}
+
+// mixed_iter (FP64 only): iterate in FP32 with FP64 residual replacement.
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
-              int* iters_dev) {
-    (void)iters_dev;
+              bool mixed_iter) {
     const int C = 2 * V.B;
     PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps, L.fin};
     const bool single = (long long)M.N * C <= SINGLE_CTA_MAX_WORK;
-    const bool vec4 = (sizeof(T) == 4) && (C % 4 == 0);
     cudaError_t e;
-    if (single) e = vec4 ? launch_pcg<T, true, (sizeof(T) == 4 ? 4 : 2)>(L, M, a, C) : launch_pcg<T, true, 2>(L, M, a, C);
-    else e = vec4 ? launch_pcg<T, false, (sizeof(T) == 4 ? 4 : 2)>(L, M, a, C) : launch_pcg<T, false, 2>(L, M, a, C);
+    if constexpr (sizeof(T) == 8) {
+        if (mixed_iter) {
+            e = M.gen ? dispatch_pcg<T, true, true>(L, M, a, C, single)
+                      : dispatch_pcg<T, false, true>(L, M, a, C, single);
+            *L.launches += 1;
+            return e == cudaSuccess ? 0 : (int)e;
+        }
+    }
+    e = M.gen ? dispatch_pcg<T, true, false>(L, M, a, C, single) : dispatch_pcg<T, false, false>(L, M, a, C, single);
     *L.launches += 1;
     return e == cudaSuccess ? 0 : (int)e;
 }
@@ -672,11 +786,12 @@ int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mod
 // Columns 0..B-1 of the [nb][2B] surface arrays belong to the forward chain,
 // columns B..2B-1 to the adjoint chain.
 
-// Per-lane accumulator of a matrix-vector product in the matrix precision: a
-// compensated (Kahan) sum for FP32 matrices, so that the product stays bound by
-// memory bandwidth rather than by GB300's FP64 units, and a plain FP64 sum for
-// FP64 matrices.
-template <typename TA> struct DotAcc;
+// Per-lane accumulator of a matrix-vector product, chosen by the VECTOR type:
+// FP32 vectors (the FP32 phase) use a compensated (Kahan) FP32 sum, so that the
+// product stays bound by memory bandwidth rather than by GB300's FP64 units;
+// FP64 vectors (FP64 runs and the FP64 phase of mixed runs, whose matrix may be
+// the FP32 copy) keep every vector value in FP64 and sum in FP64.
+template <typename T> struct DotAcc;
 template <> struct DotAcc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
@@ -700,8 +815,8 @@ __global__ void k_gemv(const TA* __restrict__ A, const T* __restrict__ x, T* __r
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int row = warp; row < nb; row += nw) {
         const TA* a = A + (size_t)row * nb;
-        DotAcc<TA> acc;
-        for (int j = lane; j < nb; j += 32) acc.add(a[j], TA(x[(size_t)j * inc]));
+        DotAcc<T> acc;
+        for (int j = lane; j < nb; j += 32) acc.add(T(a[j]), x[(size_t)j * inc]);
         double v = acc.value();
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) y[(size_t)row * inc] = T(v);
@@ -715,9 +830,58 @@ __global__ void k_gemv_t_part(const TA* __restrict__ A, const T* __restrict__ x,
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i0 = blockIdx.y * rows_per_chunk, i1 = min(nb, i0 + rows_per_chunk);
     if (j >= nb) return;
-    DotAcc<TA> acc;
+    DotAcc<T> acc;
 #pragma unroll 4
-    for (int i = i0; i < i1; ++i) acc.add(A[(size_t)i * nb + j], TA(x[(size_t)i * inc]));
+    for (int i = i0; i < i1; ++i) acc.add(T(A[(size_t)i * nb + j]), x[(size_t)i * inc]);
+    part[(size_t)blockIdx.y * nb + j] = acc.value();
+}
+
+// FP64 vectors against the FP32 matrix (FP64 phase of single-instance mixed
+// runs): x is split once into FP32 parts x = hi + lo (about 48 significant
+// bits), and each product sums a*hi + a*lo with the compensated FP32
+// accumulator, so that the product reads 4 bytes per matrix entry and never
+// waits on the FP64 units.
+__global__ void k_split_vec(const double* __restrict__ x, int inc, float* __restrict__ hi, float* __restrict__ lo,
+                            int nb) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
+        const double v = x[(size_t)j * inc];
+        const float h = (float)v;
+        hi[j] = h;
+        lo[j] = (float)(v - (double)h);
+    }
+}
+
+__global__ void k_gemv_split(const float* __restrict__ A, const float* __restrict__ hi, const float* __restrict__ lo,
+                             double* __restrict__ y, int nb, int inc) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int row = warp; row < nb; row += nw) {
+        const float* a = A + (size_t)row * nb;
+        DotAcc<float> acc;
+        for (int j = lane; j < nb; j += 32) {
+            const float aj = a[j];
+            acc.add(aj, hi[j]);
+            acc.add(aj, lo[j]);
+        }
+        double v = acc.value();
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) y[(size_t)row * inc] = v;
+    }
+}
+
+__global__ void k_gemv_t_part_split(const float* __restrict__ A, const float* __restrict__ hi,
+                                    const float* __restrict__ lo, double* __restrict__ part, int nb,
+                                    int rows_per_chunk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = blockIdx.y * rows_per_chunk, i1 = min(nb, i0 + rows_per_chunk);
+    if (j >= nb) return;
+    DotAcc<float> acc;
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) {
+        const float a = A[(size_t)i * nb + j];
+        acc.add(a, hi[i]);
+        acc.add(a, lo[i]);
+    }
     part[(size_t)blockIdx.y * nb + j] = acc.value();
 }
 
@@ -791,7 +955,25 @@ int bem_chunks(int nb, int num_sms) {
 template <typename TA, typename T>
 static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const BatchView<T>& V) {
     const int B = V.B, C = 2 * B, nb = M.nb;
-    if (B == 1) {
+    if (B == 1 && sizeof(TA) == 4 && sizeof(T) == 8) {
+        // scratch: S chunks x nb partial sums, then hi/lo of both input vectors
+        const int S = bem_chunks(nb, L.num_sms);
+        const int rpc = (nb + S - 1) / S;
+        double* part = (double*)V.bem_part;
+        float* hf = (float*)(part + (size_t)32 * nb);
+        float* lf = hf + nb;
+        float* ha = lf + nb;
+        float* la = ha + nb;
+        const int sb = (nb + 255) / 256;
+        k_split_vec<<<sb, 256, 0, L.stream>>>((const double*)V.ub_in, C, hf, lf, nb);
+        k_split_vec<<<sb, 256, 0, L.stream>>>((const double*)V.ub_in + 1, C, ha, la, nb);
+        int blocks = (nb * 32 + 255) / 256;
+        if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
+        k_gemv_split<<<blocks, 256, 0, L.stream>>>((const float*)Bm, hf, lf, (double*)V.ub_out, nb, C);
+        k_gemv_t_part_split<<<dim3((nb + 255) / 256, S), 256, 0, L.stream>>>((const float*)Bm, ha, la, part, nb, rpc);
+        k_sum_parts<T><<<(nb + 255) / 256, 256, 0, L.stream>>>(part, S, nb, V.ub_out + 1, C);
+        *L.launches += 5;
+    } else if (B == 1) {
         int blocks = (nb * 32 + 255) / 256;
         if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
         k_gemv<TA, T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub_in, V.ub_out, nb, C);
@@ -825,7 +1007,7 @@ int field_blocks(const Launch& L, const MeshView& M, int B) {
     return nblk < maxblk ? nblk : maxblk;
 }
 
-template <typename T>
+template <typename T, bool GEN>
 __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T> V, int demag) {
     extern __shared__ double fsm[];
     double* scratch = fsm;                        // [Q_COUNT][bd]
@@ -847,15 +1029,14 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
         double* Gt = V.H + (size_t)(1 - cur) * N * 3 * B;        // grad phi at the trial point
         const double* Gb = V.H + (size_t)cur * N * 3 * B;   // grad phi at the base point
         for (int row = blockIdx.x * RB + rl; row < N; row += gridDim.x * RB) {
-            const int nd = M.node[row];
-            const double vi = (double)(nd & 0xff);
+            const double vi = GEN ? M.gV[row] : (double)(M.node[row] & 0xff);
             const size_t i3 = (size_t)row * 3 * B + b;
             const double mx = mt[i3], my = mt[i3 + B], mz = mt[i3 + 2 * B];
             T ex0 = T(0), ex1 = T(0), ex2 = T(0), hd0 = T(0), hd1 = T(0), hd2 = T(0);
             const int e0 = M.rowptr[row], e1 = M.rowptr[row + 1];
             for (int e = e0; e < e1; ++e) {
                 const int j = __ldg(&M.col[e]) & 0x7fffffff;
-                const T k = T(sbyte(__ldg(&M.pkA[e]), 0));
+                const T k = GEN ? T(GenTab<T>::A(M)[e].x) : T(sbyte(__ldg(&M.pkA[e]), 0));
                 const size_t j3 = (size_t)j * 3 * B + b;
                 // difference form: exact zero for a uniform state, no cancellation
                 ex0 += k * T(mt[j3] - mx);
@@ -864,12 +1045,19 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
                 if (demag) {
                     // (forward + adjoint)/2: the potential whose lumped gradient is the
                     // exact gradient of the stray-field energy
-                    const int wb = __ldg(&M.pkB[e]);
                     const size_t jc = (size_t)j * 2 * B + b;
                     const T u = T(0.5) * (V.U1[jc] + V.U2[jc] + V.U2[jc + B]);
-                    hd0 += T(sbyte(wb, 0)) * u;
-                    hd1 += T(sbyte(wb, 1)) * u;
-                    hd2 += T(sbyte(wb, 2)) * u;
+                    if constexpr (GEN) {
+                        const typename GenTab<T>::V4 gb = GenTab<T>::Bt(M)[e];
+                        hd0 += gb.x * u;
+                        hd1 += gb.y * u;
+                        hd2 += gb.z * u;
+                    } else {
+                        const int wb = __ldg(&M.pkB[e]);
+                        hd0 += T(sbyte(wb, 0)) * u;
+                        hd1 += T(sbyte(wb, 1)) * u;
+                        hd2 += T(sbyte(wb, 2)) * u;
+                    }
                 }
             }
             const double m[3] = {mx, my, mz};
@@ -938,10 +1126,12 @@ void field_eval(const Launch& L, const MeshView& M, const BatchView<T>& V, int d
     const size_t smem = sizeof(double) * Q_COUNT * (FIELD_THREADS + V.B);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_field<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_field<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         attr_set = true;
     }
-    k_field<T><<<nblk, FIELD_THREADS, smem, L.stream>>>(M, V, demag);
+    if (M.gen) k_field<T, true><<<nblk, FIELD_THREADS, smem, L.stream>>>(M, V, demag);
+    else k_field<T, false><<<nblk, FIELD_THREADS, smem, L.stream>>>(M, V, demag);
     *L.launches += 1;
 }
 
@@ -988,8 +1178,8 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     const double gg = v[Q_GG], torque = v[Q_TORQUE];
     const bool conv = so.grad_tol > 0.0 ? (gg < so.grad_tol) : (torque < so.tol);
     bool accept;
-    if (s.phase == PH_INIT) {
-        accept = true;
+    if (s.phase == PH_INIT || s.phase == PH_LB) {
+        accept = true;   // LaBonte's iteration takes every step
     } else if (s.phase == PH_SEARCH) {
         accept = E <= s.E_ref - so.c1 * s.tau * s.gg_base;
     } else {
@@ -1039,6 +1229,12 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
         s.kappa = so.kappa0;
         if (conv) { s.status = 0; s.phase = PH_DONE; return; }
         if (so.max_iter <= 0) { s.status = 3; s.phase = PH_DONE; return; }
+        if (so.method == 1) {
+            s.tau = so.omega;
+            s.phase = PH_LB;
+            s.line_searches = 0;
+            return;
+        }
         s.tau = 1.0 / v[Q_HMAX];
         s.phase = PH_SEARCH;
         s.E_ref = E;
@@ -1051,9 +1247,15 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     s.iters += 1;
     if (conv) { s.status = 0; s.phase = PH_DONE; return; }
     if (s.iters >= so.max_iter) { s.status = 3; s.phase = PH_DONE; return; }
+    if (s.phase == PH_LB) return;   // LaBonte: the next step uses the same relaxation
     const double ss = v[Q_SS], sy = v[Q_SY], yy = v[Q_YY];
     double tau = 1.0 / v[Q_HMAX];   // s.y <= 0: restart with the first-step trial
-    if (sy > 0.0) {
+    if (sy > 0.0 && so.bb_rule != 0) {
+        // plain rules: BB1, BB2, or BB1 and BB2 on alternate steps
+        const double t1 = ss / sy, t2 = sy / yy;
+        const bool first = so.bb_rule == 1 || (so.bb_rule == 3 && ((s.iters - 1) & 1) == 0);
+        tau = first ? t1 : t2;
+    } else if (sy > 0.0) {
         const double t1 = ss / sy, t2 = sy / yy;
         const int ma = so.m_alpha < MALPHA_MAX ? so.m_alpha : MALPHA_MAX;
         if (s.ntau2 < ma) {
@@ -1103,6 +1305,26 @@ __global__ void k_trial(int N, BatchView<T> V) {
             mt[i3] = mb[i3];
             mt[i3 + B] = mb[i3 + B];
             mt[i3 + 2 * B] = mb[i3 + 2 * B];
+            continue;
+        }
+        if (phase == PH_LB) {
+            // LaBonte, all nodes at once: m <- normalize((1 - omega) m + omega h/|h|);
+            // h is parallel to -grad phi (positive nodal volumes)
+            const double* Gb = V.H + (size_t)cur * N * 3 * B;
+            const double om = V.st[b].tau;
+            const double m0 = mb[i3], m1 = mb[i3 + B], m2 = mb[i3 + 2 * B];
+            const double g0 = Gb[i3], g1 = Gb[i3 + B], g2 = Gb[i3 + 2 * B];
+            const double gn = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+            double x0 = m0, x1 = m1, x2 = m2;
+            if (gn > 0.0) {
+                x0 = (1.0 - om) * m0 - om * g0 / gn;
+                x1 = (1.0 - om) * m1 - om * g1 / gn;
+                x2 = (1.0 - om) * m2 - om * g2 / gn;
+            }
+            const double xn = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+            mt[i3] = x0 / xn;
+            mt[i3 + B] = x1 / xn;
+            mt[i3 + 2 * B] = x2 / xn;
             continue;
         }
         // x = [(1 - |w|^2) m - 2 m x w + 2 (m.w) w] / (1 + |w|^2),  w = tau H / 2
@@ -1210,7 +1432,7 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
 }
 
 #define LBM_INSTANTIATE(T)                                                                               \
-    template int pcg_solve<T>(const Launch&, const MeshView&, const BatchView<T>&, int, double, int, int*); \
+    template int pcg_solve<T>(const Launch&, const MeshView&, const BatchView<T>&, int, double, int, bool); \
     template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&, bool);               \
     template void field_eval<T>(const Launch&, const MeshView&, const BatchView<T>&, int);                 \
     template void trial_update<T>(const Launch&, const MeshView&, const BatchView<T>&);                    \

@@ -292,20 +292,22 @@ def test_sweep_config2_vs_oracle(ctx, prec):
     assert abs(sw_gpu[0] - sw_ora[0]) <= 0.1 + 1e-9
 
 
-def test_batched_config4_vs_oracle(ctx):
+@pytest.mark.parametrize("prec", [lbm.LBM_MIXED, lbm.LBM_MIXED_TC])
+def test_batched_config4_vs_oracle(ctx, prec):
     """The benchmark's workload in its launch configuration (64 instances on the
-    30^3-cell cube, mixed precision): every instance converges and its energy is
-    within 1e-6 relative of the oracle's (golden, written by the oracle)."""
+    30^3-cell cube, mixed precision with SIMT or tensor-core BEM products): every
+    instance converges and its energy is within 1e-6 relative of the oracle's
+    (golden, written by the oracle)."""
     from oracle.micromag import MU0
     from synth.inputs import batched_case
     g = _golden("batched_n30.json")["results"]
     insts = batched_case(30, 64, seed=4)
     mesh = ctx.mesh_cube(2e-9, 30)
-    inst = ctx.instance_create(mesh, 64, lbm.LBM_MIXED)
+    inst = ctx.instance_create(mesh, 64, prec)
     inst.set_material(JS_T, A_JM, K1_JM3, np.stack([i.axis for i in insts]))
     inst.set_field(np.stack([i.h_ext for i in insts]))
     inst.set_m(np.stack([i.m0 for i in insts]))
-    res = inst.minimise(lbm.default_opts(lbm.LBM_MIXED))
+    res = inst.minimise(lbm.default_opts(prec))
     inst.destroy()
     ctx.mesh_destroy(mesh)
     Kd = JS_T ** 2 / (2 * MU0)
@@ -313,3 +315,60 @@ def test_batched_config4_vs_oracle(ctx):
         assert r["status"] == lbm.LBM_OK and r["torque"] < 1e-6, b
         scale = max(abs(o["E"]), Kd * (30 * 2e-9) ** 3)
         assert abs(r["energy"][4] - o["E"]) / scale < 1e-6, (b, r["energy"][4], o["E"])
+
+
+@pytest.mark.parametrize("n,B", [(3, 1), (7, 1), (6, 8)])
+def test_fp64_solves_with_fp32_iterations_match_plain(ctx, n, B):
+    """FP64 potential solves iterated in FP32 with the FP64 residual recomputed
+    at every restart end on the same FP64 residual test (1e-13), so fields,
+    potentials and energies equal those of plain FP64 PCG to 1e-10 and the
+    oracle's to 1e-10."""
+    N = (n + 1) ** 3
+    axes = np.array([tilted_axis(20.0 + b, 0.3 * b) for b in range(B)])
+    fields = np.array([[0.3, -0.7, 1.9 - 0.5 * b] for b in range(B)])
+    m0 = np.stack([m_random_sphere(N, 70 + n + b) for b in range(B)])
+    mesh = ctx.mesh_cube(2e-9, n)
+    out = []
+    for mixed_iter in (0, 1):
+        inst = ctx.instance_create(mesh, B, lbm.LBM_FP64)
+        inst.set_material(JS_T, A_JM, K1_JM3, axes)
+        inst.set_field(fields)
+        inst.set_m(m0)
+        out.append(inst.evaluate(lbm.default_opts(lbm.LBM_FP64, cg_mixed_iter=mixed_iter)))
+        inst.destroy()
+    (r0, h0, u0), (r1, h1, u1) = out
+    assert np.abs(h1 - h0).max() <= 1e-10 * np.abs(h0).max()
+    assert np.abs(u1 - u0).max() <= 1e-9 * np.abs(u0).max()
+    p = CubeProblem(n, JS_T, A_JM, K1_JM3, axes[0])
+    ev = p.evaluate(m0[0], fields[0])
+    assert np.abs(h1[0] - ev.h).max() <= 1e-10 * np.abs(ev.h).max()
+    Eunit = p.Kd * p.cell ** 3 * N
+    for a, b in zip(r0, r1):
+        assert np.abs(np.array(a["energy"]) - np.array(b["energy"])).max() <= 1e-10 * Eunit
+    ctx.mesh_destroy(mesh)
+
+
+def test_mixed_polish_with_fp32_iterations_reaches_same_minima(ctx):
+    """Mixed-precision minimisation: the FP64 phase with FP32-iteration solves
+    and with plain FP64 PCG end at the same minima (energies within 1e-8)."""
+    n, B = 8, 8
+    N = (n + 1) ** 3
+    rng = np.random.default_rng(9)
+    axes = np.array([tilted_axis(5 * rng.random(), 6.3 * rng.random()) for _ in range(B)])
+    fields = np.array([[0.0, 0.0, -8 * rng.random()] for _ in range(B)])
+    m0 = np.stack([m_perturbed(N, 900 + b) for b in range(B)])
+    mesh = ctx.mesh_cube(2e-9, n)
+    res = []
+    for mixed_iter in (0, 1):
+        inst = ctx.instance_create(mesh, B, lbm.LBM_MIXED)
+        inst.set_material(JS_T, A_JM, K1_JM3, axes)
+        inst.set_field(fields)
+        inst.set_m(m0)
+        res.append(inst.minimise(lbm.default_opts(lbm.LBM_MIXED, cg_mixed_iter=mixed_iter)))
+        inst.destroy()
+    ctx.mesh_destroy(mesh)
+    Kd = JS_T ** 2 / (2 * 4e-7 * math.pi)
+    scale = Kd * (n * 2e-9) ** 3
+    for a, b in zip(*res):
+        assert a["status"] == b["status"] == lbm.LBM_OK
+        assert abs(a["energy"][4] - b["energy"][4]) <= 1e-8 * max(abs(a["energy"][4]), scale)

@@ -436,3 +436,74 @@ def test_seeded_generators_are_stable():
     z = normals(1, 4)
     assert np.all(np.isfinite(z)) and z.shape == (4,)
     assert np.array_equal(normals(1, 4), z)
+
+
+# --- step-rule variants and LaBonte's method ------------------------------------
+
+def test_bb_rule_variants_reach_the_same_minimum():
+    """BB1 only, BB2 only, plain alternation and the adaptive rule (Sec. 2.3)
+    converge from the same start to the same minimum."""
+    from oracle.minimise import StepRule
+    p = _problem(4, axis=(0.05, 0.0, 1.0))
+    m0 = np.tile([0.0, 0.0, 1.0], (p.mesh.N, 1)) + 0.02 * RNG.normal(size=(p.mesh.N, 3))
+    m0 /= np.linalg.norm(m0, axis=1, keepdims=True)
+    h = np.array([0.0, 0.0, -4.0])
+    E = []
+    for bb in ("adaptive", "bb1", "bb2", "alternate"):
+        r = minimise(p, m0, h, tol=1e-7, rule=StepRule(bb=bb))
+        assert r.status == OK, bb
+        E.append(r.E)
+    assert max(E) - min(E) <= 1e-9 * abs(E[0])
+
+
+def test_bb_variant_steps_on_a_quadratic():
+    """With y = A s (A SPD): tau^1 >= tau^2 (Cauchy-Schwarz), both inside
+    [1/lambda_max, 1/lambda_min]; "alternate" takes tau^1 then tau^2."""
+    from oracle.minimise import BBState, StepRule, next_bb_tau
+    Q, _ = np.linalg.qr(RNG.normal(size=(9, 9)))
+    lam = np.linspace(0.5, 40.0, 9)
+    A = Q @ np.diag(lam) @ Q.T
+    s = RNG.normal(size=(3, 3))
+    y = (A @ s.ravel()).reshape(3, 3)
+    t1 = next_bb_tau(s, y, 1.0, BBState(0.5), StepRule(bb="bb1"))
+    t2 = next_bb_tau(s, y, 1.0, BBState(0.5), StepRule(bb="bb2"))
+    assert 1 / lam.max() <= t2 <= t1 <= 1 / lam.min()
+    st = BBState(0.5)
+    alt = [next_bb_tau(s, y, 1.0, st, StepRule(bb="alternate")) for _ in range(4)]
+    assert alt == [t1, t2, t1, t2]
+    assert next_bb_tau(s, -y, 0.125, BBState(0.5), StepRule(bb="bb2")) == 0.125   # s.y <= 0: restart
+
+
+def test_labonte_fixed_point_and_norm():
+    """A state aligned with its effective field is a fixed point (no
+    iteration); every LaBonte step keeps |m_i| = 1."""
+    from oracle.minimise import labonte
+    p = _problem(2, demag=False)
+    m_up = np.tile([0.0, 0.0, 1.0], (p.mesh.N, 1))
+    r = labonte(p, m_up, np.array([0.0, 0.0, 2.0]), omega=1.0)
+    assert r.status == OK and r.iterations == 0
+    m0 = _rand_unit(p.mesh.N)
+    r = labonte(p, m0, np.array([0.3, 0.1, 2.0]), omega=0.7, max_iter=5, record=(1, 3, 5))
+    for _, m in r.trajectory:
+        assert np.abs(np.linalg.norm(m, axis=1) - 1.0).max() < 1e-14
+
+
+def test_labonte_reaches_single_domain_equilibrium():
+    """On a single-domain particle beyond its switching field the under-relaxed
+    rotate-to-field iteration (omega = 0.1; the plain replacement, omega = 1,
+    oscillates when all nodes move at once) converges to the Stoner-Wohlfarth
+    equilibrium, the 1-D root of K1 sin 2theta + Js H sin(theta - psi) = 0."""
+    from oracle.minimise import labonte
+    p = _sw_problem((0, 0, 1))
+    HK = 2 * K1_JM3 * MU0 / JS_T
+    psi = math.radians(150.0)
+    hval = 0.8 * HK
+    h = hval * np.array([math.sin(psi), 0.0, math.cos(psi)])
+    m0 = np.tile([0.0, 0.0, 1.0], (p.mesh.N, 1))
+    r = labonte(p, m0, h, omega=0.1, tol=1e-9, max_iter=20000)
+    assert r.status == OK
+    mm = p.mean_m(r.m)
+    theta = math.atan2(mm[0], mm[2])
+    f = lambda t: K1_JM3 * math.sin(2 * t) + (JS_T / MU0) * hval * math.sin(t - psi)
+    th_sw = brentq(f, psi, math.pi)
+    assert abs(theta - th_sw) < 1e-7
