@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "fp64"])
+    ap.add_argument("--precision", default="mixed_tc", choices=["mixed", "mixed_tc", "fp64"])
     ap.add_argument("--fp64-sample", type=int, default=4,
                     help="instances of the plain-FP64 single-instance comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -115,6 +115,31 @@ def dist_init(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of the independent batch a rank solves: rank 0 solves the seed-4
+    batch (the one the parity tests pin); rank r > 0 an independent batch of the
+    same distribution.  The problems are independent, so ranks share nothing on
+    the data path (weak scaling: BATCH solves per rank per step)."""
+    return 4 if rank == 0 else 4 + 7919 * rank
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Whole-job time: the slowest rank's seconds (all-reduce MAX over the
+    initialised process group; the identity for one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(solves_per_rank: int, seconds: float, ws: int) -> float:
+    """solves/s of the whole job: every rank's solves over the slowest rank's time."""
+    return ws * solves_per_rank / seconds
 
 
 def cpu_oracle_sample(insts, evals_per_solve_gpu, budget_s):
@@ -197,9 +222,13 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def pcg_bytes_per_instance_iter(N, tsize):
-    # z gather, p rw, q rw, x rw, r rw, p, q read, z write: 12 vector words per node
-    return 12 * tsize * N
+def pcg_bytes_per_row(kind):
+    """Algorithmic bytes of one PCG iteration per row and system: z gather, p rw,
+    q rw (phase A); x rw, r rw, p and q read, z write (phase B) = 12 vector
+    words.  FP32 solves: 12 x 4 B; plain FP64: 12 x 8 B; FP64 solves iterated in
+    FP32 (FP64 x, FP32 work vectors): 10 x 4 B + 2 x 8 B.  The int8 stiffness
+    tables are shared by all systems and not counted."""
+    return {"fp32": 48, "fp64": 96, "fp64_fp32iter": 56}[kind]
 
 
 def run_ours(args, ws, rank, local):
@@ -212,7 +241,7 @@ def run_ours(args, ws, rank, local):
     prec = {"mixed": lbm.LBM_MIXED, "mixed_tc": lbm.LBM_MIXED_TC, "fp64": lbm.LBM_FP64}[args.precision]
     stream = torch.cuda.current_stream()
     ctx = lbm.Context(local, stream=stream.cuda_stream)
-    insts = batched_case(N_CELLS, BATCH, seed=4)
+    insts = batched_case(N_CELLS, BATCH, seed=rank_seed(rank))
     mesh = ctx.mesh_cube(2e-9, N_CELLS)
     info = ctx.mesh_info(mesh)
     N = info["N"]
@@ -255,16 +284,15 @@ def run_ours(args, ws, rank, local):
         step_ms.append(e0.elapsed_time(e1))
         evals.extend(r["evaluations"] for r in res)
         bad.extend(r["status"] for r in res if r["status"] != 0)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read(reset=True)
     ctx.profile_enable(False)
     clocks = sampler.stop()
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * BATCH * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, ws, device=f"cuda:{local}")
+    value = whole_job_value(BATCH * args.steps, total_s, ws)
     final_res = res
 
     # end to end through the public API with host buffers (H2D of m0, D2H of m)
@@ -276,7 +304,8 @@ def run_ours(args, ws, rank, local):
         inst.minimise(opts)
         m_out = inst.get_m()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = ws * BATCH / (statistics.mean(e2e_ms) / 1e3)
+    e2e_s = max_over_ranks(statistics.mean(e2e_ms) / 1e3, ws, device=f"cuda:{local}")
+    e2e_value = whole_job_value(BATCH, e2e_s, ws)
 
     if rank != 0:
         return
@@ -293,15 +322,17 @@ def run_ours(args, ws, rank, local):
     kinds = {k: v for k, v in prof.items() if k not in ("cg_iters", "cg_sweeps")}
     total_kernel_ms = sum(v["ms"] for v in kinds.values())
     pcg = {}
-    for name, idx, word in (("fp32", 0, 4), ("fp64", 1, 8)):
+    fp64_kind = "fp64_fp32iter" if opts.cg_mixed_iter and prec != lbm.LBM_FP64 else "fp64"
+    for name, idx, kind in (("fp32", 0, "fp32"), ("fp64", 1, fp64_kind)):
         ms = kinds[f"pcg1_{name}"]["ms"] + kinds[f"pcg2_{name}"]["ms"]
         nl = kinds[f"pcg1_{name}"]["launches"] + kinds[f"pcg2_{name}"]["launches"]
-        by = prof["cg_iters"][idx] * 12 * word * N
-        pcg[name] = dict(ms=ms, launches=nl, bytes=by)
+        by = prof["cg_iters"][idx] * pcg_bytes_per_row(kind) * N
+        pcg[name] = dict(ms=ms, launches=nl, bytes=by, kind=kind)
     dom = max(pcg, key=lambda k: pcg[k]["ms"])
     d = pcg[dom]
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": f"k_pcg ({dom} potential solves, forward + adjoint)",
+    roofline = {"bound": "hbm", "kernel": f"k_pcg ({d['kind']} potential solves, forward + adjoint)",
+                "bytes_per_row_system_iteration": pcg_bytes_per_row(d["kind"]),
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
