@@ -103,6 +103,11 @@ typedef struct {
                                Not guaranteed to converge (exchange-coupled nodes
                                moved together oscillate unless omega is small) */
     double  omega;          /* LaBonte relaxation factor, 0 < omega <= 2 (default 1) */
+    int32_t stall_iters;    /* a phase gives up (status LBM_E_NOT_CONVERGED) after this
+                               many accepted steps without halving its smallest torque; the
+                               FP32 phase of a mixed run then hands the instance to the
+                               FP64 phase (which ignores it).  0 = never.  Default 200
+                               for the mixed precisions, 0 for LBM_FP64 */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -198,6 +203,9 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
 int lbm_instance_destroy(lbm_ctx* ctx, lbm_inst inst);
 int lbm_set_material(lbm_ctx* ctx, lbm_inst inst, const lbm_material* mats /* [batch] */);
 int lbm_set_field(lbm_ctx* ctx, lbm_inst inst, const double* h /* [batch*3], tesla */);
+/* lbm_set_m / lbm_set_m_device also reset the instances' step state and set
+ * their potentials to zero, so that the next solve depends only on its inputs
+ * (a repeated solve gives the same bits). */
 int lbm_set_m(lbm_ctx* ctx, lbm_inst inst, const double* m /* [batch*N*3] host */);
 int lbm_get_m(lbm_ctx* ctx, lbm_inst inst, double* m /* [batch*N*3] host */);
 

@@ -186,7 +186,7 @@ void prof_harvest(lbm_ctx* ctx) {
 // Byte offsets of the per-instance arrays inside one allocation; every array
 // starts on a 256-byte boundary (the PCG reads 8- and 16-byte vectors).
 struct VecLayout {
-    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, total;
+    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, m32, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -208,6 +208,7 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.ub_in = take(tsize * nb * C);
     L.ub_out = take(tsize * nb * C);
     L.bem_part = take(8 * 34 * nb);   // 32 x nb partial sums + hi/lo FP32 parts of two vectors
+    L.m32 = tsize == 4 ? take(4 * N * 3 * B) : 0;
     L.total = o;
     return L;
 }
@@ -231,6 +232,7 @@ BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool w
     v.ub_in = (T*)(base + L.ub_in);
     v.ub_out = (T*)(base + L.ub_out);
     v.bem_part = (T*)(base + L.bem_part);
+    v.m32 = sizeof(T) == 4 ? (float*)(base + L.m32) : nullptr;
     v.part = I.part;
     v.st = I.st;
     v.ic = I.ic;
@@ -238,6 +240,16 @@ BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool w
 }
 
 size_t vec_bytes(const Mesh& M, int B, int tsize) { return vec_layout(M, B, tsize).total; }
+
+// A new magnetisation starts its potential solves from zero (not from the
+// previous solve's potentials), so that a solve depends only on its inputs.
+int zero_potentials(lbm_ctx* ctx, const Mesh& M, const Inst& I) {
+    const VecLayout L = vec_layout(M, I.B, I.tsize);
+    const size_t bytes = (size_t)I.tsize * M.N * 2 * I.B;
+    CK(cudaMemsetAsync((char*)I.vec + L.U1, 0, bytes, ctx->stream));
+    CK(cudaMemsetAsync((char*)I.vec + L.U2, 0, bytes, ctx->stream));
+    return LBM_OK;
+}
 
 size_t part_elems(const lbm_ctx* ctx, int B) {
     const size_t a = (size_t)4 * ctx->num_sms * B * NQ;   // field kernel partials
@@ -310,6 +322,7 @@ StepOpts step_opts(const lbm_solve_opts& o) {
     s.bb_rule = o.bb_rule;
     s.method = o.method;
     s.omega = o.omega;
+    s.stall_iters = o.stall_iters;
     return s;
 }
 
@@ -318,7 +331,7 @@ int check_opts(const lbm_solve_opts& o) {
         o.m_alpha > MALPHA_MAX || o.max_backtracks < 0 || o.cg_max_iter < 1 || !(o.cg_tol > 0) ||
         o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
         !(o.cg_tol_polish > 0) || o.bb_rule < 0 || o.bb_rule > 3 || o.method < 0 || o.method > 1 ||
-        (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)))
+        (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)) || o.stall_iters < 0)
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -466,7 +479,8 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
     Mesh& M = *ctx->meshes[I->mesh];
     const auto t0 = std::chrono::steady_clock::now();
     lbm_solve_opts o1 = o;
-    o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;
+    o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;   // FP32 phase; it hands a stalled
+                                                            // instance to the FP64 phase
     std::vector<InstState> s1, s2;
     int rc = run_minimise<float>(ctx, I, o1, nullptr, false, nullptr, nullptr, &s1);
     if (rc) return rc;
@@ -517,6 +531,7 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
         ctx->launches += 2;
         lbm_solve_opts o2 = o;
         o2.cg_tol = o.cg_tol_polish;
+        o2.stall_iters = 0;   // the FP64 phase runs to tol or max_iter
         rc = run_minimise<double>(ctx, P, o2, nullptr, false, nullptr, nullptr, &s2);
         if (rc) return rc;
         CK(cudaMemcpyAsync(I->vec, P->vec, sizeof(double) * 2 * N * 3 * B, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -568,6 +583,7 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->bb_rule = 0;
     o->method = 0;
     o->omega = 1.0;
+    o->stall_iters = precision == LBM_FP64 ? 0 : 200;
     if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
@@ -1072,6 +1088,7 @@ int lbm_set_m(lbm_ctx* ctx, lbm_inst inst, const double* m) {
     Launch L = ctx->launch();
     StepOpts so{};
     reset_states(L, I->st, I->B, so, 1);
+    if (int rc = zero_potentials(ctx, M, *I)) return rc;
     CK(cudaMemcpyAsync(I->staged, m, sizeof(double) * I->B * M.N * 3, cudaMemcpyHostToDevice, ctx->stream));
     if (I->tsize == 8) pack_m<double>(L, M.view(), batch_view<double>(ctx, M, *I, false), I->staged);
     else pack_m<float>(L, M.view(), batch_view<float>(ctx, M, *I, false), I->staged);
@@ -1087,6 +1104,7 @@ int lbm_set_m_device(lbm_ctx* ctx, lbm_inst inst, const double* d_m) {
     Launch L = ctx->launch();
     StepOpts so{};
     reset_states(L, I->st, I->B, so, 1);
+    if (int rc = zero_potentials(ctx, M, *I)) return rc;
     if (I->tsize == 8) pack_m<double>(L, M.view(), batch_view<double>(ctx, M, *I, false), d_m);
     else pack_m<float>(L, M.view(), batch_view<float>(ctx, M, *I, false), d_m);
     CK(cudaGetLastError());
@@ -1336,6 +1354,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     V.part = part;
     V.st = st;
     V.ic = ic;
+    V.m32 = nullptr;   // FP64 evaluation: no FP32 copy of the trial point
     Launch L{s, ctx->num_sms, bar, err, &ctx->launches, sweeps, fin, 0};
     const MeshView mv = M->view();
     lbm_solve_opts oo = o;
@@ -1653,6 +1672,7 @@ void serve_loop(Server* Sp) {
     o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;
     lbm_solve_opts o2 = o;
     o2.cg_tol = o.cg_tol_polish;
+    o2.stall_iters = 0;
     const StepOpts so1 = step_opts(o1), so2 = step_opts(o2);
     lbm_solve_opts o64 = o;        // plain FP64 requests
     for (;;) {

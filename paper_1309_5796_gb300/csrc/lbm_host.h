@@ -90,6 +90,7 @@ struct BatchView {
     InstState* st;             // [B]
     const InstConst* ic;       // [B]
     double* hout;              // optional [N][3][B] effective field (nullable)
+    float* m32 = nullptr;      // FP32 batches: [N][3][B] FP32 copy of the trial point (else null)
 };
 
 struct Launch {

@@ -49,6 +49,7 @@ struct StepOpts {
     double tol, grad_tol, c1, kappa0, tau_min, tau_max;
     int max_iter, max_backtracks, memory, m_alpha;
     int bb_rule;     // 0 adaptive, 1 BB1, 2 BB2, 3 BB1/BB2 alternation
+    int stall_iters; // give up after this many accepted steps without a new smallest torque (0: never)
     int method;      // 0 curvilinear steepest descent (Sec. 2), 1 LaBonte rotate-to-field
     double omega;    // LaBonte relaxation factor
 };
@@ -58,6 +59,8 @@ struct InstState {
     long long cg1, cg2;
     double tau, E_ref, gg_base, E, kappa, torque, gg;
     double Eacc;                   // base energy carried by exact differences (decisions)
+    double best_torque;            // smallest torque of the accepted points so far
+    int best_iter;                 // the iteration where it was reached
     double terms[4];
     double mean_m[3];
     double hist[HIST_MAX];

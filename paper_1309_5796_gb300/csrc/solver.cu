@@ -275,6 +275,60 @@ __device__ __forceinline__ void row_kv(const int* __restrict__ kent, const T* __
     }
 }
 
+// As row_kv for a warp that owns the row, with the row's packed entries
+// already in registers (lane l holds entry e0 + l, l < 32: `mine`, and its
+// value `mk` for general meshes), so that no index load sits on the row's
+// critical path; entries beyond the 32nd are loaded here.
+template <typename T, int VEC, bool CG, bool DIFF, bool GEN>
+__device__ __forceinline__ void row_kv_warp(int mine, T mk, int e0, int e1, const int* __restrict__ kent,
+                                            const T* __restrict__ kval, const T* v, int C, int c0,
+                                            const T (&vi)[VEC], T (&acc)[VEC]) {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) acc[k] = T(0);
+    const int cnt = e1 - e0;
+    for (int base = 0; base < cnt; base += MAXK) {
+        int w[MAXK];
+        T kv[MAXK];
+#pragma unroll
+        for (int t = 0; t < MAXK; ++t) {
+            const int idx = base + t;   // warp-uniform
+            if (idx < 32) {
+                w[t] = __shfl_sync(0xffffffffu, mine, idx);
+                kv[t] = GEN ? __shfl_sync(0xffffffffu, mk, idx) : T(0);
+            } else {
+                const bool has = idx < cnt;
+                w[t] = has ? __ldg(&kent[e0 + idx]) : 0;
+                kv[t] = (GEN && has) ? __ldg(&kval[e0 + idx]) : T(0);
+            }
+            if (!GEN) kv[t] = T(sbyte(w[t], 0));
+        }
+        T vj[MAXK][VEC];
+#pragma unroll
+        for (int t = 0; t < MAXK; ++t) {
+            if (w[t] != 0) vload<T, VEC, CG>(vj[t], &v[(size_t)((unsigned)w[t] >> 8) * C + c0]);
+            else
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
+        }
+#pragma unroll
+        for (int t = 0; t < MAXK; ++t)
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) acc[k] += kv[t] * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
+    }
+}
+
+// The trial point of an instance whose base point is `cur`, in T.
+template <typename T>
+__device__ __forceinline__ const T* trial_m(const BatchView<T>& V, int cur, int N) {
+    if constexpr (sizeof(T) == 4) {
+        (void)cur;
+        (void)N;
+        return V.m32;
+    } else {
+        return V.m + (size_t)(1 - cur) * N * 3 * V.B;
+    }
+}
+
 template <typename T>
 struct PcgArgs {
     MeshView M;
@@ -324,20 +378,20 @@ __device__ __forceinline__ bool grid_reduce(const double* part, int q0, int C, d
 }
 
 // b_i = (1/4) sum_j Gint_ij . m_j (the divergence right-hand side) at the trial point
+// meval: the trial point in T (FP32 kernels: its FP32 copy)
 template <typename T, bool GEN>
 __device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* __restrict__ pkA,
                                         const typename GenTab<T>::V4* __restrict__ gA, int e0, int e1,
-                                        const double* meval, int B, int b) {
+                                        const T* meval, int B, int b) {
     T acc = T(0);
     for (int e = e0; e < e1; ++e) {
         const size_t mj = (size_t)(__ldg(&col[e]) & 0x7fffffff) * 3 * B + b;
         if constexpr (GEN) {
             const typename GenTab<T>::V4 a = gA[e];
-            acc += a.y * T(meval[mj]) + a.z * T(meval[mj + B]) + a.w * T(meval[mj + 2 * B]);
+            acc += a.y * meval[mj] + a.z * meval[mj + B] + a.w * meval[mj + 2 * B];
         } else {
             const int w = __ldg(&pkA[e]);
-            acc += T(sbyte(w, 1)) * T(meval[mj]) + T(sbyte(w, 2)) * T(meval[mj + B]) +
-                   T(sbyte(w, 3)) * T(meval[mj + 2 * B]);
+            acc += T(sbyte(w, 1)) * meval[mj] + T(sbyte(w, 2)) * meval[mj + B] + T(sbyte(w, 3)) * meval[mj + 2 * B];
         }
     }
     return 0.25 * (double)acc;
@@ -492,7 +546,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                     // f: the right-hand side (b in every system but the stage-2 forward one)
                     double f = 0.0;
                     if (!(mode == 1 && !neu[k]) && actk[k])
-                        f = rhs_b<T, GEN>(col, pkA, gA, e0, e1, A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B,
+                        f = rhs_b<T, GEN>(col, pkA, gA, e0, e1, trial_m(A.V, s_cur[c0 + k], N), B,
                                           bk[k]);
                     if (mode == 1 && neu[k] && bp) f += (double)A.V.ub_out[(size_t)(bp - 1) * C + c0 + k];
                     double ref = f;   // norm reference: f (Neumann), f - K_IS x_S (Dirichlet)
@@ -589,7 +643,44 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
         W tpq[1][VEC];   // per-thread and block partial sums in W; grid sums in FP64
 #pragma unroll
         for (int k = 0; k < VEC; ++k) tpq[0][k] = W(0);
-        if (run_rows)
+        if (run_rows && warp_row) {
+            // software-pipelined rows: the row pointers two rows ahead and the
+            // packed entries and node word one row ahead are in flight while
+            // the current row gathers, so each row waits on its gathers only
+            const int lane = threadIdx.x & 31;
+            int row = row0, rown = row0 + rstride;
+            int kp0 = 0, kp1 = 0, kn0 = 0, kn1 = 0;
+            if (row < N) { kp0 = kptr[row]; kp1 = kptr[row + 1]; }
+            if (rown < N) { kn0 = kptr[rown]; kn1 = kptr[rown + 1]; }
+            int mine = (row < N && kp0 + lane < kp1) ? __ldg(&kent[kp0 + lane]) : 0;
+            W mk = (GEN && row < N && kp0 + lane < kp1) ? __ldg(&kvalW[kp0 + lane]) : W(0);
+            int nd = row < N ? node[row] : 0;
+            for (; row < N; row = rown, rown += rstride) {
+                const int rown2 = rown + rstride;
+                int kf0 = 0, kf1 = 0;
+                if (rown2 < N) { kf0 = kptr[rown2]; kf1 = kptr[rown2 + 1]; }
+                const int minen = (rown < N && kn0 + lane < kn1) ? __ldg(&kent[kn0 + lane]) : 0;
+                const W mkn = (GEN && rown < N && kn0 + lane < kn1) ? __ldg(&kvalW[kn0 + lane]) : W(0);
+                const int ndn = rown < N ? node[rown] : 0;
+                const bool surf = ((unsigned)nd >> 16) != 0;
+                const size_t ib = (size_t)row * C + c0;
+                W zi[VEC], w[VEC], pv[VEC], qv[VEC];
+                vload<W, VEC, false>(zi, &z[ib]);
+                vload<W, VEC, false>(pv, &p[ib]);
+                vload<W, VEC, false>(qv, &q[ib]);
+                row_kv_warp<W, VEC, CG, false, GEN>(mine, mk, kp0, kp1, kent, kvalW, z, C, c0, zi, w);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    pv[k] = zi[k] + beta[k] * pv[k];
+                    qv[k] = (!neu[k] && surf) ? W(0) : w[k] + beta[k] * qv[k];
+                    tpq[0][k] += pv[k] * qv[k];
+                }
+                vstore<W, VEC>(&p[ib], pv);
+                vstore<W, VEC>(&q[ib], qv);
+                kp0 = kn0; kp1 = kn1; kn0 = kf0; kn1 = kf1;
+                mine = minen; mk = mkn; nd = ndn;
+            }
+        } else if (run_rows) {
             for (int row = row0; row < N; row += rstride) {
                 const int nd = node[row];
                 const bool surf = ((unsigned)nd >> 16) != 0;
@@ -608,6 +699,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 vstore<W, VEC>(&p[ib], pv);
                 vstore<W, VEC>(&q[ib], qv);
             }
+        }
         if (!reduce(tpq, 0)) return;
         if (tid < C) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
         __syncthreads();
@@ -621,29 +713,51 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
         W v4[4][VEC];   // r.z, r.r, (unused), sum r: per-thread and block sums in W, grid sums in FP64
 #pragma unroll
         for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = W(0);
+        // two rows per pass: both rows' loads are in flight together
         if (run)
-            for (int row = row0; row < N; row += rstride) {
-                const int nd = node[row];
-                const size_t ib = (size_t)row * C + c0;
-                const W dinv = W(1) / (GEN ? kdiagW[row] : W((nd >> 8) & 0xff));
-                T xv[VEC];
-                W rv[VEC], pv[VEC], qv[VEC], zv[VEC];
-                vload<T, VEC, false>(xv, &x[ib]);
-                vload<W, VEC, false>(rv, &r[ib]);
-                vload<W, VEC, false>(pv, &p[ib]);
-                vload<W, VEC, false>(qv, &q[ib]);
+            for (int row = row0; row < N; row += 2 * rstride) {
+                const int rowb = row + rstride;
+                const bool two = rowb < N;
+                const size_t ia = (size_t)row * C + c0, ibb = (size_t)(two ? rowb : row) * C + c0;
+                const int nda = node[row], ndb = node[two ? rowb : row];
+                T xa[VEC], xb[VEC];
+                W ra[VEC], pa[VEC], qa[VEC], rb[VEC], pb[VEC], qb[VEC], za[VEC], zb[VEC];
+                vload<T, VEC, false>(xa, &x[ia]);
+                vload<W, VEC, false>(ra, &r[ia]);
+                vload<W, VEC, false>(pa, &p[ia]);
+                vload<W, VEC, false>(qa, &q[ia]);
+                vload<T, VEC, false>(xb, &x[ibb]);
+                vload<W, VEC, false>(rb, &r[ibb]);
+                vload<W, VEC, false>(pb, &p[ibb]);
+                vload<W, VEC, false>(qb, &q[ibb]);
+                const W dinva = W(1) / (GEN ? kdiagW[row] : W((nda >> 8) & 0xff));
+                const W dinvb = W(1) / (GEN ? kdiagW[two ? rowb : row] : W((ndb >> 8) & 0xff));
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
-                    xv[k] += alpha[k] * T(pv[k]);
-                    rv[k] -= alphaw[k] * qv[k];
-                    zv[k] = rv[k] * dinv;
-                    v4[0][k] += rv[k] * zv[k];
-                    v4[1][k] += rv[k] * rv[k];
-                    v4[3][k] += rv[k];
+                    xa[k] += alpha[k] * T(pa[k]);
+                    ra[k] -= alphaw[k] * qa[k];
+                    za[k] = ra[k] * dinva;
+                    v4[0][k] += ra[k] * za[k];
+                    v4[1][k] += ra[k] * ra[k];
+                    v4[3][k] += ra[k];
                 }
-                vstore<T, VEC>(&x[ib], xv);
-                vstore<W, VEC>(&r[ib], rv);
-                vstore<W, VEC>(&z[ib], zv);
+                vstore<T, VEC>(&x[ia], xa);
+                vstore<W, VEC>(&r[ia], ra);
+                vstore<W, VEC>(&z[ia], za);
+                if (two) {
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        xb[k] += alpha[k] * T(pb[k]);
+                        rb[k] -= alphaw[k] * qb[k];
+                        zb[k] = rb[k] * dinvb;
+                        v4[0][k] += rb[k] * zb[k];
+                        v4[1][k] += rb[k] * rb[k];
+                        v4[3][k] += rb[k];
+                    }
+                    vstore<T, VEC>(&x[ibb], xb);
+                    vstore<W, VEC>(&r[ibb], rb);
+                    vstore<W, VEC>(&z[ibb], zb);
+                }
             }
         // quantity 2 (ref.ref) is carried over from the prologue in `out`
         double keep2[1];
@@ -717,7 +831,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 } else if (mode == 0 && bp) {
                     A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] =
                         T(rhs_b<T, GEN>(col, pkA, gA, rowptr[row], rowptr[row + 1],
-                                        A.V.m + (size_t)(1 - s_cur[c0 + k]) * N * 3 * B, B, bk[k])) - kw[k];
+                                        trial_m(A.V, s_cur[c0 + k], N), B, bk[k])) - kw[k];
                 }
             }
             vstore<T, VEC>(&x[ib], xv);
@@ -767,7 +881,11 @@ int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mod
               bool mixed_iter) {
     const int C = 2 * V.B;
     PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps, L.fin};
-    const bool single = (long long)M.N * C <= SINGLE_CTA_MAX_WORK;
+    // one CTA is fastest for small FP32 work (no grid barriers); FP64 arithmetic
+    // issues at a small fraction of the FP32 rate, so plain FP64 solves spread
+    // over the grid from a much smaller size on
+    const long long work = (long long)M.N * C * ((sizeof(T) == 8 && !mixed_iter) ? 16 : 1);
+    const bool single = work <= SINGLE_CTA_MAX_WORK;
     cudaError_t e;
     if constexpr (sizeof(T) == 8) {
         if (mixed_iter) {
@@ -944,9 +1062,12 @@ template <typename T> __host__ __device__ inline const T* bem_ptr(const MeshView
 template <> __host__ __device__ inline const double* bem_ptr<double>(const MeshView& M) { return M.B64; }
 template <> __host__ __device__ inline const float* bem_ptr<float>(const MeshView& M) { return M.B32; }
 
+// Row chunks of the column-parallel transposed product: enough blocks for about
+// eight per SM, so that the column loads of many warps are in flight (at most
+// 32 chunks: the partial sums are 32 x nb).
 int bem_chunks(int nb, int num_sms) {
     const int colblocks = (nb + 255) / 256;
-    int S = (2 * num_sms + colblocks - 1) / colblocks;
+    int S = (8 * num_sms + colblocks - 1) / colblocks;
     if (S > 32) S = 32;
     if (S < 1) S = 1;
     return S;
@@ -1033,15 +1154,19 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
             const size_t i3 = (size_t)row * 3 * B + b;
             const double mx = mt[i3], my = mt[i3 + B], mz = mt[i3 + 2 * B];
             T ex0 = T(0), ex1 = T(0), ex2 = T(0), hd0 = T(0), hd1 = T(0), hd2 = T(0);
+            // neighbour values in T: the FP32 kernel reads the FP32 copy of the trial
+            // point (exact zero differences for equal values are kept)
+            const T* mn = (sizeof(T) == 4) ? reinterpret_cast<const T*>(V.m32) : reinterpret_cast<const T*>(mt);
+            const T tx = mn[i3], ty = mn[i3 + B], tz = mn[i3 + 2 * B];
             const int e0 = M.rowptr[row], e1 = M.rowptr[row + 1];
             for (int e = e0; e < e1; ++e) {
                 const int j = __ldg(&M.col[e]) & 0x7fffffff;
                 const T k = GEN ? T(GenTab<T>::A(M)[e].x) : T(sbyte(__ldg(&M.pkA[e]), 0));
                 const size_t j3 = (size_t)j * 3 * B + b;
                 // difference form: exact zero for a uniform state, no cancellation
-                ex0 += k * T(mt[j3] - mx);
-                ex1 += k * T(mt[j3 + B] - my);
-                ex2 += k * T(mt[j3 + 2 * B] - mz);
+                ex0 += k * (mn[j3] - tx);
+                ex1 += k * (mn[j3 + B] - ty);
+                ex2 += k * (mn[j3 + 2 * B] - tz);
                 if (demag) {
                     // (forward + adjoint)/2: the potential whose lumped gradient is the
                     // exact gradient of the stray-field energy
@@ -1227,6 +1352,8 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
         s.backtracks = 0;
         s.ntau2 = 0;
         s.kappa = so.kappa0;
+        s.best_torque = torque;
+        s.best_iter = 0;
         if (conv) { s.status = 0; s.phase = PH_DONE; return; }
         if (so.max_iter <= 0) { s.status = 3; s.phase = PH_DONE; return; }
         if (so.method == 1) {
@@ -1247,6 +1374,16 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     s.iters += 1;
     if (conv) { s.status = 0; s.phase = PH_DONE; return; }
     if (s.iters >= so.max_iter) { s.status = 3; s.phase = PH_DONE; return; }
+    // progress = the smallest torque so far halved; a phase that creeps (new
+    // minima, but no halving within stall_iters steps) has stalled
+    if (torque < 0.5 * s.best_torque) {
+        s.best_torque = torque;
+        s.best_iter = s.iters;
+    } else if (so.stall_iters > 0 && s.iters - s.best_iter >= so.stall_iters) {
+        s.status = 3;
+        s.phase = PH_DONE;
+        return;
+    }
     if (s.phase == PH_LB) return;   // LaBonte: the next step uses the same relaxation
     const double ss = v[Q_SS], sy = v[Q_SY], yy = v[Q_YY];
     double tau = 1.0 / v[Q_HMAX];   // s.y <= 0: restart with the first-step trial
@@ -1301,10 +1438,20 @@ __global__ void k_trial(int N, BatchView<T> V) {
         const size_t i3 = row * 3 * B + b;
         const double* mb = V.m + (size_t)cur * N * 3 * B;
         double* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
+        // the trial point, and its FP32 copy for the FP32 kernels (one conversion
+        // per node instead of one per neighbour entry)
+        auto put = [&](double x0, double x1, double x2) {
+            mt[i3] = x0;
+            mt[i3 + B] = x1;
+            mt[i3 + 2 * B] = x2;
+            if (V.m32) {
+                V.m32[i3] = (float)x0;
+                V.m32[i3 + B] = (float)x1;
+                V.m32[i3 + 2 * B] = (float)x2;
+            }
+        };
         if (phase == PH_INIT) {
-            mt[i3] = mb[i3];
-            mt[i3 + B] = mb[i3 + B];
-            mt[i3 + 2 * B] = mb[i3 + 2 * B];
+            put(mb[i3], mb[i3 + B], mb[i3 + 2 * B]);
             continue;
         }
         if (phase == PH_LB) {
@@ -1322,9 +1469,7 @@ __global__ void k_trial(int N, BatchView<T> V) {
                 x2 = (1.0 - om) * m2 - om * g2 / gn;
             }
             const double xn = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
-            mt[i3] = x0 / xn;
-            mt[i3 + B] = x1 / xn;
-            mt[i3 + 2 * B] = x2 / xn;
+            put(x0 / xn, x1 / xn, x2 / xn);
             continue;
         }
         // x = [(1 - |w|^2) m - 2 m x w + 2 (m.w) w] / (1 + |w|^2),  w = tau H / 2
@@ -1338,9 +1483,8 @@ __global__ void k_trial(int N, BatchView<T> V) {
         const double mw = m0 * w0 + m1 * w1 + m2 * w2;
         const double c0 = m1 * w2 - m2 * w1, c1 = m2 * w0 - m0 * w2, c2 = m0 * w1 - m1 * w0;
         const double den = 1.0 + ww;
-        mt[i3] = ((1.0 - ww) * m0 - 2.0 * c0 + 2.0 * mw * w0) / den;
-        mt[i3 + B] = ((1.0 - ww) * m1 - 2.0 * c1 + 2.0 * mw * w1) / den;
-        mt[i3 + 2 * B] = ((1.0 - ww) * m2 - 2.0 * c2 + 2.0 * mw * w2) / den;
+        put(((1.0 - ww) * m0 - 2.0 * c0 + 2.0 * mw * w0) / den, ((1.0 - ww) * m1 - 2.0 * c1 + 2.0 * mw * w1) / den,
+            ((1.0 - ww) * m2 - 2.0 * c2 + 2.0 * mw * w2) / den);
     }
 }
 

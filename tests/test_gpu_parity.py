@@ -372,3 +372,52 @@ def test_mixed_polish_with_fp32_iterations_reaches_same_minima(ctx):
     for a, b in zip(*res):
         assert a["status"] == b["status"] == lbm.LBM_OK
         assert abs(a["energy"][4] - b["energy"][4]) <= 1e-8 * max(abs(a["energy"][4]), scale)
+
+
+def test_repeated_solve_is_bitwise_identical(ctx):
+    """set_m restarts the potentials from zero: solving the same inputs twice
+    gives the same bits (deterministic reductions, no carried-over state)."""
+    n, B = 6, 4
+    N = (n + 1) ** 3
+    axes = np.array([tilted_axis(3.0 * b, 0.4 * b) for b in range(B)])
+    fields = np.array([[0.0, 0.0, -2.5 * b] for b in range(B)])
+    m0 = np.stack([m_perturbed(N, 1200 + b) for b in range(B)])
+    mesh = ctx.mesh_cube(2e-9, n)
+    inst = ctx.instance_create(mesh, B, lbm.LBM_MIXED)
+    inst.set_material(JS_T, A_JM, K1_JM3, axes)
+    inst.set_field(fields)
+    out = []
+    for _ in range(2):
+        inst.set_m(m0)
+        r = inst.minimise(lbm.default_opts(lbm.LBM_MIXED))
+        out.append((r, inst.get_m()))
+    assert np.array_equal(out[0][1], out[1][1])
+    for a, b in zip(out[0][0], out[1][0]):
+        assert a["energy"] == b["energy"] and a["iterations"] == b["iterations"]
+    inst.destroy()
+    ctx.mesh_destroy(mesh)
+
+
+def test_stalled_fp32_phase_hands_over_to_fp64(ctx):
+    """A switch tolerance the FP32 phase cannot reach: the phase gives up after
+    stall_iters steps without a new smallest torque and the FP64 phase finishes
+    at the FP64 answer."""
+    n, B = 8, 4
+    N = (n + 1) ** 3
+    axes = np.array([tilted_axis(2.0 * b, 0.3 * b) for b in range(B)])
+    fields = np.array([[0.0, 0.0, -1.5 * b] for b in range(B)])
+    m0 = np.stack([m_perturbed(N, 1300 + b) for b in range(B)])
+    mesh = ctx.mesh_cube(2e-9, n)
+    res = {}
+    for prec, kw in ((lbm.LBM_FP64, {}), (lbm.LBM_MIXED, dict(switch_tol=1e-12, stall_iters=40))):
+        inst = ctx.instance_create(mesh, B, prec)
+        inst.set_material(JS_T, A_JM, K1_JM3, axes)
+        inst.set_field(fields)
+        inst.set_m(m0)
+        res[prec] = inst.minimise(lbm.default_opts(prec, **kw))
+        inst.destroy()
+    ctx.mesh_destroy(mesh)
+    scale = JS_T ** 2 / (2 * 4e-7 * math.pi) * (n * 2e-9) ** 3
+    for a, b in zip(res[lbm.LBM_FP64], res[lbm.LBM_MIXED]):
+        assert b["status"] == lbm.LBM_OK and b["torque"] < 1e-6
+        assert abs(a["energy"][4] - b["energy"][4]) <= 1e-6 * max(abs(a["energy"][4]), scale)
