@@ -38,6 +38,15 @@ N_CELLS = 30
 BATCH = 64
 
 
+def batched_config() -> dict:
+    """The benchmark workload (identical on both arms)."""
+    N = (N_CELLS + 1) ** 3
+    nb = N - (N_CELLS - 1) ** 3
+    return {"workload": f"batched same-mesh: {BATCH} instances on a {N_CELLS}^3-cell (60 nm) Kuhn cube, "
+                        f"{N} nodes, {nb} surface nodes",
+            "n": N_CELLS, "batch": BATCH, "tol": 1e-6, "l2": "flushed between timed steps (512 MB write)"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,8 +58,11 @@ def parse():
                     help="instances of the plain-FP64 single-instance comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
-    ap.add_argument("--workload", default="batched", choices=["batched", "served"],
-                    help="batched: 64 same-mesh instances (default); served: Poisson request stream")
+    ap.add_argument("--workload", default="batched", choices=["batched", "served", "large"],
+                    help="batched: 64 same-mesh instances (default); served: Poisson request stream; "
+                         "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix)")
+    ap.add_argument("--n", type=int, default=80, help="cells per side of the large workload")
+    ap.add_argument("--max-iter", type=int, default=100000, help="iteration cap of the large workload")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals/s (0: 0.8 x calibrated capacity)")
     return ap.parse_args()
@@ -211,8 +223,7 @@ def run_reference(args, ws, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_eval * evals_per_solve * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batched same-mesh, {BATCH} instances, {N_CELLS}^3-cell cube",
-                       "n": N_CELLS, "batch": BATCH},
+            "config": batched_config(),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"{total_evals} oracle evaluations over {args.steps} steps of "
                                        f"{per_step:.0f} s; scaled by {evals_per_solve:.0f} "
@@ -375,10 +386,7 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed": "f32+f64", "mixed_tc": "f32+tf32x3+f64", "fp64": "f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"batched same-mesh: {BATCH} instances on a {N_CELLS}^3-cell "
-                               f"(60 nm) Kuhn cube, {N} nodes, {info['nb']} surface nodes",
-                   "n": N_CELLS, "batch": BATCH, "precision": args.precision, "tol": 1e-6,
-                   "l2": "flushed between timed steps (512 MB write)"},
+        "config": batched_config(), "precision": args.precision,
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "statuses_nonzero": bad,
         "evaluations_per_solve": statistics.mean(evals),
@@ -449,6 +457,87 @@ def run_served(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args, ws, rank, local):
+    """One instance on a large cube (random start on the sphere, -3 T along z,
+    mixed precision): time to solution and the roofline of the BEM products,
+    the kernels whose operand (the FP32 matrix, 4 nb^2 bytes) exceeds L2."""
+    import torch
+    import paper_1309_5796_gb300 as lbm
+    from synth.inputs import large_case
+    torch.cuda.set_device(local)
+    prec = {"mixed": lbm.LBM_MIXED, "mixed_tc": lbm.LBM_MIXED, "fp64": lbm.LBM_FP64}[args.precision]
+    stream = torch.cuda.current_stream()
+    ctx = lbm.Context(local, stream=stream.cuda_stream)
+    case = large_case(args.n)
+    t0 = time.perf_counter()
+    mesh = ctx.mesh_cube(2e-9, args.n)
+    setup_s = time.perf_counter() - t0
+    info = ctx.mesh_info(mesh)
+    N, nb = info["N"], info["nb"]
+    inst = ctx.instance_create(mesh, 1, prec)
+    inst.set_material(JS_T, A_JM, K1_JM3, case.axis)
+    inst.set_field(case.h_ext)
+    opts = lbm.default_opts(prec, max_iter=args.max_iter)
+    m0 = torch.from_numpy(np.ascontiguousarray(case.m0)).to(f"cuda:{local}")
+    for _ in range(args.warmup):
+        inst.set_m_device(m0.data_ptr())
+        inst.minimise(opts)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile_read(reset=True)
+    ctx.profile_enable(True)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ms, res = [], None
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst.set_m_device(m0.data_ptr())
+        res = inst.minimise(opts)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - launches0
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # one evaluation = one forward and one transposed product; the matrix is FP32
+    # in both phases of a mixed run (FP64 matrix in FP64 runs)
+    word = 8 if prec == lbm.LBM_FP64 else 4
+    bem = prof["bem_product"]
+    bem_bytes = bem["launches"] * 2 * word * nb * nb
+    achieved = bem_bytes / (bem["ms"] / 1e3) / 1e9 if bem["ms"] > 0 else 0.0
+    kinds = {k: v for k, v in prof.items() if k not in ("cg_iters", "cg_sweeps")}
+    line = {"metric": "solves/s, one instance on a large cube", "value": 1e3 / statistics.mean(ms),
+            "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == lbm.LBM_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"large: one instance on a {args.n}^3-cell Kuhn cube, {N} nodes, {nb} surface "
+                                   "nodes, random start on the sphere (seed 3), -3 T along z",
+                       "n": args.n, "precision": "fp64" if prec == lbm.LBM_FP64 else "mixed",
+                       "l2": f"BEM matrix {word * nb * nb / 1e9:.2f} GB > L2"},
+            "mesh_setup_s": setup_s, "status": res["status"], "iterations": res["iterations"],
+            "evaluations": res["evaluations"], "torque": res["torque"], "energy_J": res["energy"][4],
+            "gpu_launches": launches, "clocks": clocks,
+            "roofline": {"bound": "hbm", "kernel": "BEM products (forward row GEMV + transposed column GEMV)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                         "bytes_per_launch": 2 * word * nb * nb,
+                         "avg_launch_ms": bem["ms"] / max(bem["launches"], 1)},
+            "kernel_ms": {k: round(v["ms"], 2) for k, v in kinds.items()},
+            "cg_sweeps": prof["cg_sweeps"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
@@ -457,6 +546,9 @@ def main():
         return
     if args.workload == "served":
         run_served(args, ws, rank, local)
+        return
+    if args.workload == "large":
+        run_large(args, ws, rank, local)
         return
     run_ours(args, ws, rank, local)
 
