@@ -233,6 +233,15 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per millisecond of kernel time of the potential-solve
+# kernels, from one ncu capture each of the batched workload (profiles/), used to
+# report the roofline's measured traffic per launch: (bytes/ms) x average launch ms.
+PROFILED_DRAM_BYTES_PER_MS = {
+    "fp32": (5.415e9 / 6.009, "profiles/k_pcg_fp32_batched64_n30.md"),
+    "fp64_fp32iter": (20.499e9 / 19.453, "profiles/k_pcg_fp64_fp32iter_batched64_n30.md"),
+}
+
+
 def pcg_bytes_per_row(kind):
     """Algorithmic bytes of one PCG iteration per row and system: z gather, p rw,
     q rw (phase A); x rw, r rw, p and q read, z write (phase B) = 12 vector
@@ -342,13 +351,20 @@ def run_ours(args, ws, rank, local):
     dom = max(pcg, key=lambda k: pcg[k]["ms"])
     d = pcg[dom]
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    avg_ms = d["ms"] / max(d["launches"], 1)
+    traffic, traffic_src = None, None
+    if d["kind"] in PROFILED_DRAM_BYTES_PER_MS and args.workload == "batched":
+        rate, traffic_src = PROFILED_DRAM_BYTES_PER_MS[d["kind"]]
+        traffic = rate * avg_ms
     roofline = {"bound": "hbm", "kernel": f"k_pcg ({d['kind']} potential solves, forward + adjoint)",
                 "bytes_per_row_system_iteration": pcg_bytes_per_row(d["kind"]),
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum per ms of kernel time "
+                                   f"({traffic_src}) x average launch duration") if traffic_src else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "bytes_per_launch": d["bytes"] / max(d["launches"], 1),
-                "avg_launch_ms": d["ms"] / max(d["launches"], 1),
+                "avg_launch_ms": avg_ms,
                 "share_of_kernel_time": d["ms"] / total_kernel_ms if total_kernel_ms else None,
                 "other": {k: {"ms": round(v["ms"], 2), "GB_s": (v["bytes"] / (v["ms"] / 1e3) / 1e9
                                                                  if v["ms"] > 0 else None)}
