@@ -238,7 +238,6 @@ def run_reference(args, ws, rank):
 # report the roofline's measured traffic per launch: (bytes/ms) x average launch ms.
 PROFILED_DRAM_BYTES_PER_MS = {
     "fp32": (5.415e9 / 6.009, "profiles/k_pcg_fp32_batched64_n30.md"),
-    "fp64_fp32iter": (20.499e9 / 19.453, "profiles/k_pcg_fp64_fp32iter_batched64_n30.md"),
 }
 
 
@@ -246,9 +245,10 @@ def pcg_bytes_per_row(kind):
     """Algorithmic bytes of one PCG iteration per row and system: z gather, p rw,
     q rw (phase A); x rw, r rw, p and q read, z write (phase B) = 12 vector
     words.  FP32 solves: 12 x 4 B; plain FP64: 12 x 8 B; FP64 solves iterated in
-    FP32 (FP64 x, FP32 work vectors): 10 x 4 B + 2 x 8 B.  The int8 stiffness
-    tables are shared by all systems and not counted."""
-    return {"fp32": 48, "fp64": 96, "fp64_fp32iter": 56}[kind]
+    FP32: 12 x 4 B (the FP32 correction takes x's place; it is folded into the
+    FP64 x once per restart cycle, not counted).  The int8 stiffness tables are
+    shared by all systems and not counted."""
+    return {"fp32": 48, "fp64": 96, "fp64_fp32iter": 48}[kind]
 
 
 def run_ours(args, ws, rank, local):

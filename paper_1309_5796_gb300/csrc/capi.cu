@@ -1356,6 +1356,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     V.ic = ic;
     V.m32 = nullptr;   // FP64 evaluation: no FP32 copy of the trial point
     Launch L{s, ctx->num_sms, bar, err, &ctx->launches, sweeps, fin, 0};
+    L.tune = false;   // no waiting inside this call (and it may be captured)
     const MeshView mv = M->view();
     lbm_solve_opts oo = o;
     oo.max_iter = 0;

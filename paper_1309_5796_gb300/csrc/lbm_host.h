@@ -102,6 +102,7 @@ struct Launch {
     unsigned long long* sweeps;  // device counters [4]: batched PCG iterations per stage and precision
     double* fin;                 // device scratch for grid reductions (>= 4 * 512 doubles)
     int max_blocks;              // cap on the cooperative PCG grid (0: one block per SM)
+    bool tune = true;            // launch-shape autotuning allowed (it waits on events)
 };
 
 template <typename T>

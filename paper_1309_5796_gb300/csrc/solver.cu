@@ -15,6 +15,10 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "lbm_host.h"
@@ -475,6 +479,12 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     T* __restrict__ x = mode ? A.V.U2 : A.V.U1;
     // work vectors in W (MP: FP32 values in the FP64 arrays' storage)
     W* __restrict__ r = reinterpret_cast<W*>(A.V.r);
+    // where the update phase accumulates alpha p: x itself, or (MP) an FP32
+    // correction d in the unused upper half of r's FP64 storage, folded into the
+    // FP64 x once per cycle (no FP64 arithmetic in the iterations)
+    using XA = typename std::conditional<MP, W, T>::type;
+    XA* __restrict__ xacc = MP ? reinterpret_cast<XA*>(reinterpret_cast<W*>(A.V.r) + (size_t)A.M.N * C)
+                               : reinterpret_cast<XA*>(mode ? A.V.U2 : A.V.U1);
     W* __restrict__ z = reinterpret_cast<W*>(A.V.z);
     W* __restrict__ p = reinterpret_cast<W*>(A.V.p);
     W* __restrict__ q = reinterpret_cast<W*>(A.V.q);
@@ -518,6 +528,11 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 if (actk[k] && !neu[k])
                     x[(size_t)row * C + c0 + k] = mode ? A.V.ub_out[(size_t)(bp - 1) * C + bk[k]] : T(0);
         }
+    if constexpr (MP) {
+        const W zero[VEC] = {};
+        if (lane)
+            for (int row = row0; row < N; row += rstride) vstore<W, VEC>(&xacc[(size_t)row * C + c0], zero);
+    }
     if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
     // One cycle: the residual of the current x in the precision of x (T), then
     // preconditioned CG iterations in the work precision W.  MP (FP64 x, FP32
@@ -703,11 +718,11 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
         if (!reduce(tpq, 0)) return;
         if (tid < C) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
         __syncthreads();
-        T alpha[VEC];
+        XA alpha[VEC];
         W alphaw[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
-            alpha[k] = T(s_ab[c0 + k]);
+            alpha[k] = XA(s_ab[c0 + k]);
             alphaw[k] = W(s_ab[c0 + k]);
         }
         W v4[4][VEC];   // r.z, r.r, (unused), sum r: per-thread and block sums in W, grid sums in FP64
@@ -720,13 +735,13 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 const bool two = rowb < N;
                 const size_t ia = (size_t)row * C + c0, ibb = (size_t)(two ? rowb : row) * C + c0;
                 const int nda = node[row], ndb = node[two ? rowb : row];
-                T xa[VEC], xb[VEC];
+                XA xa[VEC], xb[VEC];
                 W ra[VEC], pa[VEC], qa[VEC], rb[VEC], pb[VEC], qb[VEC], za[VEC], zb[VEC];
-                vload<T, VEC, false>(xa, &x[ia]);
+                vload<XA, VEC, false>(xa, &xacc[ia]);
                 vload<W, VEC, false>(ra, &r[ia]);
                 vload<W, VEC, false>(pa, &p[ia]);
                 vload<W, VEC, false>(qa, &q[ia]);
-                vload<T, VEC, false>(xb, &x[ibb]);
+                vload<XA, VEC, false>(xb, &xacc[ibb]);
                 vload<W, VEC, false>(rb, &r[ibb]);
                 vload<W, VEC, false>(pb, &p[ibb]);
                 vload<W, VEC, false>(qb, &q[ibb]);
@@ -734,27 +749,27 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                 const W dinvb = W(1) / (GEN ? kdiagW[two ? rowb : row] : W((ndb >> 8) & 0xff));
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
-                    xa[k] += alpha[k] * T(pa[k]);
+                    xa[k] += alpha[k] * XA(pa[k]);
                     ra[k] -= alphaw[k] * qa[k];
                     za[k] = ra[k] * dinva;
                     v4[0][k] += ra[k] * za[k];
                     v4[1][k] += ra[k] * ra[k];
                     v4[3][k] += ra[k];
                 }
-                vstore<T, VEC>(&x[ia], xa);
+                vstore<XA, VEC>(&xacc[ia], xa);
                 vstore<W, VEC>(&r[ia], ra);
                 vstore<W, VEC>(&z[ia], za);
                 if (two) {
 #pragma unroll
                     for (int k = 0; k < VEC; ++k) {
-                        xb[k] += alpha[k] * T(pb[k]);
+                        xb[k] += alpha[k] * XA(pb[k]);
                         rb[k] -= alphaw[k] * qb[k];
                         zb[k] = rb[k] * dinvb;
                         v4[0][k] += rb[k] * zb[k];
                         v4[1][k] += rb[k] * rb[k];
                         v4[3][k] += rb[k];
                     }
-                    vstore<T, VEC>(&x[ibb], xb);
+                    vstore<XA, VEC>(&xacc[ibb], xb);
                     vstore<W, VEC>(&r[ibb], rb);
                     vstore<W, VEC>(&z[ibb], zb);
                 }
@@ -773,6 +788,21 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
     if constexpr (!MP) {
         break;
     } else {
+        // fold the cycle's FP32 correction into the FP64 x before anything reads x
+        if (lane)
+            for (int row = row0; row < N; row += rstride) {
+                const size_t ib = (size_t)row * C + c0;
+                T xv[VEC];
+                W dv[VEC];
+                const W zero[VEC] = {};
+                vload<T, VEC, false>(xv, &x[ib]);
+                vload<W, VEC, false>(dv, &xacc[ib]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) xv[k] += T(dv[k]);
+                vstore<T, VEC>(&x[ib], xv);
+                vstore<W, VEC>(&xacc[ib], zero);
+            }
+        if (!pcg_sync<SINGLE>(A.bar, epoch, A.err)) return;
         // done when every column met the tolerance on its true residual at the
         // start of this cycle (or ran out of iterations or cycles)
         if (__syncthreads_and(tid < C ? s_done[tid] : 1) || cycle + 1 >= MP_MAX_CYCLES) break;
@@ -1073,13 +1103,62 @@ int bem_chunks(int nb, int num_sms) {
     return S;
 }
 
+// ---- autotuner: row chunks of the transposed single-instance product ------------------
+// At the first product of a (nb, matrix type, vector type, SM count) the
+// column-parallel kernel is timed with 4, 8, 16 and 32 row chunks (CUDA events
+// on the launching stream; it reads the live input and writes only the
+// partial-sum scratch); the fastest is kept for the process.
+static std::mutex g_chunks_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_chunks;
+
+template <typename F>
+static int tuned_chunks(const Launch& L, int nb, int key_a, int key_b, F&& launch_with) {
+    const auto key = std::make_tuple(nb, key_a, key_b, L.num_sms);
+    {
+        std::lock_guard<std::mutex> lk(g_chunks_mu);
+        auto it = g_chunks.find(key);
+        if (it != g_chunks.end()) return it->second;
+    }
+    if (!L.tune) return bem_chunks(nb, L.num_sms);
+    int best = bem_chunks(nb, L.num_sms);
+    float best_ms = -1.f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int S : {4, 8, 16, 32}) {
+        float t[3];
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, L.stream);
+            launch_with(S);
+            cudaEventRecord(e1, L.stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t[rep], e0, e1);
+            *L.launches += 1;
+        }
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (best_ms < 0.f || med < best_ms) {
+            best = S;
+            best_ms = med;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_chunks_mu);
+    g_chunks[key] = best;
+    return best;
+}
+
+int gemv_chunks_chosen(int nb, int key_a, int key_b, int num_sms) {
+    std::lock_guard<std::mutex> lk(g_chunks_mu);
+    auto it = g_chunks.find(std::make_tuple(nb, key_a, key_b, num_sms));
+    return it == g_chunks.end() ? 0 : it->second;
+}
+
 template <typename TA, typename T>
 static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const BatchView<T>& V) {
     const int B = V.B, C = 2 * B, nb = M.nb;
     if (B == 1 && sizeof(TA) == 4 && sizeof(T) == 8) {
         // scratch: S chunks x nb partial sums, then hi/lo of both input vectors
-        const int S = bem_chunks(nb, L.num_sms);
-        const int rpc = (nb + S - 1) / S;
         double* part = (double*)V.bem_part;
         float* hf = (float*)(part + (size_t)32 * nb);
         float* lf = hf + nb;
@@ -1088,6 +1167,11 @@ static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const B
         const int sb = (nb + 255) / 256;
         k_split_vec<<<sb, 256, 0, L.stream>>>((const double*)V.ub_in, C, hf, lf, nb);
         k_split_vec<<<sb, 256, 0, L.stream>>>((const double*)V.ub_in + 1, C, ha, la, nb);
+        const int S = tuned_chunks(L, nb, 1, 2, [&](int s) {
+            k_gemv_t_part_split<<<dim3((nb + 255) / 256, s), 256, 0, L.stream>>>((const float*)Bm, ha, la, part, nb,
+                                                                              (nb + s - 1) / s);
+        });
+        const int rpc = (nb + S - 1) / S;
         int blocks = (nb * 32 + 255) / 256;
         if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
         k_gemv_split<<<blocks, 256, 0, L.stream>>>((const float*)Bm, hf, lf, (double*)V.ub_out, nb, C);
@@ -1098,7 +1182,11 @@ static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const B
         int blocks = (nb * 32 + 255) / 256;
         if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
         k_gemv<TA, T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub_in, V.ub_out, nb, C);
-        const int S = bem_chunks(nb, L.num_sms);
+        const int S = tuned_chunks(L, nb, (int)sizeof(TA), (int)sizeof(T), [&](int s) {
+            k_gemv_t_part<TA, T><<<dim3((nb + 255) / 256, s), 256, 0, L.stream>>>(Bm, V.ub_in + 1,
+                                                                                 (double*)V.bem_part, nb, C,
+                                                                                 (nb + s - 1) / s);
+        });
         const int rpc = (nb + S - 1) / S;
         k_gemv_t_part<TA, T><<<dim3((nb + 255) / 256, S), 256, 0, L.stream>>>(Bm, V.ub_in + 1, (double*)V.bem_part,
                                                                              nb, C, rpc);

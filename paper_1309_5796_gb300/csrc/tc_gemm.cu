@@ -16,6 +16,10 @@
 // quadrant).  Every wait on an mbarrier gives up after one second, sets the
 // context's error word and leaves the CTA through the common exit that frees
 // the TMEM columns.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cuda.h>
 #include <stdint.h>
 
@@ -306,12 +310,78 @@ static int make_map(CUtensorMap* map, const float* base, int inner, int outer, i
 
 int tc_ld(int nb) { return (nb + 31) & ~31; }
 
+constexpr int TC_MAX_SPLITS = 8;   // largest split-K count the autotuner tries
+
 size_t tc_scratch_floats(int nb, int B, int num_sms) {
+    (void)num_sms;
     const int ldp = tc_ld(nb);
-    const int mt = (nb + tc::BM - 1) / tc::BM;
-    int splits = (num_sms + mt - 1) / mt;
-    if (splits < 1) splits = 1;
-    return (size_t)2 * (2 * B) * ldp + (size_t)splits * nb * tc::BN + 64;
+    return (size_t)2 * (2 * B) * ldp + (size_t)TC_MAX_SPLITS * nb * tc::BN + 64;
+}
+
+// ---- autotuner: split-K count of the tensor-core product ----------------------------
+// At the first product of a (nb, B, SM count) the kernel is timed with every
+// candidate split count (K blocks per split rounded so that every split has
+// work) on the operands in scratch, with CUDA events on the launching stream;
+// the fastest is kept for the process.  Only scratch is written while tuning.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tc_splits;
+
+int splits_for(int nkb, int want, int* kps_out) {
+    int splits = want < 1 ? 1 : (want > nkb ? nkb : want);
+    const int kps = (nkb + splits - 1) / splits;
+    *kps_out = kps;
+    return (nkb + kps - 1) / kps;   // every split has at least one K block
+}
+}  // namespace
+
+static int tc_tuned_splits(const Launch& L, const CUtensorMap& mA, const CUtensorMap& mXh, const CUtensorMap& mXl,
+                           int nb, int B, float* ypart) {
+    const auto key = std::make_tuple(nb, B, L.num_sms);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tc_splits.find(key);
+        if (it != g_tc_splits.end()) return it->second;
+    }
+    const int mt = (nb + tc::BM - 1) / tc::BM, nkb = (nb + tc::BK - 1) / tc::BK;
+    if (!L.tune) return (L.num_sms + mt - 1) / mt;
+    int best = 0;
+    float best_ms = 0.f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int want = 1; want <= TC_MAX_SPLITS; ++want) {
+        int kps;
+        const int splits = splits_for(nkb, want, &kps);
+        if (splits != want) continue;
+        float t[3];
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, L.stream);
+            tc::k_bem_tc<<<dim3(mt, splits), tc::THREADS, tc::SMEM_BYTES, L.stream>>>(mA, mXh, mXl, 0, nb, B, kps,
+                                                                                      ypart, L.err);
+            cudaEventRecord(e1, L.stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t[rep], e0, e1);
+            *L.launches += 1;
+        }
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (best == 0 || med < best_ms) {
+            best = splits;
+            best_ms = med;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best == 0) best = 1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tc_splits[key] = best;
+    return best;
+}
+
+int tc_splits_chosen(int nb, int B, int num_sms) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tc_splits.find(std::make_tuple(nb, B, num_sms));
+    return it == g_tc_splits.end() ? 0 : it->second;
 }
 
 // Both BEM products of the batch on the tensor cores.  A32 / A32T: padded FP32
@@ -332,17 +402,14 @@ int bem_product_tc(const Launch& L, int nb, const float* A32, const float* A32T,
     const int total = nb * C;
     tc::k_tc_split<T><<<(total + 255) / 256, 256, 0, L.stream>>>(ub_in, nb, C, ldp, xhi, xlo);
     const int mt = (nb + tc::BM - 1) / tc::BM, nkb = (nb + tc::BK - 1) / tc::BK;
-    int splits = (L.num_sms + mt - 1) / mt;
-    if (splits > nkb) splits = nkb;
-    if (splits < 1) splits = 1;
-    const int kps = (nkb + splits - 1) / splits;
-    splits = (nkb + kps - 1) / kps;   // every split has at least one K block
     CUtensorMap mA, mAT, mXh, mXl;
     int e = make_map(&mA, A32, nb, nb, ldp, tc::BK, tc::BM);
     if (!e) e = make_map(&mAT, A32T, nb, nb, ldp, tc::BK, tc::BM);
     if (!e) e = make_map(&mXh, xhi, nb, C, ldp, tc::BK, tc::BN);
     if (!e) e = make_map(&mXl, xlo, nb, C, ldp, tc::BK, tc::BN);
     if (e) return e;
+    int kps;
+    const int splits = splits_for(nkb, tc_tuned_splits(L, mA, mXh, mXl, nb, B, ypart), &kps);
     const dim3 grid(mt, splits);
     // forward: rows 0..B-1 of X; adjoint: rows B..2B-1 with B^T
     tc::k_bem_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, L.stream>>>(mA, mXh, mXl, 0, nb, B, kps, ypart, L.err);
