@@ -6,4 +6,4 @@ counter-based generator, so that the oracle and the CUDA path start from the
 same bytes.
 """
 from .inputs import *  # noqa: F401,F403
-from .meshes import ball_mesh, jittered_cube  # noqa: F401
+from .meshes import ball_mesh, jittered_cube, l_shape  # noqa: F401

@@ -85,6 +85,25 @@ def jittered_cube(n: int, cell: float = 2e-9, amp: float = 0.1, seed: int = 6):
     return xyz, _orient(xyz, tets)
 
 
+def l_shape(n: int, cell: float = 2e-9):
+    """The n^3 cube lattice without the cells with i >= n/2 and j >= n/2: an
+    L-shaped prism (a non-convex body with a reflex edge along z), 5-tetrahedra
+    split, unused nodes removed and the rest renumbered in order."""
+    if n < 2 or n % 2:
+        raise ValueError("l_shape needs an even n >= 2")
+    nodes, tets = _five_tet_split(n)
+    h = n // 2
+    cells = np.arange(n ** 3)
+    cx, cy = cells % n, (cells // n) % n
+    keep_cell = ~((cx >= h) & (cy >= h))
+    tets = tets.reshape(n ** 3, 5, 4)[keep_cell].reshape(-1, 4)
+    used = np.unique(tets)
+    new_id = -np.ones(nodes.shape[0], dtype=np.int64)
+    new_id[used] = np.arange(used.size)
+    xyz = nodes[used].astype(np.float64) * cell
+    return xyz, _orient(xyz, new_id[tets])
+
+
 def ball_mesh(n: int, diameter: float = 20e-9):
     """The n^3 lattice of [-1, 1]^3 mapped onto a ball of the given diameter."""
     if n < 2 or n % 2:

@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle.bem import hat_double_layer, interior_solid_angle, box_interior_solid_angle
+from oracle.bem import bem_matrix_general, box_interior_solid_angle, hat_double_layer, interior_solid_angle
 from oracle.mesh import assemble_fp64, cube_mesh, length_unit, surface_faces, tet_mesh
 from oracle.micromag import MU0, mesh_problem
 from oracle.minimise import OK, minimise
@@ -164,3 +164,28 @@ def test_minimiser_on_ball_reaches_a_minimum():
     assert res.E < E0
     mz = (p.V * res.m[:, 2]).sum() / p.V.sum()
     assert mz > 0.999
+
+
+def test_non_convex_surface_solid_angles_and_bem():
+    """An L-shaped prism (a reflex edge along z): Girard's theorem gives 3 pi on
+    the reflex edge (interior dihedral 3 pi / 2 on a straight edge), pi on the
+    convex edges and 2 pi on the faces, and it agrees with the Gauss sum at
+    every surface node; B 1 = -1 still holds."""
+    from synth import l_shape
+    n, h = 4, 1.0
+    xyz, tets = l_shape(n, h)
+    g = tet_mesh(xyz, tets)
+    om = interior_solid_angle(g.nodes, g.bnd, g.tris)
+    excl = np.any(g.tris[None] == g.bnd[:, None, None], axis=2)
+    gauss = -hat_double_layer(g.nodes[g.bnd], g.nodes[g.tris], exclude=excl).sum(axis=(1, 2))
+    assert np.abs(om - gauss).max() < 1e-12
+    P = g.xyz_m[g.bnd]
+    on_reflex = (np.abs(P[:, 0] - n / 2 * h) < 1e-12) & (np.abs(P[:, 1] - n / 2 * h) < 1e-12) & \
+        (P[:, 2] > 0.5 * h) & (P[:, 2] < (n - 0.5) * h)
+    assert on_reflex.sum() == n - 1
+    assert np.abs(om[on_reflex] - 3 * math.pi).max() < 1e-12
+    on_face = (np.abs(P[:, 2]) < 1e-12) & (P[:, 0] > 0.5 * h) & (P[:, 0] < 1.5 * h) & \
+        (P[:, 1] > 0.5 * h) & (P[:, 1] < 1.5 * h)
+    assert on_face.sum() >= 1 and np.abs(om[on_face] - 2 * math.pi).max() < 1e-12
+    B = bem_matrix_general(g.nodes, g.bnd, g.tris)
+    assert np.abs(B.sum(axis=1) + 1.0).max() < 1e-12
