@@ -495,7 +495,10 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
             P->B = I->B;
             P->precision = LBM_FP64;
             P->tsize = 8;
-            P->bem32 = true;
+            // FP64 matrix and FP64 arithmetic: the FP32 product's rounding (its
+            // nb-term sums) left a stray-field error that kept the true torque of
+            // the final state near 4e-5 although the phase's own torque met tol
+            P->bem32 = false;
             // The FP64 phase fixes the final accuracy: its BEM products stay on the
             // SIMT path (FP32 matrix).  The tensor cores' FP32 accumulation is not
             // round-to-nearest, and over the long reductions of the product
@@ -1562,7 +1565,7 @@ Group* group_get(Server& S, int n, double cell) {
     if (lbm_instance_create(ctx, G->mesh_id, B, LBM_FP64, &G->i64_id) != LBM_OK) return bad(0);
     G->I32 = ctx->insts[G->i32_id];
     G->I64 = ctx->insts[G->i64_id];
-    G->I64->bem32 = true;      // the FP64 phase of mixed requests
+    G->I64->bem32 = false;     // the FP64 phase of mixed requests: FP64 matrix and arithmetic
     const int N = ctx->meshes[G->mesh_id]->N;
     if (cudaMalloc(&G->staged, sizeof(double) * 3 * N) != cudaSuccess) return bad(0);
     k_slots_done<<<(B + 127) / 128, 128, 0, ctx->stream>>>(G->I32->st, B);
