@@ -526,11 +526,14 @@ def run_large(args, ws, rank, local):
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # one evaluation = one forward and one transposed product; the matrix is FP32
-    # in both phases of a mixed run (FP64 matrix in FP64 runs)
+    # one evaluation = one forward and one transposed product: the FP32 matrix in
+    # the FP32 phase, the FP64 matrix in FP64 runs and in the FP64 phase of mixed
+    # runs (one BEM scope per evaluation: as many as first-stage solves)
     word = 8 if prec == lbm.LBM_FP64 else 4
     bem = prof["bem_product"]
-    bem_bytes = bem["launches"] * 2 * word * nb * nb
+    n32, n64 = prof["pcg1_fp32"]["launches"], prof["pcg1_fp64"]["launches"]
+    bem_bytes = (n32 * 2 * 4 + n64 * 2 * 8) * nb * nb if n32 + n64 == bem["launches"] else \
+        bem["launches"] * 2 * word * nb * nb
     achieved = bem_bytes / (bem["ms"] / 1e3) / 1e9 if bem["ms"] > 0 else 0.0
     kinds = {k: v for k, v in prof.items() if k not in ("cg_iters", "cg_sweeps")}
     line = {"metric": "solves/s, one instance on a large cube", "value": 1e3 / statistics.mean(ms),
@@ -547,7 +550,7 @@ def run_large(args, ws, rank, local):
             "roofline": {"bound": "hbm", "kernel": "BEM products (forward row GEMV + transposed column GEMV)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                         "bytes_per_launch": 2 * word * nb * nb,
+                         "bytes_per_launch": bem_bytes / max(bem["launches"], 1),
                          "avg_launch_ms": bem["ms"] / max(bem["launches"], 1)},
             "kernel_ms": {k: round(v["ms"], 2) for k, v in kinds.items()},
             "cg_sweeps": prof["cg_sweeps"]}
