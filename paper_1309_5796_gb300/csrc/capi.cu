@@ -93,7 +93,6 @@ struct Inst {
     double* staged = nullptr;      // B*N*3 doubles (host <-> device layout conversion)
     double* staged_u = nullptr;    // B*2*N doubles
     Inst* polish = nullptr;        // FP64 shadow batch finishing mixed-precision runs
-    bool bem32 = false;            // BEM product with the FP32 matrix (FP64 phase of mixed runs)
     bool use_tc = false;           // BEM products on the tensor cores (LBM_MIXED_TC, 2 <= batch <= 64)
     float* tc_scratch = nullptr;
     bool owns_tc_scratch = true;
@@ -207,7 +206,7 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.q = take(tsize * N * C);
     L.ub_in = take(tsize * nb * C);
     L.ub_out = take(tsize * nb * C);
-    L.bem_part = take(8 * 34 * nb);   // 32 x nb partial sums + hi/lo FP32 parts of two vectors
+    L.bem_part = take(8 * 32 * nb);   // 32 x nb partial sums of the transposed product
     L.m32 = tsize == 4 ? take(4 * N * 3 * B) : 0;
     L.total = o;
     return L;
@@ -355,7 +354,7 @@ int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, cons
                 e = bem_product_tc<T>(L, M.nb, M.tcA, M.tcAT, V.ub_in, V.ub_out, V.B, I.tc_scratch);
                 if (e) return fail(LBM_E_CUDA, "tensor-core BEM product failed (%d)", e);
             } else {
-                bem_product<T>(L, mv, V, I.bem32);
+                bem_product<T>(L, mv, V);
             }
         }
         {
@@ -495,10 +494,6 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
             P->B = I->B;
             P->precision = LBM_FP64;
             P->tsize = 8;
-            // FP64 matrix and FP64 arithmetic: the FP32 product's rounding (its
-            // nb-term sums) left a stray-field error that kept the true torque of
-            // the final state near 4e-5 although the phase's own torque met tol
-            P->bem32 = false;
             // The FP64 phase fixes the final accuracy: its BEM products stay on the
             // SIMT path (FP32 matrix).  The tensor cores' FP32 accumulation is not
             // round-to-nearest, and over the long reductions of the product
@@ -1368,7 +1363,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     if (o.demag) {
         int e = pcg_solve<double>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, false);
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
-        bem_product<double>(L, mv, V, false);
+        bem_product<double>(L, mv, V);
         e = pcg_solve<double>(L, mv, V, 1, o.cg_tol, o.cg_max_iter, false);
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
     }
@@ -1565,7 +1560,6 @@ Group* group_get(Server& S, int n, double cell) {
     if (lbm_instance_create(ctx, G->mesh_id, B, LBM_FP64, &G->i64_id) != LBM_OK) return bad(0);
     G->I32 = ctx->insts[G->i32_id];
     G->I64 = ctx->insts[G->i64_id];
-    G->I64->bem32 = false;     // the FP64 phase of mixed requests: FP64 matrix and arithmetic
     const int N = ctx->meshes[G->mesh_id]->N;
     if (cudaMalloc(&G->staged, sizeof(double) * 3 * N) != cudaSuccess) return bad(0);
     k_slots_done<<<(B + 127) / 128, 128, 0, ctx->stream>>>(G->I32->st, B);

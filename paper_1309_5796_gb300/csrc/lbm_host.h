@@ -109,7 +109,7 @@ template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
               bool mixed_iter);
 template <typename T>
-void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V, bool bem32);
+void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V);
 template <typename T>
 void field_eval(const Launch& L, const MeshView& M, const BatchView<T>& V, int demag);
 template <typename T>

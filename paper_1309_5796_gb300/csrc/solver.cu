@@ -984,55 +984,6 @@ __global__ void k_gemv_t_part(const TA* __restrict__ A, const T* __restrict__ x,
     part[(size_t)blockIdx.y * nb + j] = acc.value();
 }
 
-// FP64 vectors against the FP32 matrix (FP64 phase of single-instance mixed
-// runs): x is split once into FP32 parts x = hi + lo (about 48 significant
-// bits), and each product sums a*hi + a*lo with the compensated FP32
-// accumulator, so that the product reads 4 bytes per matrix entry and never
-// waits on the FP64 units.
-__global__ void k_split_vec(const double* __restrict__ x, int inc, float* __restrict__ hi, float* __restrict__ lo,
-                            int nb) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
-        const double v = x[(size_t)j * inc];
-        const float h = (float)v;
-        hi[j] = h;
-        lo[j] = (float)(v - (double)h);
-    }
-}
-
-__global__ void k_gemv_split(const float* __restrict__ A, const float* __restrict__ hi, const float* __restrict__ lo,
-                             double* __restrict__ y, int nb, int inc) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int row = warp; row < nb; row += nw) {
-        const float* a = A + (size_t)row * nb;
-        DotAcc<float> acc;
-        for (int j = lane; j < nb; j += 32) {
-            const float aj = a[j];
-            acc.add(aj, hi[j]);
-            acc.add(aj, lo[j]);
-        }
-        double v = acc.value();
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[(size_t)row * inc] = v;
-    }
-}
-
-__global__ void k_gemv_t_part_split(const float* __restrict__ A, const float* __restrict__ hi,
-                                    const float* __restrict__ lo, double* __restrict__ part, int nb,
-                                    int rows_per_chunk) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i0 = blockIdx.y * rows_per_chunk, i1 = min(nb, i0 + rows_per_chunk);
-    if (j >= nb) return;
-    DotAcc<float> acc;
-#pragma unroll 4
-    for (int i = i0; i < i1; ++i) {
-        const float a = A[(size_t)i * nb + j];
-        acc.add(a, hi[i]);
-        acc.add(a, lo[i]);
-    }
-    part[(size_t)blockIdx.y * nb + j] = acc.value();
-}
-
 template <typename T>
 __global__ void k_sum_parts(const double* __restrict__ part, int S, int nb, T* __restrict__ y, int inc) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1157,28 +1108,7 @@ int gemv_chunks_chosen(int nb, int key_a, int key_b, int num_sms) {
 template <typename TA, typename T>
 static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const BatchView<T>& V) {
     const int B = V.B, C = 2 * B, nb = M.nb;
-    if (B == 1 && sizeof(TA) == 4 && sizeof(T) == 8) {
-        // scratch: S chunks x nb partial sums, then hi/lo of both input vectors
-        double* part = (double*)V.bem_part;
-        float* hf = (float*)(part + (size_t)32 * nb);
-        float* lf = hf + nb;
-        float* ha = lf + nb;
-        float* la = ha + nb;
-        const int sb = (nb + 255) / 256;
-        k_split_vec<<<sb, 256, 0, L.stream>>>((const double*)V.ub_in, C, hf, lf, nb);
-        k_split_vec<<<sb, 256, 0, L.stream>>>((const double*)V.ub_in + 1, C, ha, la, nb);
-        const int S = tuned_chunks(L, nb, 1, 2, [&](int s) {
-            k_gemv_t_part_split<<<dim3((nb + 255) / 256, s), 256, 0, L.stream>>>((const float*)Bm, ha, la, part, nb,
-                                                                              (nb + s - 1) / s);
-        });
-        const int rpc = (nb + S - 1) / S;
-        int blocks = (nb * 32 + 255) / 256;
-        if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
-        k_gemv_split<<<blocks, 256, 0, L.stream>>>((const float*)Bm, hf, lf, (double*)V.ub_out, nb, C);
-        k_gemv_t_part_split<<<dim3((nb + 255) / 256, S), 256, 0, L.stream>>>((const float*)Bm, ha, la, part, nb, rpc);
-        k_sum_parts<T><<<(nb + 255) / 256, 256, 0, L.stream>>>(part, S, nb, V.ub_out + 1, C);
-        *L.launches += 5;
-    } else if (B == 1) {
+    if (B == 1) {
         int blocks = (nb * 32 + 255) / 256;
         if (blocks > 8 * L.num_sms) blocks = 8 * L.num_sms;
         k_gemv<TA, T><<<blocks, 256, 0, L.stream>>>(Bm, V.ub_in, V.ub_out, nb, C);
@@ -1200,11 +1130,12 @@ static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const B
     }
 }
 
-// bem32: use the FP32 copy of B (a fixed operator, so energy and gradient stay
-// consistent) even for FP64 vectors -- the FP64 phase of a mixed-precision run.
+// FP32 vectors use the FP32 copy of B, FP64 vectors the FP64 matrix (the FP64
+// phase of a mixed run included: FP32 arithmetic in its products perturbed the
+// stray field enough to keep the true torque of the final state near 4e-5).
 template <typename T>
-void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V, bool bem32) {
-    if (sizeof(T) == 4 || bem32) bem_launch<float, T>(L, M.B32, M, V);
+void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V) {
+    if constexpr (sizeof(T) == 4) bem_launch<float, T>(L, M.B32, M, V);
     else bem_launch<double, T>(L, M.B64, M, V);
 }
 
@@ -1665,7 +1596,7 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
 
 #define LBM_INSTANTIATE(T)                                                                               \
     template int pcg_solve<T>(const Launch&, const MeshView&, const BatchView<T>&, int, double, int, bool); \
-    template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&, bool);               \
+    template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&);                     \
     template void field_eval<T>(const Launch&, const MeshView&, const BatchView<T>&, int);                 \
     template void trial_update<T>(const Launch&, const MeshView&, const BatchView<T>&);                    \
     template void decide<T>(const Launch&, const MeshView&, const BatchView<T>&, const StepOpts&, int);    \
