@@ -58,6 +58,8 @@ def parse():
                     help="instances of the plain-FP64 single-instance comparison arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--ref-step-s", type=float, default=0.0,
+                    help="seconds of oracle work per step of the reference arm (0: 5-30 s by step count)")
     ap.add_argument("--workload", default="batched", choices=["batched", "served", "large"],
                     help="batched: 64 same-mesh instances (default); served: Poisson request stream; "
                          "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix)")
@@ -198,7 +200,7 @@ def run_reference(args, ws, rank):
     from oracle.minimise import minimise
     inst = insts[0]
     p = CubeProblem(inst.n, inst.Js, inst.A, inst.K1, inst.axis)
-    per_step = max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
+    per_step = args.ref_step_s if args.ref_step_s > 0 else max(5.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
     vals = []
     total_evals = 0
     for s in range(args.warmup + args.steps):
