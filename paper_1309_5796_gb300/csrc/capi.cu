@@ -15,6 +15,8 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -47,6 +49,22 @@ int fail(int code, const char* fmt, ...) {
     } while (0)
 
 constexpr double MU0 = 4e-7 * 3.14159265358979323846;
+
+// No C++ exception crosses the C interface: every entry point runs inside
+// LBM_TRY / LBM_CATCH, which turn host allocation failures into LBM_E_OOM and
+// anything else (e.g. a thread that cannot be started) into LBM_E_INVALID.
+#define LBM_TRY try {
+#define LBM_CATCH                                                                    \
+    }                                                                                \
+    catch (const std::bad_alloc&) {                                                  \
+        return fail(LBM_E_OOM, "host memory allocation failed");                     \
+    }                                                                                \
+    catch (const std::exception& ex_) {                                              \
+        return fail(LBM_E_INVALID, "%s", ex_.what());                                \
+    }                                                                                \
+    catch (...) {                                                                    \
+        return fail(LBM_E_INVALID, "unexpected error");                              \
+    }
 
 struct Mesh {
     int n = 0, N = 0, nb = 0, nnz = 0, F = 0, T = 0;
@@ -588,6 +606,7 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
 const char* lbm_last_error(void) { return g_err.c_str(); }
 
 int lbm_create(lbm_ctx** out, int32_t device, void* stream) {
+    LBM_TRY
     if (!out) return fail(LBM_E_INVALID, "null output pointer");
     *out = nullptr;
     int ndev = 0;
@@ -623,9 +642,11 @@ int lbm_create(lbm_ctx** out, int32_t device, void* stream) {
     cudaMemset(c->sweeps, 0, 64);
     *out = c;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_destroy(lbm_ctx* ctx) {
+    LBM_TRY
     if (!ctx) return LBM_OK;
     if (ctx->server) lbm_serve_stop(ctx);
     cudaSetDevice(ctx->device);
@@ -641,15 +662,19 @@ int lbm_destroy(lbm_ctx* ctx) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_launch_count(lbm_ctx* ctx, int64_t* count) {
+    LBM_TRY
     if (!ctx || !count) return fail(LBM_E_INVALID, "null argument");
     *count = ctx->launches;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
+    LBM_TRY
     if (!ctx || !out || n < 1 || n > 96 || !(cell_m > 0)) return fail(LBM_E_INVALID, "lbm_mesh_cube: bad argument");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
@@ -738,10 +763,12 @@ int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
     ctx->meshes[id] = M;
     *out = id;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_mesh_upload(lbm_ctx* ctx, const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                     lbm_mesh* out) {
+    LBM_TRY
     if (!ctx || !out || !xyz || !tets) return fail(LBM_E_INVALID, "lbm_mesh_upload: null argument");
     if (n_nodes < 4 || n_nodes > LBM_UPLOAD_MAX_NODES || n_tets < 1 || n_tets > LBM_UPLOAD_MAX_TETS)
         return fail(LBM_E_INVALID, "lbm_mesh_upload: need 4 <= n_nodes <= %d and 1 <= n_tets <= %d",
@@ -862,9 +889,11 @@ int lbm_mesh_upload(lbm_ctx* ctx, const double* xyz, int64_t n_nodes, const int3
     ctx->meshes[id] = M;
     *out = id;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_mesh_values(lbm_ctx* ctx, lbm_mesh mesh, double* K, double* G, double* Gt, double* V, double* unit_m) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M) return fail(LBM_E_INVALID, "unknown mesh");
     CK(cudaSetDevice(ctx->device));
@@ -904,9 +933,11 @@ int lbm_mesh_values(lbm_ctx* ctx, lbm_mesh mesh, double* K, double* G, double* G
     if (V)
         for (int i = 0; i < M->N; ++i) V[i] = sV * (double)(nd[i] & 0xff);
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_mesh_destroy(lbm_ctx* ctx, lbm_mesh mesh) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M) return fail(LBM_E_INVALID, "unknown mesh");
     for (auto& kv : ctx->insts)
@@ -915,9 +946,11 @@ int lbm_mesh_destroy(lbm_ctx* ctx, lbm_mesh mesh) {
     free_mesh(M);
     ctx->meshes.erase(mesh);
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_mesh_info(lbm_ctx* ctx, lbm_mesh mesh, int64_t info[8]) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M || !info) return fail(LBM_E_INVALID, "unknown mesh");
     info[0] = M->N;
@@ -929,10 +962,12 @@ int lbm_mesh_info(lbm_ctx* ctx, lbm_mesh mesh, int64_t info[8]) {
     info[6] = M->n;
     info[7] = 0;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_mesh_export(lbm_ctx* ctx, lbm_mesh mesh, int32_t* tets, int32_t* rowptr, int32_t* col, int32_t* kval,
                     int32_t* gval, int32_t* gtval, int32_t* vol, int32_t* bnd, int32_t* tris) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M) return fail(LBM_E_INVALID, "unknown mesh");
     CK(cudaSetDevice(ctx->device));
@@ -974,18 +1009,22 @@ int lbm_mesh_export(lbm_ctx* ctx, lbm_mesh mesh, int32_t* tets, int32_t* rowptr,
     if (vol)
         for (int i = 0; i < M->N; ++i) vol[i] = nd[i] & 0xff;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_bem_rows(lbm_ctx* ctx, lbm_mesh mesh, int64_t row0, int64_t nrows, double* out) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M || !out || row0 < 0 || nrows < 0 || row0 + nrows > M->nb) return fail(LBM_E_INVALID, "bad rows");
     CK(cudaMemcpyAsync(out, M->B64 + (size_t)row0 * M->nb, sizeof(double) * nrows * M->nb,
                        cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t precision, lbm_inst* out) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M || !out) return fail(LBM_E_INVALID, "unknown mesh");
     if (batch < 1 || batch > 256) return fail(LBM_E_INVALID, "batch must be in [1, 256]");
@@ -1051,18 +1090,22 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
     if (rc) return rc;
     *out = id;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_instance_destroy(lbm_ctx* ctx, lbm_inst inst) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I) return fail(LBM_E_INVALID, "unknown instance");
     cudaStreamSynchronize(ctx->stream);
     free_inst(I);
     ctx->insts.erase(inst);
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_set_material(lbm_ctx* ctx, lbm_inst inst, const lbm_material* mats) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !mats) return fail(LBM_E_INVALID, "bad argument");
     for (int b = 0; b < I->B; ++b)
@@ -1070,16 +1113,20 @@ int lbm_set_material(lbm_ctx* ctx, lbm_inst inst, const lbm_material* mats) {
             return fail(LBM_E_INVALID, "material %d: need Js > 0, A >= 0, finite K1", b);
     I->mats.assign(mats, mats + I->B);
     return upload_consts(ctx, I, *ctx->meshes[I->mesh]);
+    LBM_CATCH
 }
 
 int lbm_set_field(lbm_ctx* ctx, lbm_inst inst, const double* h) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !h) return fail(LBM_E_INVALID, "bad argument");
     I->h.assign(h, h + 3 * I->B);
     return upload_consts(ctx, I, *ctx->meshes[I->mesh]);
+    LBM_CATCH
 }
 
 int lbm_set_m(lbm_ctx* ctx, lbm_inst inst, const double* m) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !m) return fail(LBM_E_INVALID, "bad argument");
     Mesh& M = *ctx->meshes[I->mesh];
@@ -1093,9 +1140,11 @@ int lbm_set_m(lbm_ctx* ctx, lbm_inst inst, const double* m) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaGetLastError());
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_set_m_device(lbm_ctx* ctx, lbm_inst inst, const double* d_m) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !d_m) return fail(LBM_E_INVALID, "bad argument");
     Mesh& M = *ctx->meshes[I->mesh];
@@ -1107,15 +1156,19 @@ int lbm_set_m_device(lbm_ctx* ctx, lbm_inst inst, const double* d_m) {
     else pack_m<float>(L, M.view(), batch_view<float>(ctx, M, *I, false), d_m);
     CK(cudaGetLastError());
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_profile_enable(lbm_ctx* ctx, int32_t on) {
+    LBM_TRY
     if (!ctx) return fail(LBM_E_INVALID, "null context");
     ctx->prof = on != 0;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset) {
+    LBM_TRY
     if (!ctx || !out) return fail(LBM_E_INVALID, "null argument");
     CK(cudaStreamSynchronize(ctx->stream));
     prof_harvest(ctx);
@@ -1137,9 +1190,11 @@ int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset) {
         ctx->prof_cg[0] = ctx->prof_cg[1] = 0;
     }
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_get_m(lbm_ctx* ctx, lbm_inst inst, double* m) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !m) return fail(LBM_E_INVALID, "bad argument");
     Mesh& M = *ctx->meshes[I->mesh];
@@ -1150,9 +1205,11 @@ int lbm_get_m(lbm_ctx* ctx, lbm_inst inst, double* m) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaGetLastError());
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_evaluate(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, double* h, double* u, lbm_result* res) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I) return fail(LBM_E_INVALID, "unknown instance");
     lbm_solve_opts o;
@@ -1162,9 +1219,11 @@ int lbm_evaluate(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, double*
     CK(cudaSetDevice(ctx->device));
     return I->tsize == 8 ? run_minimise<double>(ctx, I, o, res, true, h, u)
                          : run_minimise<float>(ctx, I, o, res, true, h, u);
+    LBM_CATCH
 }
 
 int lbm_energy(lbm_ctx* ctx, lbm_inst inst, double* e_terms) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !e_terms) return fail(LBM_E_INVALID, "lbm_energy: unknown instance or null output");
     lbm_solve_opts o;
@@ -1175,9 +1234,11 @@ int lbm_energy(lbm_ctx* ctx, lbm_inst inst, double* e_terms) {
     for (int b = 0; b < I->B; ++b)
         for (int k = 0; k < 5; ++k) e_terms[5 * b + k] = r[b].energy[k];
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_minimise(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, lbm_result* res) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I) return fail(LBM_E_INVALID, "unknown instance");
     lbm_solve_opts o;
@@ -1187,10 +1248,12 @@ int lbm_minimise(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, lbm_res
     CK(cudaSetDevice(ctx->device));
     if (I->tsize == 8) return run_minimise<double>(ctx, I, o, res, false, nullptr, nullptr);
     return minimise_mixed(ctx, I, o, res);
+    LBM_CATCH
 }
 
 int lbm_hysteresis(lbm_ctx* ctx, lbm_inst inst, const double dir[3], const double* fields, int32_t n_pts,
                    const lbm_solve_opts* opt, double* m_par, double* energy, lbm_result* res) {
+    LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
     if (!I || !dir || !fields || n_pts < 0) return fail(LBM_E_INVALID, "bad argument");
     const double dn = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
@@ -1212,6 +1275,7 @@ int lbm_hysteresis(lbm_ctx* ctx, lbm_inst inst, const double dir[3], const doubl
         }
     }
     return LBM_OK;
+    LBM_CATCH
 }
 
 }  // extern "C"
@@ -1801,6 +1865,7 @@ void lbm_default_serve_opts(lbm_serve_opts* o) {
 }
 
 int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt) {
+    LBM_TRY
     if (!ctx) return fail(LBM_E_INVALID, "null context");
     if (ctx->server) return fail(LBM_E_INVALID, "already serving");
     Server* S = new Server();
@@ -1816,9 +1881,11 @@ int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt) {
     ctx->server = S;
     S->worker = std::thread(serve_loop, S);
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_submit(lbm_ctx* ctx, const lbm_request* req, lbm_ticket* out) {
+    LBM_TRY
     if (!ctx || !ctx->server || !req || !out || !req->m0) return fail(LBM_E_INVALID, "bad argument or not serving");
     if (req->n < 1 || req->n > 96 || !(req->cell_m > 0) || !(req->mat.Js > 0) ||
         (req->precision != LBM_FP64 && req->precision != LBM_MIXED))
@@ -1839,9 +1906,11 @@ int lbm_submit(lbm_ctx* ctx, const lbm_request* req, lbm_ticket* out) {
     *out = t;
     S.cv_work.notify_one();
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_poll(lbm_ctx* ctx, lbm_ticket t, lbm_result* res, double* m_out) {
+    LBM_TRY
     if (!ctx || !ctx->server) return fail(LBM_E_INVALID, "not serving");
     Server& S = *ctx->server;
     std::lock_guard<std::mutex> lk(S.mu);
@@ -1853,9 +1922,11 @@ int lbm_poll(lbm_ctx* ctx, lbm_ticket t, lbm_result* res, double* m_out) {
     if (res) *res = T.res;
     if (m_out && !T.m_out.empty()) memcpy(m_out, T.m_out.data(), sizeof(double) * T.m_out.size());
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_wait(lbm_ctx* ctx, lbm_ticket t, double timeout_s, lbm_result* res, double* m_out) {
+    LBM_TRY
     if (!ctx || !ctx->server) return fail(LBM_E_INVALID, "not serving");
     Server& S = *ctx->server;
     const double t_end = now_s() + timeout_s;
@@ -1866,9 +1937,11 @@ int lbm_wait(lbm_ctx* ctx, lbm_ticket t, double timeout_s, lbm_result* res, doub
         std::unique_lock<std::mutex> lk(S.mu);
         S.cv_done.wait_for(lk, std::chrono::milliseconds(5));
     }
+    LBM_CATCH
 }
 
 int lbm_serve_stats(lbm_ctx* ctx, int64_t stats[8]) {
+    LBM_TRY
     if (!ctx || !ctx->server || !stats) return fail(LBM_E_INVALID, "not serving");
     Server& S = *ctx->server;
     std::lock_guard<std::mutex> lk(S.mu);
@@ -1883,9 +1956,11 @@ int lbm_serve_stats(lbm_ctx* ctx, int64_t stats[8]) {
     stats[6] = S.n_stalls;
     stats[7] = S.n_evicted;
     return LBM_OK;
+    LBM_CATCH
 }
 
 int lbm_serve_stop(lbm_ctx* ctx) {
+    LBM_TRY
     if (!ctx || !ctx->server) return fail(LBM_E_INVALID, "not serving");
     Server* S = ctx->server;
     {
@@ -1899,6 +1974,7 @@ int lbm_serve_stop(lbm_ctx* ctx) {
     ctx->server = nullptr;
     delete S;
     return LBM_OK;
+    LBM_CATCH
 }
 
 }  // extern "C"
