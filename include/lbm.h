@@ -167,8 +167,9 @@ int lbm_mesh_upload(lbm_ctx* ctx, const double* xyz, int64_t n_nodes, const int3
                     int64_t n_tets, lbm_mesh* out);
 int lbm_mesh_destroy(lbm_ctx* ctx, lbm_mesh mesh);
 
-/* FP64 copies of the assembled operators of any mesh, in SI units, on the CSR
- * pattern of lbm_mesh_export (any pointer may be NULL):
+/* FP64 copies of the assembled P1 operators of any mesh (Sec. 2.1 finite element
+ * discretisation), in SI units, on the CSR pattern of lbm_mesh_export (any
+ * pointer may be NULL):
  *   K[nnz] int grad phi_i . grad phi_j (m), G[nnz*3] sum_e (vol_e/4) grad phi_i|_e
  *   (m^2), Gt[nnz*3] G_ji, V[N] lumped volumes (m^3), unit_m the length unit
  *   (the cell edge of a cube mesh, L of an uploaded one). */

@@ -55,3 +55,17 @@ def test_create_without_gpu_fails_cleanly(library):
         pytest.skip("a GPU is present")
     with pytest.raises(lbm.LBMError):
         lbm.Context(0)
+
+
+def test_header_is_plain_c():
+    """include/lbm.h is a C interface: it compiles as C99 and as C++17."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    hdr = os.path.join(ROOT, "include", "lbm.h")
+    for args in (["-std=c99", "-x", "c"], ["-std=c++17", "-x", "c++"]):
+        r = subprocess.run([gcc, "-fsyntax-only", "-Wall", "-Wextra", "-Werror", *args, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
