@@ -69,3 +69,28 @@ def test_header_is_plain_c():
         r = subprocess.run([gcc, "-fsyntax-only", "-Wall", "-Wextra", "-Werror", *args, hdr],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_c_client_builds_and_runs():
+    """tests/c_client/minimise.c, a plain C99 program using only include/lbm.h,
+    compiles and links against liblbm.so; run, it either minimises (a GPU is
+    present: exit 0) or reports the failed context creation cleanly (no GPU:
+    exit 1 with the library's message), never crashes."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lib_dir = os.path.dirname(lbm_build.build())
+    with tempfile.TemporaryDirectory() as tmp:
+        exe = os.path.join(tmp, "minimise")
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                            os.path.join(ROOT, "tests", "c_client", "minimise.c"), "-L", lib_dir, "-llbm", "-lm",
+                            "-Wl,-rpath," + lib_dir, "-o", exe], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        run = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+        if run.returncode == 0:
+            assert run.stdout.count("status 0") == 2
+        else:
+            assert run.returncode == 1 and "lbm_create" in run.stderr, (run.returncode, run.stderr)
