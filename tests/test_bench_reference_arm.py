@@ -14,7 +14,8 @@ import bench  # noqa: E402
 
 def test_reference_arm_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--ref-step-s", "1"], capture_output=True, text=True, timeout=600,
+                          "--warmup", "0", "--ref-step-s", "1", "--ref-cores", "2"], capture_output=True,
+                         text=True, timeout=900,
                          cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
@@ -23,6 +24,6 @@ def test_reference_arm_line():
     assert line["config"] == bench.batched_config()
     assert line["value"] > 0 and line["n_gpus"] == 1 and line["steps"] == 1 and line["warmup"] == 0
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["value"] == line["value"] and "2 processes" in cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
