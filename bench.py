@@ -194,7 +194,7 @@ def host_cores(max_workers=None):
     return min(n, max_workers) if max_workers else n
 
 
-def oracle_all_cores(budget_s, cores, n_windows=1, setup_timeout_s=900.0):
+def oracle_all_cores(budget_s, cores, n_windows=1, setup_timeout_s=300.0):
     """Oracle throughput with `cores` processes at once, each on its own instance
     of the workload; all start every timed window together.  Returns, per
     window, (evaluations per second, evaluations, seconds)."""
@@ -212,7 +212,7 @@ def oracle_all_cores(budget_s, cores, n_windows=1, setup_timeout_s=900.0):
         out = []
         for w in range(n_windows):
             go[w].set()
-            res = [q_out.get(timeout=budget_s + 600.0) for _ in range(cores)]
+            res = [q_out.get(timeout=budget_s + 300.0) for _ in range(cores)]
             evals = sum(r[1] for r in res)
             secs = max(r[2] for r in res)
             out.append((evals / secs, evals, secs))
