@@ -189,3 +189,17 @@ def test_non_convex_surface_solid_angles_and_bem():
     assert on_face.sum() >= 1 and np.abs(om[on_face] - 2 * math.pi).max() < 1e-12
     B = bem_matrix_general(g.nodes, g.bnd, g.tris)
     assert np.abs(B.sum(axis=1) + 1.0).max() < 1e-12
+
+
+def test_assembly_is_independent_of_tetrahedron_orientation():
+    """lbm_mesh_upload accepts any vertex order: reversing the orientation of
+    every other tetrahedron leaves K, G, G^T, V and the outward surface unchanged."""
+    xyz, tets = jittered_cube(3, 2e-9, 0.1, seed=13)
+    flipped = tets.copy()
+    flipped[::2] = flipped[::2][:, [0, 1, 3, 2]]
+    a = tet_mesh(xyz, tets)
+    b = tet_mesh(xyz, flipped)
+    for key in ("K", "G", "Gt", "V"):
+        ref = getattr(a.ops, key)
+        assert np.abs(getattr(b.ops, key) - ref).max() <= 1e-15 * np.abs(ref).max(), key
+    assert np.array_equal(a.tris, b.tris) and np.array_equal(a.bnd, b.bnd)
