@@ -94,3 +94,45 @@ def test_c_client_builds_and_runs():
             assert run.stdout.count("status 0") == 2
         else:
             assert run.returncode == 1 and "lbm_create" in run.stderr, (run.returncode, run.stderr)
+
+
+def test_ctypes_structs_match_the_header():
+    """Every ctypes structure of the binding has the C struct's field names in the
+    same order, the same offsets and the same size (checked by compiling a C
+    program that prints offsetof/sizeof from include/lbm.h)."""
+    import json
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    pairs = [("lbm_material", lbm.Material), ("lbm_solve_opts", lbm.SolveOpts), ("lbm_result", lbm.Result),
+             ("lbm_profile_stats", lbm.ProfileStats), ("lbm_request", lbm.Request),
+             ("lbm_serve_opts", lbm.ServeOpts)]
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "lbm.h"', "int main(void) {", 'printf("{");']
+    for k, (cname, py) in enumerate(pairs):
+        sep = "," if k else ""
+        src.append(f'printf("{sep}\\"{cname}\\": {{\\"size\\": %zu, \\"fields\\": [", sizeof({cname}));')
+        for j, (fname, _) in enumerate(py._fields_):
+            fsep = "," if j else ""
+            src.append(f'printf("{fsep}[\\"{fname}\\", %zu]", offsetof({cname}, {fname}));')
+        src.append('printf("]}");')
+    src += ['printf("}\\n");', "return 0; }"]
+    with tempfile.TemporaryDirectory() as tmp:
+        c_file, exe = os.path.join(tmp, "layout.c"), os.path.join(tmp, "layout")
+        open(c_file, "w").write("\n".join(src))
+        r = subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), c_file, "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr     # a field missing from the C struct fails here
+        layout = json.loads(subprocess.run([exe], capture_output=True, text=True, check=True).stdout)
+    for cname, py in pairs:
+        c = layout[cname]
+        assert c["size"] == ctypes_sizeof(py), (cname, c["size"], ctypes_sizeof(py))
+        for (fname, off) in c["fields"]:
+            assert getattr(py, fname).offset == off, (cname, fname, off, getattr(py, fname).offset)
+
+
+def ctypes_sizeof(t):
+    import ctypes
+    return ctypes.sizeof(t)
