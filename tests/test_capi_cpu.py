@@ -136,3 +136,17 @@ def test_ctypes_structs_match_the_header():
 def ctypes_sizeof(t):
     import ctypes
     return ctypes.sizeof(t)
+
+
+def test_binding_argument_counts_match_the_header():
+    """Each prototype in include/lbm.h has as many parameters as the binding's
+    argtypes for that symbol (a wrong count would misread arguments silently)."""
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(?:int|void|const char\*)\s+(lbm_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = m.group(2).strip()
+        protos[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    assert len(protos) == len(lbm.SIGNATURES)
+    for name, _, args in lbm.SIGNATURES:
+        assert protos[name] == len(args), (name, protos[name], len(args))
