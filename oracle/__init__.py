@@ -21,7 +21,9 @@ The oracle follows Exl et al., "LaBonte's method revisited" (arXiv:1309.5796):
 Readings where the paper is silent are stated in each module.
 Modules:
   mesh      Kuhn-split cube, boundary, integer-scaled P1 assembly
-  bem       double-layer (Fredkin-Koehler) boundary matrix
+  bem       double-layer (Fredkin-Koehler) boundary matrix, whole or by sub-block
+  hmatrix   hierarchical (H-matrix) form of that matrix: cluster tree, block
+            tree, low-rank leaves (Sec. 3.1 names H-matrices for the BEM)
   micromag  energies, effective fields, magnetostatic potential
   minimise  Cayley update, step rules, minimiser, hysteresis sweep
 """

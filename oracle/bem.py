@@ -181,3 +181,32 @@ def bem_matrix_general(nodes: np.ndarray, bnd: np.ndarray, tris: np.ndarray, row
         out[s:s + chunk] = (S.T @ I.reshape(r.size, -1).T).T / (4.0 * math.pi)
     out[np.arange(rows.size), rows] += omega / (4.0 * math.pi) - 1.0
     return out
+
+
+def bem_block(nodes: np.ndarray, bnd: np.ndarray, tris: np.ndarray, rows, cols) -> np.ndarray:
+    """B[rows][:, cols] (boundary positions) without assembling the rest of B:
+    the same entries as bem_matrix_general, from the triangles around the column
+    nodes only, with the solid-angle term where a row meets its own column."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    rows, cols = np.asarray(rows), np.asarray(cols)
+    pos = -np.ones(nodes.shape[0], dtype=np.int64)
+    pos[bnd] = np.arange(bnd.size)
+    local = -np.ones(bnd.size, dtype=np.int64)
+    local[cols] = np.arange(cols.size)
+    slot = local[pos[tris]]                                  # (F, 3): block column of each vertex, or -1
+    sel = np.nonzero((slot >= 0).any(axis=1))[0]
+    ids = bnd[rows]
+    out = np.zeros((rows.size, cols.size))
+    if sel.size:
+        excl = np.any(tris[sel][None, :, :] == ids[:, None, None], axis=2)
+        I = hat_double_layer(nodes[ids], nodes[tris[sel]], exclude=excl)   # (P, S, 3)
+        for k in range(3):
+            c = slot[sel, k]
+            ok = c >= 0
+            np.add.at(out.T, c[ok], I[:, ok, k].T)
+        out /= 4.0 * math.pi
+    a, b = np.nonzero(rows[:, None] == cols[None, :])
+    if a.size:
+        omega = interior_solid_angle(nodes, bnd[rows[a]], tris)
+        out[a, b] += omega / (4.0 * math.pi) - 1.0
+    return out

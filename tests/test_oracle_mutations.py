@@ -4,8 +4,11 @@ Each test plants one mistake in the oracle (on the CPU, for the duration of the
 test) and checks that a pin written against the paper or the mathematics
 fails with it: a wrong sign in the Eq. (8) update, the adjoint chain dropped
 from the stray field, the BEM term dropped from the potential, a wrong interior
-solid angle, BB1 and BB2 swapped, a wrong cofactor, and reflex dihedral angles
-folded into [0, pi].
+solid angle, BB1 and BB2 swapped, a wrong cofactor, reflex dihedral angles
+folded into [0, pi]; and in the hierarchical-matrix boundary operator a cluster
+that loses a node, admissibility by the larger diameter or without the hat
+supports, a truncation one rank short, a wrong residual sign in the cross
+approximation, and low-rank products added into the wrong rows.
 """
 import importlib.util
 import math
@@ -125,3 +128,109 @@ def test_reflex_angles_folded(monkeypatch):
 
     monkeypatch.setattr(gpins, "interior_solid_angle", folded)
     _caught(gpins.test_non_convex_surface_solid_angles_and_bem)
+
+
+# -- hierarchical-matrix boundary operator ------------------------------------
+
+hpins = _load("test_oracle_hmatrix")
+
+
+@pytest.fixture(scope="module")
+def hm_inputs():
+    from oracle.bem import bem_matrix, bem_matrix_general
+    from oracle.mesh import cube_mesh, tet_mesh
+    from synth import ball_mesh
+    c = cube_mesh(12, 1.0)
+    xyz, tets = ball_mesh(10, 1.0)
+    t = tet_mesh(xyz, tets)
+    return (c, bem_matrix(c.nodes, 12, c.bnd, c.tris)), (t, bem_matrix_general(t.nodes, t.bnd, t.tris))
+
+
+def test_hmatrix_pins_pass_unmutated(hm_inputs):
+    hpins.test_cluster_tree_is_a_balanced_geometric_bisection(*hm_inputs, 16)
+    hpins.test_block_tree_covers_every_entry_once_and_admits_only_separated_pairs(*hm_inputs, 2.0)
+    hpins.test_hmatrix_obeys_the_frobenius_bound(*hm_inputs, "svd", 1e-4)
+    hpins.test_truncated_svd_takes_the_smallest_sufficient_rank(1e-4)
+    hpins.test_cross_approximation_recovers_exact_low_rank(5)
+
+
+def test_cluster_loses_a_node(monkeypatch, hm_inputs):
+    from oracle import hmatrix as hm
+    good = hm._cluster
+    monkeypatch.setattr(hm, "_cluster", lambda idx, pts, slo, shi: good(
+        idx if idx.size == pts.shape[0] else idx[:-1], pts, slo, shi))
+    _caught(hpins.test_cluster_tree_is_a_balanced_geometric_bisection, *hm_inputs, 16)
+    _caught(hpins.test_block_tree_covers_every_entry_once_and_admits_only_separated_pairs, *hm_inputs, 2.0)
+
+
+def test_admissibility_with_the_larger_diameter(monkeypatch, hm_inputs):
+    from oracle import hmatrix as hm
+
+    def max_rule(tau, sigma, eta):
+        d = hm.box_dist(tau.lo_r, tau.hi_r, sigma.lo_c, sigma.hi_c)
+        return d > 0.0 and max(hm.box_diam(tau.lo_r, tau.hi_r), hm.box_diam(sigma.lo_c, sigma.hi_c)) <= eta * d
+
+    monkeypatch.setattr(hm, "admissible", max_rule)
+    _caught(hpins.test_block_tree_covers_every_entry_once_and_admits_only_separated_pairs, *hm_inputs, 2.0)
+
+
+def test_admissibility_without_the_hat_supports(monkeypatch, hm_inputs):
+    from oracle import hmatrix as hm
+
+    def points_only(tau, sigma, eta):
+        d = hm.box_dist(tau.lo_r, tau.hi_r, sigma.lo_r, sigma.hi_r)
+        return d > 0.0 and min(hm.box_diam(tau.lo_r, tau.hi_r), hm.box_diam(sigma.lo_r, sigma.hi_r)) <= eta * d
+
+    monkeypatch.setattr(hm, "admissible", points_only)
+    _caught(hpins.test_block_tree_covers_every_entry_once_and_admits_only_separated_pairs, *hm_inputs, 2.0)
+
+
+def test_truncation_one_rank_short(monkeypatch, hm_inputs):
+    from oracle import hmatrix as hm
+    good = hm.truncated_svd
+
+    def short(A, eps):
+        U, V = good(A, eps)
+        k = max(U.shape[1] - 1, 0)
+        return U[:, :k], V[:k]
+
+    monkeypatch.setattr(hm, "truncated_svd", short)
+    _caught(hpins.test_truncated_svd_takes_the_smallest_sufficient_rank, 1e-4)
+    _caught(hpins.test_hmatrix_obeys_the_frobenius_bound, *hm_inputs, "svd", 1e-4)
+
+
+def test_cross_approximation_residual_sign(monkeypatch):
+    from oracle import hmatrix as hm
+
+    def wrong_sign(A, eps):
+        R = np.array(A, dtype=np.float64)
+        norm = float(np.linalg.norm(R))
+        us, vs = [], []
+        while np.linalg.norm(R) > eps * norm and len(us) < min(R.shape):
+            i, j = np.unravel_index(int(np.argmax(np.abs(R))), R.shape)
+            u, v = R[:, j].copy(), R[i, :] / R[i, j]
+            R += np.outer(u, v)
+            us.append(u)
+            vs.append(v)
+        return np.stack(us, axis=1), np.stack(vs, axis=0)
+
+    monkeypatch.setattr(hm, "cross_approximation", wrong_sign)
+    _caught(hpins.test_cross_approximation_recovers_exact_low_rank, 5)
+
+
+def test_low_rank_product_into_the_wrong_rows(monkeypatch, hm_inputs):
+    from oracle import hmatrix as hm
+
+    def matmul(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.zeros((self.nb,) + x.shape[1:])
+        for L in self.leaves:
+            if L.low_rank:
+                y[L.rows[::-1]] += L.U @ (L.V @ x[L.cols])
+            else:
+                y[L.rows] += L.D @ x[L.cols]
+        return y
+
+    monkeypatch.setattr(hm.HMatrix, "__matmul__", matmul)
+    _caught(hpins.test_hmatrix_obeys_the_frobenius_bound, *hm_inputs, "svd", 1e-4)
+    _caught(hpins.test_demag_energy_and_field_with_the_hmatrix, 1e-4)
