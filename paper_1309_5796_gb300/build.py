@@ -22,6 +22,8 @@ LIB = os.path.join(OUT, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+# host code whose comparisons must come out the same on every host: no contraction into FMAs
+FILE_FLAGS = {"hpartition.cu": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def _nvcc() -> str:
@@ -57,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, src):
-            jobs.append([nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj])
+            jobs.append([nvcc, *ARCH, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj])
 
     def run(cmd):
         if verbose:

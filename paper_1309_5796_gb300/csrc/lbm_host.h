@@ -45,6 +45,29 @@ void launch_kcsr_count_gen(int N, const int* rowptr, const Dbl4* A64, int* cnt, 
 void launch_kcsr_fill_gen(int N, const int* rowptr, const int* col, const Dbl4* A64, const int* kptr, int* kent,
                           double* k64, float* k32, cudaStream_t st);
 
+// ---- hierarchical form of the boundary matrix: host set-up (csrc/hpartition.cu) --------
+struct HCluster {
+    int begin = 0, size = 0;           // boundary positions HPartition::idx[begin, begin + size), ascending
+    int child[2] = {-1, -1};           // cluster ids; -1 for a leaf cluster
+    double lo_r[3], hi_r[3];           // bounding box of the collocation points
+    double lo_c[3], hi_c[3];           // bounding box of the supports of the hat functions
+};
+struct HLeaf {
+    int row, col;                      // cluster ids of the block (row cluster, column cluster)
+    int low_rank;                      // 1: admissible (low-rank) leaf, 0: dense leaf
+};
+struct HPartition {
+    std::vector<int> idx;              // the clusters' positions, concatenated
+    std::vector<HCluster> clusters;    // [0] is the root; breadth-first, the two children together
+    std::vector<HLeaf> leaves;         // leaves of the block tree, depth-first
+};
+// lo/hi (nb x 3): bounding box of the surface triangles around each boundary node.
+void host_support_boxes(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double* lo,
+                        double* hi);
+// Cluster tree and block-tree leaves; returns an empty string, or why the input was refused.
+std::string host_hmatrix_partition(int nb, const double* pts, const double* slo, const double* shi, double eta,
+                                   int n_min, HPartition& P);
+
 // ---- device view of one mesh --------------------------------------------------------
 struct MeshView {
     int n, N, nb, nnz, F;
