@@ -25,5 +25,7 @@ Modules:
   hmatrix   hierarchical (H-matrix) form of that matrix: cluster tree, block
             tree, low-rank leaves (Sec. 3.1 names H-matrices for the BEM)
   micromag  energies, effective fields, magnetostatic potential
+  spacetrans the open boundary by space transformation (air box and a shell
+            mapped onto the exterior; Sec. 3.1: the paper's own solver's scheme)
   minimise  Cayley update, step rules, minimiser, hysteresis sweep
 """

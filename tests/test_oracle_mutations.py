@@ -8,7 +8,9 @@ solid angle, BB1 and BB2 swapped, a wrong cofactor, reflex dihedral angles
 folded into [0, pi]; and in the hierarchical-matrix boundary operator a cluster
 that loses a node, admissibility by the larger diameter or without the hat
 supports, a truncation one rank short, a wrong residual sign in the cross
-approximation, and low-rank products added into the wrong rows.
+approximation, and low-rank products added into the wrong rows; and in the
+space-transformation boundary a shell tensor built from J instead of its
+inverse, one without the |det J| factor, and a shell left untransformed.
 """
 import importlib.util
 import math
@@ -234,3 +236,47 @@ def test_low_rank_product_into_the_wrong_rows(monkeypatch, hm_inputs):
     monkeypatch.setattr(hm.HMatrix, "__matmul__", matmul)
     _caught(hpins.test_hmatrix_obeys_the_frobenius_bound, *hm_inputs, "svd", 1e-4)
     _caught(hpins.test_demag_energy_and_field_with_the_hmatrix, 1e-4)
+
+
+# -- space-transformation open boundary ----------------------------------------
+
+spins = _load("test_oracle_spacetrans")
+
+
+def _shells(levels):
+    from oracle.spacetrans import ShellProblem
+    return {lv: ShellProblem(lv[0], spins.JS, spins.A, spins.K1, [0, 0, 1], lv[1], lv[2], cell=1.0)
+            for lv in levels}
+
+
+def test_shell_pins_pass_unmutated():
+    spins.test_tensor_is_spd_with_determinant_det_J_and_identity_outside(_shells(spins.LEVELS[1:2]))
+
+
+def test_shell_tensor_from_J_instead_of_its_inverse(monkeypatch):
+    from oracle import spacetrans as st
+
+    def forward(x, c, R1, R2):
+        J, detJ = st.shell_jacobian(x, c, R1, R2)
+        return np.abs(detJ)[:, None, None] * np.einsum("pij,pkj->pik", J, J)
+
+    monkeypatch.setattr(st, "shell_tensor", forward)
+    _caught(spins.test_tensor_is_spd_with_determinant_det_J_and_identity_outside, _shells(spins.LEVELS[1:2]))
+
+
+def test_shell_tensor_without_the_volume_factor(monkeypatch):
+    from oracle import spacetrans as st
+
+    def no_det(x, c, R1, R2):
+        J, _ = st.shell_jacobian(x, c, R1, R2)
+        Ji = np.linalg.inv(J)
+        return np.einsum("pij,pkj->pik", Ji, Ji)
+
+    monkeypatch.setattr(st, "shell_tensor", no_det)
+    _caught(spins.test_tensor_is_spd_with_determinant_det_J_and_identity_outside, _shells(spins.LEVELS[1:2]))
+
+
+def test_shell_left_untransformed(monkeypatch):
+    from oracle import spacetrans as st
+    monkeypatch.setattr(st, "shell_tensor", lambda x, c, R1, R2: np.broadcast_to(np.eye(3), (len(x), 3, 3)).copy())
+    _caught(spins.test_potential_converges_to_the_box_solution_inside_and_outside, _shells(spins.LEVELS))
