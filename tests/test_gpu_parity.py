@@ -421,31 +421,3 @@ def test_stalled_fp32_phase_hands_over_to_fp64(ctx):
     for a, b in zip(res[lbm.LBM_FP64], res[lbm.LBM_MIXED]):
         assert b["status"] == lbm.LBM_OK and b["torque"] < 1e-6
         assert abs(a["energy"][4] - b["energy"][4]) <= 1e-6 * max(abs(a["energy"][4]), scale)
-
-
-def test_mixed_final_states_converged_in_the_fp64_problem(ctx):
-    """The batched workload's mixed-precision minima, re-evaluated with plain
-    FP64 solves and the FP64 BEM matrix, meet the stop test max|m x h|/Js < 1e-6
-    of the exact problem (not only of the mixed path's own arithmetic)."""
-    from synth.inputs import batched_case
-    insts = batched_case(30, 64, seed=4)
-    axes = np.stack([i.axis for i in insts])
-    fields = np.stack([i.h_ext for i in insts])
-    mesh = ctx.mesh_cube(2e-9, 30)
-    inst = ctx.instance_create(mesh, 64, lbm.LBM_MIXED_TC)
-    inst.set_material(JS_T, A_JM, K1_JM3, axes)
-    inst.set_field(fields)
-    inst.set_m(np.stack([i.m0 for i in insts]))
-    res = inst.minimise(lbm.default_opts(lbm.LBM_MIXED_TC))
-    m = inst.get_m()
-    inst.destroy()
-    chk = ctx.instance_create(mesh, 64, lbm.LBM_FP64)
-    chk.set_material(JS_T, A_JM, K1_JM3, axes)
-    chk.set_field(fields)
-    chk.set_m(m)
-    r64, _, _ = chk.evaluate(lbm.default_opts(lbm.LBM_FP64), want_h=False, want_u=False)
-    chk.destroy()
-    ctx.mesh_destroy(mesh)
-    for a, b in zip(res, r64):
-        assert a["status"] == lbm.LBM_OK
-        assert b["torque"] < 1e-6

@@ -7,8 +7,8 @@ keeps its intermediate vectors in one fixed device array inside the library.
 Here it must give what lbm_evaluate gives (FP64 field, potentials and energy
 terms, to the 1e-10 tolerance of the other FP64 parity tests) on two calls in a
 row with different inputs, and reject meshes larger than its fixed array.
-This file is collected last so that a run stopping at the first failure has
-already run every other test.
+This file is collected near the end so that a run stopping at the first
+failure has already run the other tests.
 """
 import numpy as np
 import pytest
