@@ -43,11 +43,10 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
-import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .bem import bem_matrix, bem_matrix_general
-from .mesh import CubeMesh, TetMesh, cube_mesh, tet_mesh
+from .mesh import CubeMesh, cube_mesh, tet_mesh
 
 MU0 = 4e-7 * math.pi
 

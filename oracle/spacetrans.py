@@ -41,8 +41,6 @@ magnet.  The linear system is solved directly (sparse LU).
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -159,9 +157,3 @@ class ShellProblem(CubeProblem):
         return Evaluation(E=e_ex + e_an + e_z + e_d, terms=terms, h=h, grad=grad, torque=torque,
                           u1=u, u2=zero, uT=u)
 
-
-def dipole_potential(xp: np.ndarray, c: np.ndarray, moment: np.ndarray) -> np.ndarray:
-    """Reduced potential u (metres) of a point dipole moment (m^3, i.e. V m) at c:
-    u = moment . r / (4 pi |r|^3)."""
-    r = np.asarray(xp, dtype=np.float64) - c
-    return (r @ moment) / (4.0 * math.pi * np.linalg.norm(r, axis=-1) ** 3)
