@@ -4,7 +4,6 @@ A request gives the same result alone and in a mix of concurrent requests of
 other cube sizes (each instance's arithmetic and reduction order is independent
 of what else is in its batch), and the same result as the batch API.
 """
-import time
 
 import numpy as np
 import pytest

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle.bem import bem_matrix_general, box_interior_solid_angle, hat_double_layer, interior_solid_angle
-from oracle.mesh import assemble_fp64, cube_mesh, length_unit, surface_faces, tet_mesh
+from oracle.mesh import cube_mesh, length_unit, surface_faces, tet_mesh
 from oracle.micromag import MU0, mesh_problem
 from oracle.minimise import OK, minimise
 from synth import ball_mesh, jittered_cube
