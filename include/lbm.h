@@ -43,12 +43,15 @@ extern "C" {
 /* ---- precision modes ---------------------------------------------------------- */
 #define LBM_FP64      0  /* every vector, field and reduction in FP64 */
 #define LBM_MIXED     1  /* FP64 state m; FP32 potential solves and BEM
-                            product until max|m x h|/Js < switch_tol, then an
-                            FP64 phase (FP32 BEM matrix, FP64 solves) to tol;
+                            product (FP32 matrix) until max|m x h|/Js <
+                            switch_tol, then an FP64 phase (FP64 BEM matrix and
+                            arithmetic; FP64 solves, see cg_mixed_iter) to tol;
                             FP64 reductions (dots, energy differences, stop
                             test, CG residual norms) throughout */
-#define LBM_MIXED_TC  2  /* as LBM_MIXED, BEM product on the tensor cores
-                            (3xTF32 split, FP32 accumulation) when batch > 1 */
+#define LBM_MIXED_TC  2  /* as LBM_MIXED, with the FP32 phase's BEM products
+                            on the tensor cores (3xTF32 split, FP32
+                            accumulation) when batch > 1; the FP64 phase as in
+                            LBM_MIXED */
 #define LBM_MIXED_TF32 LBM_MIXED_TC   /* the same mode under its arithmetic's name */
 
 typedef struct lbm_ctx lbm_ctx;
@@ -80,8 +83,9 @@ typedef struct {
     int32_t demag;          /* 1: stray field on (default), 0: off */
     int32_t check_every;    /* host polls convergence every this many steps */
     double  switch_tol;     /* mixed precision: the FP32 phase runs until
-                               max|m x h|/Js < switch_tol (or its line search
-                               stalls), then an FP64 phase finishes to tol */
+                               max|m x h|/Js < switch_tol (or it stalls: its line
+                               search gives up, or see stall_iters), then an FP64
+                               phase finishes to tol */
     double  cg_tol_polish;  /* relative residual of the potential solves in the
                                FP64 phase of a mixed-precision run */
     int32_t cg_mixed_iter;  /* FP64 potential solves (LBM_FP64 runs and the FP64
