@@ -363,8 +363,13 @@ class Instance:
         """m from a device buffer (batch*N*3 doubles), e.g. a torch tensor's data_ptr()."""
         _check(lib().lbm_set_m_device(self.ctx._h, self.h, C.c_void_p(ptr)))
 
-    def get_m(self) -> np.ndarray:
-        out = np.empty((self.B, self.N, 3))
+    def get_m(self, out: np.ndarray | None = None) -> np.ndarray:
+        """m of every instance, [B, N, 3]; written into `out` when given (a C-contiguous
+        float64 array of that shape, e.g. a view of page-locked memory)."""
+        if out is None:
+            out = np.empty((self.B, self.N, 3))
+        elif out.shape != (self.B, self.N, 3) or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of shape (B, N, 3)")
         _check(lib().lbm_get_m(self.ctx._h, self.h, _dptr(out)))
         return out
 
