@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 # host code whose comparisons must come out the same on every host: no contraction into FMAs
-FILE_FLAGS = {"hpartition.cu": ["-Xcompiler", "-ffp-contract=off"]}
+FILE_FLAGS = {"hpartition.cu": ["-Xcompiler", "-ffp-contract=off"], "hbuild.cu": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def _nvcc() -> str:

@@ -1,0 +1,421 @@
+// Host construction of the hierarchical (H-matrix) form of the double-layer
+// boundary matrix B of the hybrid FEM/BEM open boundary (Sec. 3.1), on the
+// partition of csrc/hpartition.cu:
+//   * dense leaves hold the exact entries;
+//   * admissible leaves are compressed by adaptive cross approximation with
+//     partial pivoting (Bebendorf): only the pivot rows and columns are
+//     evaluated.  Start from the first row; take the column of the residual
+//     row's largest entry as pivot, append u = residual column, v = residual
+//     row / pivot, and go on from the unused row where |u| is largest, until
+//     |u| |v| <= (eps/4) |S_k|_F (S_k the current approximation, its norm
+//     updated exactly from the new terms; the factor 4 covers the gap between
+//     the last term and the whole residual).  A residual row that vanishes
+//     moves on to the next unused row.
+//   * partial pivoting can miss a part of a block that none of its pivot rows
+//     sees (on a polyhedron the coplanar pairs of a face are exact zeros), so
+//     every low-rank leaf is checked at 32 pseudo-random entries; when the
+//     sampled residual, scaled to the block, exceeds eps |S_k|_F, the leaf is
+//     assembled exactly
+//     and compressed by cross approximation with full pivoting, whose bound
+//     |A - U V|_F <= eps |A|_F then holds by construction;
+//   * a leaf whose factors would not be smaller than the block stays dense.
+// Entries: B_ij = (1/4pi) sum_{t contains j} I_t,j(x_i) + (Omega_i/4pi - 1) delta_ij,
+// I the closed-form double layer of the linear hat on a flat triangle (the same
+// formula as the device assembly in csrc/mesh.cu, written here for the host:
+//   I_k(x) = -phi_k(p) Omega_t + h grad phi_k . sum_e nu_e P_e,
+// h the height of x over the plane, p its foot, Omega_t the signed solid angle of
+// the triangle (Van Oosterom-Strackee), P_e = int_e dl/|y - x|, nu_e the outward
+// in-plane edge normal); the triangles that contain x_i give 0 (excluded by
+// index).  Omega_i, the interior solid angle at node i, comes from the incident
+// triangles by Girard's theorem (the spherical polygon the cone of the fan cuts
+// from the unit sphere: the sum of its dihedral angles minus (m - 2) pi).
+// Host code only; no kernel lives here.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lbm_host.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+void hat_double_layer_host(const double x[3], const double* y0, const double* y1, const double* y2,
+                           double I[3]) {
+    const double* y[3] = {y0, y1, y2};
+    const double e12[3] = {y1[0] - y0[0], y1[1] - y0[1], y1[2] - y0[2]};
+    const double e13[3] = {y2[0] - y0[0], y2[1] - y0[1], y2[2] - y0[2]};
+    const double cr[3] = {e12[1] * e13[2] - e12[2] * e13[1], e12[2] * e13[0] - e12[0] * e13[2],
+                          e12[0] * e13[1] - e12[1] * e13[0]};
+    double r[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) r[k][d] = y[k][d] - x[d];
+    const double hnum = r[0][0] * cr[0] + r[0][1] * cr[1] + r[0][2] * cr[2];
+    if (hnum == 0.0) {
+        I[0] = I[1] = I[2] = 0.0;
+        return;
+    }
+    const double a2 = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    const double n[3] = {cr[0] / a2, cr[1] / a2, cr[2] / a2};
+    const double h = hnum / a2;
+    double eta[3];
+    for (int k = 0; k < 3; ++k) eta[k] = std::sqrt(r[k][0] * r[k][0] + r[k][1] * r[k][1] + r[k][2] * r[k][2]);
+    const double c12[3] = {r[1][1] * r[2][2] - r[1][2] * r[2][1], r[1][2] * r[2][0] - r[1][0] * r[2][2],
+                           r[1][0] * r[2][1] - r[1][1] * r[2][0]};
+    const double num = r[0][0] * c12[0] + r[0][1] * c12[1] + r[0][2] * c12[2];
+    const double d01 = r[0][0] * r[1][0] + r[0][1] * r[1][1] + r[0][2] * r[1][2];
+    const double d12 = r[1][0] * r[2][0] + r[1][1] * r[2][1] + r[1][2] * r[2][2];
+    const double d20 = r[2][0] * r[0][0] + r[2][1] * r[0][1] + r[2][2] * r[0][2];
+    const double den = eta[0] * eta[1] * eta[2] + eta[0] * d12 + eta[1] * d20 + eta[2] * d01;
+    const double omega = 2.0 * std::atan2(num, den);
+    double es[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = (k + 1) % 3;
+        const double e[3] = {y[k1][0] - y[k][0], y[k1][1] - y[k][1], y[k1][2] - y[k][2]};
+        const double s = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        const double nu[3] = {(e[1] * n[2] - e[2] * n[1]) / s, (e[2] * n[0] - e[0] * n[2]) / s,
+                              (e[0] * n[1] - e[1] * n[0]) / s};
+        const double P = std::log((eta[k] + eta[k1] + s) / (eta[k] + eta[k1] - s));
+        for (int d = 0; d < 3; ++d) es[d] += nu[d] * P;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double* a = y[(k + 1) % 3];
+        const double* b = y[(k + 2) % 3];
+        const double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double ax[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+        const double c[3] = {ab[1] * ax[2] - ab[2] * ax[1], ab[2] * ax[0] - ab[0] * ax[2],
+                             ab[0] * ax[1] - ab[1] * ax[0]};
+        const double phi = (c[0] * n[0] + c[1] * n[1] + c[2] * n[2]) / a2;
+        const double g[3] = {(n[1] * ab[2] - n[2] * ab[1]) / a2, (n[2] * ab[0] - n[0] * ab[2]) / a2,
+                             (n[0] * ab[1] - n[1] * ab[0]) / a2};
+        I[k] = -phi * omega + h * (g[0] * es[0] + g[1] * es[1] + g[2] * es[2]);
+    }
+}
+
+uint64_t splitmix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+struct Surface {
+    const double* xyz;
+    int nb;
+    const int* bidx;
+    const int* tris;
+    std::vector<int> inc_ptr, inc_tri, inc_slot;   // boundary position -> (triangle, slot)
+    std::vector<double> omega;                     // interior solid angle per position
+    std::vector<int> mark, local;                  // scratch of the block evaluation
+    int stamp = 0;
+
+    // out[a * cols.size() + b] = B[rows[a], cols[b]]
+    void block(const int* rows, int m, const int* cols, int n, double* out) {
+        if (m <= 0 || n <= 0) return;
+        std::fill(out, out + (size_t)m * n, 0.0);
+        ++stamp;
+        for (int b = 0; b < n; ++b) local[cols[b]] = b;
+        std::vector<int> tl;
+        for (int b = 0; b < n; ++b)
+            for (int q = inc_ptr[cols[b]]; q < inc_ptr[cols[b] + 1]; ++q) {
+                const int t = inc_tri[q];
+                if (mark[t] != stamp) {
+                    mark[t] = stamp;
+                    tl.push_back(t);
+                }
+            }
+        std::sort(tl.begin(), tl.end());
+        for (int a = 0; a < m; ++a) {
+            const int id = bidx[rows[a]];
+            const double* x = xyz + 3 * (size_t)id;
+            for (int t : tl) {
+                const int* v = tris + 3 * (size_t)t;
+                if (v[0] == id || v[1] == id || v[2] == id) continue;
+                double I[3];
+                hat_double_layer_host(x, xyz + 3 * (size_t)v[0], xyz + 3 * (size_t)v[1], xyz + 3 * (size_t)v[2], I);
+                for (int k = 0; k < 3; ++k) {
+                    const int p = pos_of(v[k]);
+                    if (p >= 0 && member(p, cols, n)) out[(size_t)a * n + local[p]] += I[k];
+                }
+            }
+        }
+        const double s = 0.25 / kPi;
+        for (size_t e = 0; e < (size_t)m * n; ++e) out[e] *= s;
+        for (int a = 0; a < m; ++a) {
+            const int b = member(rows[a], cols, n) ? local[rows[a]] : -1;
+            if (b >= 0) out[(size_t)a * n + b] += omega[rows[a]] * s - 1.0;
+        }
+    }
+
+    std::vector<int> pos;                          // node id -> boundary position or -1
+    std::vector<int> in_cols;                      // position -> stamp of the current column set
+    int col_stamp = 0;
+    int pos_of(int node) const { return pos[node]; }
+    bool member(int p, const int* cols, int n) const {
+        (void)cols;
+        (void)n;
+        return in_cols[p] == col_stamp;
+    }
+    void set_cols(const int* cols, int n) {
+        ++col_stamp;
+        for (int b = 0; b < n; ++b) in_cols[cols[b]] = col_stamp;
+    }
+    void eval(const int* rows, int m, const int* cols, int n, double* out) {
+        set_cols(cols, n);
+        block(rows, m, cols, n, out);
+    }
+};
+
+std::string girard(Surface& S, int N, int F) {
+    // fan of each boundary node: (a -> b) for every triangle (i, a, b) in its outward order
+    std::vector<std::vector<std::pair<int, int>>> fan(S.nb);
+    for (int t = 0; t < F; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int i = S.tris[3 * t + k];
+            if (i < 0 || i >= N || S.pos[i] < 0) return "triangle " + std::to_string(t) + " has a vertex off the surface list";
+            fan[S.pos[i]].push_back({S.tris[3 * t + (k + 1) % 3], S.tris[3 * t + (k + 2) % 3]});
+        }
+    S.omega.assign(S.nb, 0.0);
+    for (int q = 0; q < S.nb; ++q) {
+        const auto& f = fan[q];
+        const int m = (int)f.size();
+        if (m < 3) return "surface node " + std::to_string(S.bidx[q]) + " has fewer than 3 triangles";
+        const double* x = S.xyz + 3 * (size_t)S.bidx[q];
+        double total = 0.0;
+        for (const auto& ab : f) {
+            int c = -1;
+            for (const auto& e : f)
+                if (e.first == ab.second) c = e.second;
+            if (c < 0) return "open fan at surface node " + std::to_string(S.bidx[q]);
+            const double* pa = S.xyz + 3 * (size_t)ab.first;
+            const double* pb = S.xyz + 3 * (size_t)ab.second;
+            const double* pc = S.xyz + 3 * (size_t)c;
+            double u[3] = {pb[0] - x[0], pb[1] - x[1], pb[2] - x[2]};
+            const double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            for (double& v : u) v /= un;
+            double wa[3] = {pa[0] - x[0], pa[1] - x[1], pa[2] - x[2]};
+            double wc[3] = {pc[0] - x[0], pc[1] - x[1], pc[2] - x[2]};
+            const double da = wa[0] * u[0] + wa[1] * u[1] + wa[2] * u[2];
+            const double dc = wc[0] * u[0] + wc[1] * u[1] + wc[2] * u[2];
+            for (int d = 0; d < 3; ++d) {
+                wa[d] -= da * u[d];
+                wc[d] -= dc * u[d];
+            }
+            const double cx[3] = {wa[1] * wc[2] - wa[2] * wc[1], wa[2] * wc[0] - wa[0] * wc[2],
+                                  wa[0] * wc[1] - wa[1] * wc[0]};
+            double th = std::atan2(u[0] * cx[0] + u[1] * cx[1] + u[2] * cx[2],
+                                   wa[0] * wc[0] + wa[1] * wc[1] + wa[2] * wc[2]);
+            if (th < 0.0) th += 2.0 * kPi;
+            total += th;
+        }
+        S.omega[q] = total - (m - 2) * kPi;
+    }
+    return {};
+}
+
+double dot(const double* a, const double* b, int n) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+// cross approximation with full pivoting of the m x n block A (row-major, overwritten)
+void full_pivot(double* A, int m, int n, double eps, std::vector<double>& U, std::vector<double>& V, int& k) {
+    double norm2 = 0.0;
+    for (size_t e = 0; e < (size_t)m * n; ++e) norm2 += A[e] * A[e];
+    std::vector<std::vector<double>> us, vs;
+    double r2 = norm2;
+    while (r2 > eps * eps * norm2 && (int)us.size() < std::min(m, n)) {
+        size_t best = 0;
+        for (size_t e = 1; e < (size_t)m * n; ++e)
+            if (std::fabs(A[e]) > std::fabs(A[best])) best = e;
+        const int i = (int)(best / n), j = (int)(best % n);
+        const double piv = A[best];
+        if (piv == 0.0) break;
+        std::vector<double> u(m), v(n);
+        for (int a = 0; a < m; ++a) u[a] = A[(size_t)a * n + j];
+        for (int b = 0; b < n; ++b) v[b] = A[(size_t)i * n + b] / piv;
+        r2 = 0.0;
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < n; ++b) {
+                double& x = A[(size_t)a * n + b];
+                x -= u[a] * v[b];
+                r2 += x * x;
+            }
+        us.push_back(std::move(u));
+        vs.push_back(std::move(v));
+    }
+    k = (int)us.size();
+    U.assign((size_t)m * k, 0.0);
+    V.assign((size_t)k * n, 0.0);
+    for (int l = 0; l < k; ++l) {
+        for (int a = 0; a < m; ++a) U[(size_t)a * k + l] = us[l][a];
+        for (int b = 0; b < n; ++b) V[(size_t)l * n + b] = vs[l][b];
+    }
+}
+
+}  // namespace
+
+std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
+                               int n_min, double eps, HMatrixHost& H) {
+    if (!(eps > 0.0) || !(eps < 1.0)) return "eps must lie in (0, 1)";
+    if (N <= 0 || nb <= 0 || F <= 0) return "empty surface";
+    H = HMatrixHost{};
+    Surface S;
+    S.xyz = xyz;
+    S.nb = nb;
+    S.bidx = bidx;
+    S.tris = tris;
+    S.pos.assign(N, -1);
+    for (int q = 0; q < nb; ++q) {
+        if (bidx[q] < 0 || bidx[q] >= N) return "surface node id out of range";
+        S.pos[bidx[q]] = q;
+    }
+    if (std::string why = girard(S, N, F); !why.empty()) return why;
+    S.inc_ptr.assign(nb + 1, 0);
+    for (int t = 0; t < F; ++t)
+        for (int k = 0; k < 3; ++k) ++S.inc_ptr[S.pos[tris[3 * t + k]] + 1];
+    for (int q = 0; q < nb; ++q) S.inc_ptr[q + 1] += S.inc_ptr[q];
+    S.inc_tri.resize(3 * (size_t)F);
+    S.inc_slot.resize(3 * (size_t)F);
+    {
+        std::vector<int> fill(S.inc_ptr.begin(), S.inc_ptr.end() - 1);
+        for (int t = 0; t < F; ++t)
+            for (int k = 0; k < 3; ++k) {
+                const int q = S.pos[tris[3 * t + k]];
+                S.inc_tri[fill[q]] = t;
+                S.inc_slot[fill[q]++] = k;
+            }
+    }
+    S.mark.assign(F, 0);
+    S.local.assign(nb, -1);
+    S.in_cols.assign(nb, 0);
+
+    std::vector<double> pts(3 * (size_t)nb), lo(3 * (size_t)nb), hi(3 * (size_t)nb);
+    host_support_boxes(N, xyz, nb, bidx, F, tris, lo.data(), hi.data());
+    for (int q = 0; q < nb; ++q)
+        for (int d = 0; d < 3; ++d) pts[3 * q + d] = xyz[3 * (size_t)bidx[q] + d];
+    if (std::string why = host_hmatrix_partition(nb, pts.data(), lo.data(), hi.data(), eta, n_min, H.P); !why.empty())
+        return why;
+
+    const size_t L = H.P.leaves.size();
+    H.kind.assign(L, 0);
+    H.rank.assign(L, 0);
+    H.off.assign(L, 0);
+    std::vector<double> blk, row, col;
+    for (size_t li = 0; li < L; ++li) {
+        const HLeaf& lf = H.P.leaves[li];
+        const HCluster& ct = H.P.clusters[lf.row];
+        const HCluster& cs = H.P.clusters[lf.col];
+        const int m = ct.size, n = cs.size;
+        const int* R = H.P.idx.data() + ct.begin;
+        const int* C = H.P.idx.data() + cs.begin;
+        H.off[li] = H.data.size();
+        auto store_dense = [&]() {
+            blk.resize((size_t)m * n);
+            S.eval(R, m, C, n, blk.data());
+            H.kind[li] = 0;
+            H.rank[li] = 0;
+            H.data.insert(H.data.end(), blk.begin(), blk.end());
+        };
+        if (!lf.low_rank) {
+            store_dense();
+            continue;
+        }
+        // adaptive cross approximation with partial pivoting
+        std::vector<std::vector<double>> us, vs;
+        std::vector<char> used(m, 0);
+        double norm2 = 0.0;
+        int i = 0;
+        row.resize(n);
+        col.resize(m);
+        const int kmax = std::min(m, n);
+        while ((int)us.size() < kmax) {
+            used[i] = 1;
+            S.eval(R + i, 1, C, n, row.data());
+            for (size_t l = 0; l < us.size(); ++l)
+                for (int b = 0; b < n; ++b) row[b] -= us[l][i] * vs[l][b];
+            int j = 0;
+            for (int b = 1; b < n; ++b)
+                if (std::fabs(row[b]) > std::fabs(row[j])) j = b;
+            if (row[j] == 0.0) {
+                int nxt = -1;
+                for (int a = 0; a < m; ++a)
+                    if (!used[a]) { nxt = a; break; }
+                if (nxt < 0) break;
+                i = nxt;
+                continue;
+            }
+            std::vector<double> v(n), u(m);
+            for (int b = 0; b < n; ++b) v[b] = row[b] / row[j];
+            S.eval(R, m, C + j, 1, col.data());
+            for (int a = 0; a < m; ++a) {
+                double x = col[a];
+                for (size_t l = 0; l < us.size(); ++l) x -= vs[l][j] * us[l][a];
+                u[a] = x;
+            }
+            const double uu = dot(u.data(), u.data(), m), vv = dot(v.data(), v.data(), n);
+            double cross = 0.0;
+            for (size_t l = 0; l < us.size(); ++l) cross += dot(u.data(), us[l].data(), m) * dot(vs[l].data(), v.data(), n);
+            norm2 += 2.0 * cross + uu * vv;
+            us.push_back(std::move(u));
+            vs.push_back(std::move(v));
+            if (std::sqrt(uu * vv) <= 0.25 * eps * std::sqrt(std::max(norm2, 0.0))) break;
+            int nxt = -1;
+            double best = -1.0;
+            for (int a = 0; a < m; ++a)
+                if (!used[a] && std::fabs(us.back()[a]) > best) { best = std::fabs(us.back()[a]); nxt = a; }
+            if (nxt < 0) break;
+            i = nxt;
+        }
+        int k = (int)us.size();
+        // sampled check of the residual
+        double res2 = 0.0;
+        const int samples = 32;
+        for (int s = 0; s < samples; ++s) {
+            const uint64_t hsh = splitmix64(((uint64_t)li << 8) + (uint64_t)s);
+            const int a = (int)(hsh % (uint64_t)m), b = (int)((hsh >> 32) % (uint64_t)n);
+            double exact;
+            S.eval(R + a, 1, C + b, 1, &exact);
+            double approx = 0.0;
+            for (int l = 0; l < k; ++l) approx += us[l][a] * vs[l][b];
+            res2 += (exact - approx) * (exact - approx);
+        }
+        const double est = res2 * ((double)m * n / samples);
+        std::vector<double> Uf, Vf;
+        if (est > eps * eps * std::max(norm2, 0.0) || (k == 0 && res2 > 0.0)) {
+            blk.resize((size_t)m * n);
+            S.eval(R, m, C, n, blk.data());
+            std::vector<double> keep(blk);
+            full_pivot(blk.data(), m, n, eps, Uf, Vf, k);
+            ++H.fallbacks;
+            if ((size_t)k * (m + n) >= (size_t)m * n) {
+                H.kind[li] = 0;
+                H.data.insert(H.data.end(), keep.begin(), keep.end());
+                continue;
+            }
+        } else {
+            if ((size_t)k * (m + n) >= (size_t)m * n) {
+                store_dense();
+                continue;
+            }
+            Uf.assign((size_t)m * k, 0.0);
+            Vf.assign((size_t)k * n, 0.0);
+            for (int l = 0; l < k; ++l) {
+                for (int a = 0; a < m; ++a) Uf[(size_t)a * k + l] = us[l][a];
+                for (int b = 0; b < n; ++b) Vf[(size_t)l * n + b] = vs[l][b];
+            }
+        }
+        H.kind[li] = 1;
+        H.rank[li] = k;
+        H.data.insert(H.data.end(), Uf.begin(), Uf.end());
+        H.data.insert(H.data.end(), Vf.begin(), Vf.end());
+    }
+    return {};
+}
+
+}  // namespace lbm

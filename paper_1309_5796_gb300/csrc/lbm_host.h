@@ -68,6 +68,22 @@ void host_support_boxes(int N, const double* xyz, int nb, const int* bidx, int F
 std::string host_hmatrix_partition(int nb, const double* pts, const double* slo, const double* shi, double eta,
                                    int n_min, HPartition& P);
 
+// The leaves filled in (csrc/hbuild.cu): dense leaves hold their m x n entries
+// (row-major); low-rank leaves U (m x k, row-major) followed by V (k x n, row-major).
+struct HMatrixHost {
+    HPartition P;
+    std::vector<int> kind;             // per leaf: 0 dense, 1 low rank
+    std::vector<int> rank;             // per leaf: k of a low-rank leaf, 0 otherwise
+    std::vector<size_t> off;           // per leaf: offset of its values in data
+    std::vector<double> data;
+    int fallbacks = 0;                 // low-rank leaves assembled exactly after the sampled check
+};
+// B_H of the surface (xyz: node coordinates, any length unit; bidx: surface nodes,
+// ascending; tris: outward surface triangles) for tolerance eps; an empty string, or
+// why the input was refused.
+std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
+                               int n_min, double eps, HMatrixHost& H);
+
 // ---- device view of one mesh --------------------------------------------------------
 struct MeshView {
     int n, N, nb, nnz, F;
