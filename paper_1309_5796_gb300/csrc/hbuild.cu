@@ -18,6 +18,10 @@
 //     assembled exactly
 //     and compressed by cross approximation with full pivoting, whose bound
 //     |A - U V|_F <= eps |A|_F then holds by construction;
+//   * the factors of a low-rank leaf are then recompressed to the fewest terms
+//     the tolerance needs: U = Qu Ru, V^T = Qv Rv (Gram-Schmidt), the SVD of the
+//     k x k core Ru Rv^T by one-sided Jacobi rotations (Hestenes), truncated
+//     where the discarded singular values reach eps/2 of the leaf's norm;
 //   * a leaf whose factors would not be smaller than the block stays dense.
 // Entries: B_ij = (1/4pi) sum_{t contains j} I_t,j(x_i) + (Omega_i/4pi - 1) delta_ij,
 // I the closed-form double layer of the linear hat on a flat triangle (the same
@@ -258,6 +262,122 @@ void full_pivot(double* A, int m, int n, double eps, std::vector<double>& U, std
     }
 }
 
+// A = Q R for A (m x k, row-major): Q orthonormal columns (a column that
+// vanishes stays zero), R (k x k) upper triangular; classical Gram-Schmidt
+// applied twice to every column.
+void thin_qr(const std::vector<double>& A, int m, int k, std::vector<double>& Q, std::vector<double>& R) {
+    Q = A;
+    R.assign((size_t)k * k, 0.0);
+    for (int c = 0; c < k; ++c) {
+        for (int pass = 0; pass < 2; ++pass)
+            for (int p = 0; p < c; ++p) {
+                double d = 0.0;
+                for (int a = 0; a < m; ++a) d += Q[(size_t)a * k + p] * Q[(size_t)a * k + c];
+                R[(size_t)p * k + c] += d;
+                for (int a = 0; a < m; ++a) Q[(size_t)a * k + c] -= d * Q[(size_t)a * k + p];
+            }
+        double nrm = 0.0;
+        for (int a = 0; a < m; ++a) nrm += Q[(size_t)a * k + c] * Q[(size_t)a * k + c];
+        nrm = std::sqrt(nrm);
+        R[(size_t)c * k + c] = nrm;
+        for (int a = 0; a < m; ++a) Q[(size_t)a * k + c] = nrm > 0.0 ? Q[(size_t)a * k + c] / nrm : 0.0;
+    }
+}
+
+// One-sided Jacobi (Hestenes) on C (k x k, row-major): rotations of column
+// pairs until all columns are orthogonal, C Z = W with Z orthogonal; the
+// singular values are the column norms of W, in any order.
+void jacobi_svd(std::vector<double>& W, std::vector<double>& Z, int k) {
+    Z.assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i) Z[(size_t)i * k + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < k; ++i) {
+                    const double wp = W[(size_t)i * k + p], wq = W[(size_t)i * k + q];
+                    al += wp * wp;
+                    be += wq * wq;
+                    ga += wp * wq;
+                }
+                if (ga == 0.0 || std::fabs(ga) <= 1e-15 * std::sqrt(al * be)) continue;
+                off = std::max(off, std::fabs(ga) / std::sqrt(al * be));
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                for (int i = 0; i < k; ++i) {
+                    double& wp = W[(size_t)i * k + p];
+                    double& wq = W[(size_t)i * k + q];
+                    const double a = wp, b = wq;
+                    wp = c * a - s * b;
+                    wq = s * a + c * b;
+                    double& zp = Z[(size_t)i * k + p];
+                    double& zq = Z[(size_t)i * k + q];
+                    const double za = zp, zb = zq;
+                    zp = c * za - s * zb;
+                    zq = s * za + c * zb;
+                }
+            }
+        if (off <= 1e-15) break;
+    }
+}
+
+// U V (U m x k, V k x n, row-major) recompressed to the fewest singular triplets
+// whose discarded tail is at most tol |U V|_F; k updated.
+void recompress(std::vector<double>& U, std::vector<double>& V, int m, int n, int& k, double tol) {
+    if (k <= 1) return;
+    std::vector<double> Vt((size_t)n * k);
+    for (int l = 0; l < k; ++l)
+        for (int b = 0; b < n; ++b) Vt[(size_t)b * k + l] = V[(size_t)l * n + b];
+    std::vector<double> Qu, Ru, Qv, Rv;
+    thin_qr(U, m, k, Qu, Ru);
+    thin_qr(Vt, n, k, Qv, Rv);
+    std::vector<double> C((size_t)k * k, 0.0);         // Ru Rv^T
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double x = 0.0;
+            for (int l = 0; l < k; ++l) x += Ru[(size_t)i * k + l] * Rv[(size_t)j * k + l];
+            C[(size_t)i * k + j] = x;
+        }
+    std::vector<double> Z;
+    jacobi_svd(C, Z, k);                                  // C now holds W = C_in Z
+    std::vector<double> sig(k);
+    for (int j = 0; j < k; ++j) {
+        double x = 0.0;
+        for (int i = 0; i < k; ++i) x += C[(size_t)i * k + j] * C[(size_t)i * k + j];
+        sig[j] = std::sqrt(x);
+    }
+    std::vector<int> ord(k);
+    for (int j = 0; j < k; ++j) ord[j] = j;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sig[a] > sig[b]; });
+    double total = 0.0;
+    for (double v : sig) total += v * v;
+    int keep = k;
+    double tail = 0.0;
+    while (keep > 0 && tail + sig[ord[keep - 1]] * sig[ord[keep - 1]] <= tol * tol * total) {
+        tail += sig[ord[keep - 1]] * sig[ord[keep - 1]];
+        --keep;
+    }
+    // U' = Qu W[:, kept] (m x keep), V' = (Qv Z[:, kept])^T (keep x n)
+    std::vector<double> U2((size_t)m * keep, 0.0), V2((size_t)keep * n, 0.0);
+    for (int a = 0; a < m; ++a)
+        for (int c = 0; c < keep; ++c) {
+            double x = 0.0;
+            for (int l = 0; l < k; ++l) x += Qu[(size_t)a * k + l] * C[(size_t)l * k + ord[c]];
+            U2[(size_t)a * keep + c] = x;
+        }
+    for (int c = 0; c < keep; ++c)
+        for (int b = 0; b < n; ++b) {
+            double x = 0.0;
+            for (int l = 0; l < k; ++l) x += Qv[(size_t)b * k + l] * Z[(size_t)l * k + ord[c]];
+            V2[(size_t)c * n + b] = x;
+        }
+    U.swap(U2);
+    V.swap(V2);
+    k = keep;
+}
+
 }  // namespace
 
 std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
@@ -386,29 +506,30 @@ std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx
             res2 += (exact - approx) * (exact - approx);
         }
         const double est = res2 * ((double)m * n / samples);
-        std::vector<double> Uf, Vf;
+        std::vector<double> Uf, Vf, exact;
         if (est > eps * eps * std::max(norm2, 0.0) || (k == 0 && res2 > 0.0)) {
-            blk.resize((size_t)m * n);
-            S.eval(R, m, C, n, blk.data());
-            std::vector<double> keep(blk);
+            exact.resize((size_t)m * n);
+            S.eval(R, m, C, n, exact.data());
+            blk = exact;
             full_pivot(blk.data(), m, n, eps, Uf, Vf, k);
             ++H.fallbacks;
-            if ((size_t)k * (m + n) >= (size_t)m * n) {
-                H.kind[li] = 0;
-                H.data.insert(H.data.end(), keep.begin(), keep.end());
-                continue;
-            }
         } else {
-            if ((size_t)k * (m + n) >= (size_t)m * n) {
-                store_dense();
-                continue;
-            }
             Uf.assign((size_t)m * k, 0.0);
             Vf.assign((size_t)k * n, 0.0);
             for (int l = 0; l < k; ++l) {
                 for (int a = 0; a < m; ++a) Uf[(size_t)a * k + l] = us[l][a];
                 for (int b = 0; b < n; ++b) Vf[(size_t)l * n + b] = vs[l][b];
             }
+        }
+        recompress(Uf, Vf, m, n, k, 0.5 * eps);
+        if ((size_t)k * (m + n) >= (size_t)m * n) {          // not smaller than the block: dense
+            if (exact.empty()) {
+                store_dense();
+            } else {
+                H.kind[li] = 0;
+                H.data.insert(H.data.end(), exact.begin(), exact.end());
+            }
+            continue;
         }
         H.kind[li] = 1;
         H.rank[li] = k;

@@ -1,10 +1,11 @@
 """The library's host construction of the hierarchical boundary matrix
 (csrc/hbuild.cu: exact dense leaves, adaptive cross approximation with partial
 pivoting on the admissible leaves, a sampled residual check with an exact
-fallback) against the oracle's dense double-layer matrix, run through a C++
-driver on the CPU: the partition is the oracle's, dense leaves equal the dense
-matrix's entries, every low-rank leaf meets its tolerance, and the whole
-operator ||B - B_H||_F <= eps ||B||_F."""
+fallback, recompression of the factors) against the oracle's dense double-layer
+matrix, run through a C++ driver on the CPU: the partition is the oracle's,
+dense leaves equal the dense matrix's entries, every low-rank leaf meets its
+tolerance, the whole operator ||B - B_H||_F <= eps ||B||_F, and the storage is
+within 15 % of the optimal ranks (the oracle's truncated SVD of every leaf)."""
 import os
 import shutil
 import struct
@@ -111,6 +112,10 @@ def test_native_hmatrix_meets_the_bound_on_the_dense_matrix(driver, eps):
                 assert np.abs(A - approx).max() <= 1e-13 * scale, name
             D[np.ix_(rows, cols)] += approx
         assert np.linalg.norm(D - B) <= eps * np.linalg.norm(B), (name, np.linalg.norm(D - B) / np.linalg.norm(B))
+        # after recompression the storage is close to the optimal ranks (truncated SVD of every leaf)
+        stored = sum(X.size + (Y.size if Y is not None else 0) for (_, _, _, X, Y) in leaves)
+        best = hm.build_hmatrix(hm.dense_blocks(B), xyz, bnd, tris, eps=eps, eta=eta, n_min=n_min).stored()
+        assert stored <= 1.15 * best, (name, stored / best)
     assert n_low > 0
 
 
