@@ -320,7 +320,7 @@ typedef struct {
 typedef struct {
     int32_t slots;           /* batch width of each group (default 16) */
     int32_t chunk;           /* iterations issued per group between polls (default 8) */
-    int32_t max_pcg_blocks;  /* cooperative grid cap per group (default SMs/4) */
+    int32_t max_pcg_blocks;  /* cooperative grid cap per group (default 0: a quarter of the SMs) */
     double  mem_reserve;     /* fraction of device memory kept free (default 0.05) */
     lbm_solve_opts opt;      /* solve options of every request */
 } lbm_serve_opts;

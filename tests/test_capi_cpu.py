@@ -150,3 +150,33 @@ def test_binding_argument_counts_match_the_header():
     assert len(protos) == len(lbm.SIGNATURES)
     for name, _, args in lbm.SIGNATURES:
         assert protos[name] == len(args), (name, protos[name], len(args))
+
+
+def test_default_options_are_the_documented_ones(library):
+    """lbm_default_opts and lbm_default_serve_opts fill in what include/lbm.h
+    documents (no GPU needed)."""
+    import ctypes as C
+    common = dict(tol=1e-6, grad_tol=0.0, memory=20, c1=1e-4, max_backtracks=30, kappa0=0.5, m_alpha=3,
+                  switch_tol=1e-4, cg_tol_polish=1e-10, bb_rule=0, method=0, omega=1.0, demag=1)
+    per = {lbm.LBM_FP64: dict(cg_tol=1e-13, cg_mixed_iter=0, stall_iters=0),
+           lbm.LBM_MIXED: dict(cg_tol=1e-6, cg_mixed_iter=1, stall_iters=200),
+           lbm.LBM_MIXED_TC: dict(cg_tol=1e-6, cg_mixed_iter=1, stall_iters=200)}
+    for prec, extra in per.items():
+        o = lbm.default_opts(prec)
+        for k, v in {**common, **extra}.items():
+            assert getattr(o, k) == v, (prec, k, getattr(o, k))
+    assert lbm.LBM_MIXED_TF32 == lbm.LBM_MIXED_TC
+    s = lbm.ServeOpts()
+    library.lbm_default_serve_opts(C.byref(s))
+    assert (s.slots, s.chunk, s.max_pcg_blocks, s.mem_reserve) == (16, 8, 0, 0.05)
+    assert s.opt.cg_mixed_iter == 1 and s.opt.stall_iters == 200
+
+
+def test_failed_call_leaves_its_message(library):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Context(0)
+    msg = library.lbm_last_error().decode()
+    assert msg and msg in str(e.value)
