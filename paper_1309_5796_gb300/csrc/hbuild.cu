@@ -33,11 +33,15 @@
 // index).  Omega_i, the interior solid angle at node i, comes from the incident
 // triangles by Girard's theorem (the spherical polygon the cone of the fan cuts
 // from the unit sphere: the sum of its dihedral angles minus (m - 2) pi).
-// Host code only; no kernel lives here.
+// Leaves are independent: they are filled by `threads` host threads, each with
+// its own scratch, and concatenated in leaf order, so the result does not depend
+// on the thread count.  Host code only; no kernel lives here.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lbm_host.h"
@@ -378,10 +382,126 @@ void recompress(std::vector<double>& U, std::vector<double>& V, int m, int n, in
     k = keep;
 }
 
+struct LeafOut {
+    int kind = 0, rank = 0, fallback = 0;
+    std::vector<double> values;                   // dense m*n, or U (m*k) then V (k*n)
+};
+
+// One leaf of the block tree: exact entries (dense), or cross approximation,
+// sampled check, fallback and recompression (low rank).
+void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& out) {
+    const HLeaf& lf = P.leaves[li];
+    const HCluster& ct = P.clusters[lf.row];
+    const HCluster& cs = P.clusters[lf.col];
+    const int m = ct.size, n = cs.size;
+    const int* R = P.idx.data() + ct.begin;
+    const int* C = P.idx.data() + cs.begin;
+    auto store_dense = [&]() {
+        out.kind = 0;
+        out.rank = 0;
+        out.values.resize((size_t)m * n);
+        S.eval(R, m, C, n, out.values.data());
+    };
+    if (!lf.low_rank) {
+        store_dense();
+        return;
+    }
+    // adaptive cross approximation with partial pivoting
+    std::vector<std::vector<double>> us, vs;
+    std::vector<char> used(m, 0);
+    std::vector<double> row(n), col(m);
+    double norm2 = 0.0;
+    int i = 0;
+    const int kmax = std::min(m, n);
+    while ((int)us.size() < kmax) {
+        used[i] = 1;
+        S.eval(R + i, 1, C, n, row.data());
+        for (size_t l = 0; l < us.size(); ++l)
+            for (int b = 0; b < n; ++b) row[b] -= us[l][i] * vs[l][b];
+        int j = 0;
+        for (int b = 1; b < n; ++b)
+            if (std::fabs(row[b]) > std::fabs(row[j])) j = b;
+        if (row[j] == 0.0) {
+            int nxt = -1;
+            for (int a = 0; a < m; ++a)
+                if (!used[a]) { nxt = a; break; }
+            if (nxt < 0) break;
+            i = nxt;
+            continue;
+        }
+        std::vector<double> v(n), u(m);
+        for (int b = 0; b < n; ++b) v[b] = row[b] / row[j];
+        S.eval(R, m, C + j, 1, col.data());
+        for (int a = 0; a < m; ++a) {
+            double x = col[a];
+            for (size_t l = 0; l < us.size(); ++l) x -= vs[l][j] * us[l][a];
+            u[a] = x;
+        }
+        const double uu = dot(u.data(), u.data(), m), vv = dot(v.data(), v.data(), n);
+        double cross = 0.0;
+        for (size_t l = 0; l < us.size(); ++l) cross += dot(u.data(), us[l].data(), m) * dot(vs[l].data(), v.data(), n);
+        norm2 += 2.0 * cross + uu * vv;
+        us.push_back(std::move(u));
+        vs.push_back(std::move(v));
+        if (std::sqrt(uu * vv) <= 0.25 * eps * std::sqrt(std::max(norm2, 0.0))) break;
+        int nxt = -1;
+        double best = -1.0;
+        for (int a = 0; a < m; ++a)
+            if (!used[a] && std::fabs(us.back()[a]) > best) { best = std::fabs(us.back()[a]); nxt = a; }
+        if (nxt < 0) break;
+        i = nxt;
+    }
+    int k = (int)us.size();
+    // sampled check of the residual
+    double res2 = 0.0;
+    const int samples = 32;
+    for (int s = 0; s < samples; ++s) {
+        const uint64_t hsh = splitmix64(((uint64_t)li << 8) + (uint64_t)s);
+        const int a = (int)(hsh % (uint64_t)m), b = (int)((hsh >> 32) % (uint64_t)n);
+        double exact;
+        S.eval(R + a, 1, C + b, 1, &exact);
+        double approx = 0.0;
+        for (int l = 0; l < k; ++l) approx += us[l][a] * vs[l][b];
+        res2 += (exact - approx) * (exact - approx);
+    }
+    const double est = res2 * ((double)m * n / samples);
+    std::vector<double> Uf, Vf, exact;
+    if (est > eps * eps * std::max(norm2, 0.0) || (k == 0 && res2 > 0.0)) {
+        exact.resize((size_t)m * n);
+        S.eval(R, m, C, n, exact.data());
+        std::vector<double> blk(exact);
+        full_pivot(blk.data(), m, n, eps, Uf, Vf, k);
+        out.fallback = 1;
+    } else {
+        Uf.assign((size_t)m * k, 0.0);
+        Vf.assign((size_t)k * n, 0.0);
+        for (int l = 0; l < k; ++l) {
+            for (int a = 0; a < m; ++a) Uf[(size_t)a * k + l] = us[l][a];
+            for (int b = 0; b < n; ++b) Vf[(size_t)l * n + b] = vs[l][b];
+        }
+    }
+    recompress(Uf, Vf, m, n, k, 0.5 * eps);
+    if ((size_t)k * (m + n) >= (size_t)m * n) {          // not smaller than the block: dense
+        if (exact.empty()) {
+            store_dense();
+        } else {
+            out.kind = 0;
+            out.rank = 0;
+            out.values.swap(exact);
+        }
+        return;
+    }
+    out.kind = 1;
+    out.rank = k;
+    out.values.reserve(Uf.size() + Vf.size());
+    out.values.insert(out.values.end(), Uf.begin(), Uf.end());
+    out.values.insert(out.values.end(), Vf.begin(), Vf.end());
+}
+
 }  // namespace
 
 std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
-                               int n_min, double eps, HMatrixHost& H) {
+                               int n_min, double eps, int threads, HMatrixHost& H) {
     if (!(eps > 0.0) || !(eps < 1.0)) return "eps must lie in (0, 1)";
     if (N <= 0 || nb <= 0 || F <= 0) return "empty surface";
     H = HMatrixHost{};
@@ -423,118 +543,31 @@ std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx
         return why;
 
     const size_t L = H.P.leaves.size();
+    std::vector<LeafOut> outs(L);
+    const int nth = std::max(1, std::min(threads, (int)std::min<size_t>(L, 256)));
+    std::atomic<size_t> next{0};
+    auto work = [&](Surface Sw) {                         // each thread its own scratch
+        for (size_t li = next++; li < L; li = next++) fill_leaf(Sw, H.P, li, eps, outs[li]);
+    };
+    if (nth == 1) {
+        work(S);
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nth; ++t) pool.emplace_back(work, S);
+        for (auto& th : pool) th.join();
+    }
     H.kind.assign(L, 0);
     H.rank.assign(L, 0);
     H.off.assign(L, 0);
-    std::vector<double> blk, row, col;
+    size_t total = 0;
+    for (const LeafOut& o : outs) total += o.values.size();
+    H.data.reserve(total);
     for (size_t li = 0; li < L; ++li) {
-        const HLeaf& lf = H.P.leaves[li];
-        const HCluster& ct = H.P.clusters[lf.row];
-        const HCluster& cs = H.P.clusters[lf.col];
-        const int m = ct.size, n = cs.size;
-        const int* R = H.P.idx.data() + ct.begin;
-        const int* C = H.P.idx.data() + cs.begin;
+        H.kind[li] = outs[li].kind;
+        H.rank[li] = outs[li].rank;
         H.off[li] = H.data.size();
-        auto store_dense = [&]() {
-            blk.resize((size_t)m * n);
-            S.eval(R, m, C, n, blk.data());
-            H.kind[li] = 0;
-            H.rank[li] = 0;
-            H.data.insert(H.data.end(), blk.begin(), blk.end());
-        };
-        if (!lf.low_rank) {
-            store_dense();
-            continue;
-        }
-        // adaptive cross approximation with partial pivoting
-        std::vector<std::vector<double>> us, vs;
-        std::vector<char> used(m, 0);
-        double norm2 = 0.0;
-        int i = 0;
-        row.resize(n);
-        col.resize(m);
-        const int kmax = std::min(m, n);
-        while ((int)us.size() < kmax) {
-            used[i] = 1;
-            S.eval(R + i, 1, C, n, row.data());
-            for (size_t l = 0; l < us.size(); ++l)
-                for (int b = 0; b < n; ++b) row[b] -= us[l][i] * vs[l][b];
-            int j = 0;
-            for (int b = 1; b < n; ++b)
-                if (std::fabs(row[b]) > std::fabs(row[j])) j = b;
-            if (row[j] == 0.0) {
-                int nxt = -1;
-                for (int a = 0; a < m; ++a)
-                    if (!used[a]) { nxt = a; break; }
-                if (nxt < 0) break;
-                i = nxt;
-                continue;
-            }
-            std::vector<double> v(n), u(m);
-            for (int b = 0; b < n; ++b) v[b] = row[b] / row[j];
-            S.eval(R, m, C + j, 1, col.data());
-            for (int a = 0; a < m; ++a) {
-                double x = col[a];
-                for (size_t l = 0; l < us.size(); ++l) x -= vs[l][j] * us[l][a];
-                u[a] = x;
-            }
-            const double uu = dot(u.data(), u.data(), m), vv = dot(v.data(), v.data(), n);
-            double cross = 0.0;
-            for (size_t l = 0; l < us.size(); ++l) cross += dot(u.data(), us[l].data(), m) * dot(vs[l].data(), v.data(), n);
-            norm2 += 2.0 * cross + uu * vv;
-            us.push_back(std::move(u));
-            vs.push_back(std::move(v));
-            if (std::sqrt(uu * vv) <= 0.25 * eps * std::sqrt(std::max(norm2, 0.0))) break;
-            int nxt = -1;
-            double best = -1.0;
-            for (int a = 0; a < m; ++a)
-                if (!used[a] && std::fabs(us.back()[a]) > best) { best = std::fabs(us.back()[a]); nxt = a; }
-            if (nxt < 0) break;
-            i = nxt;
-        }
-        int k = (int)us.size();
-        // sampled check of the residual
-        double res2 = 0.0;
-        const int samples = 32;
-        for (int s = 0; s < samples; ++s) {
-            const uint64_t hsh = splitmix64(((uint64_t)li << 8) + (uint64_t)s);
-            const int a = (int)(hsh % (uint64_t)m), b = (int)((hsh >> 32) % (uint64_t)n);
-            double exact;
-            S.eval(R + a, 1, C + b, 1, &exact);
-            double approx = 0.0;
-            for (int l = 0; l < k; ++l) approx += us[l][a] * vs[l][b];
-            res2 += (exact - approx) * (exact - approx);
-        }
-        const double est = res2 * ((double)m * n / samples);
-        std::vector<double> Uf, Vf, exact;
-        if (est > eps * eps * std::max(norm2, 0.0) || (k == 0 && res2 > 0.0)) {
-            exact.resize((size_t)m * n);
-            S.eval(R, m, C, n, exact.data());
-            blk = exact;
-            full_pivot(blk.data(), m, n, eps, Uf, Vf, k);
-            ++H.fallbacks;
-        } else {
-            Uf.assign((size_t)m * k, 0.0);
-            Vf.assign((size_t)k * n, 0.0);
-            for (int l = 0; l < k; ++l) {
-                for (int a = 0; a < m; ++a) Uf[(size_t)a * k + l] = us[l][a];
-                for (int b = 0; b < n; ++b) Vf[(size_t)l * n + b] = vs[l][b];
-            }
-        }
-        recompress(Uf, Vf, m, n, k, 0.5 * eps);
-        if ((size_t)k * (m + n) >= (size_t)m * n) {          // not smaller than the block: dense
-            if (exact.empty()) {
-                store_dense();
-            } else {
-                H.kind[li] = 0;
-                H.data.insert(H.data.end(), exact.begin(), exact.end());
-            }
-            continue;
-        }
-        H.kind[li] = 1;
-        H.rank[li] = k;
-        H.data.insert(H.data.end(), Uf.begin(), Uf.end());
-        H.data.insert(H.data.end(), Vf.begin(), Vf.end());
+        H.data.insert(H.data.end(), outs[li].values.begin(), outs[li].values.end());
+        H.fallbacks += outs[li].fallback;
     }
     return {};
 }

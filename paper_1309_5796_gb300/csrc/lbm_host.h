@@ -79,10 +79,11 @@ struct HMatrixHost {
     int fallbacks = 0;                 // low-rank leaves assembled exactly after the sampled check
 };
 // B_H of the surface (xyz: node coordinates, any length unit; bidx: surface nodes,
-// ascending; tris: outward surface triangles) for tolerance eps; an empty string, or
+// ascending; tris: outward surface triangles) for tolerance eps, filled by `threads`
+// host threads (the result does not depend on their number); an empty string, or
 // why the input was refused.
 std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
-                               int n_min, double eps, HMatrixHost& H);
+                               int n_min, double eps, int threads, HMatrixHost& H);
 
 // ---- device view of one mesh --------------------------------------------------------
 struct MeshView {

@@ -1,6 +1,6 @@
 // Runs the library's host construction of the hierarchical boundary matrix on a
 // surface read from a binary file and writes the leaves and their values.
-//   input : int32 N, nb, F, n_min; double eta, eps; double xyz[N*3]; int32 bidx[nb]; int32 tris[F*3]
+//   input : int32 N, nb, F, n_min, threads; double eta, eps; double xyz[N*3]; int32 bidx[nb]; int32 tris[F*3]
 //   output: "error <message>\n", or "ok" then int32 n_leaves, fallbacks and, per leaf
 //           (depth-first): int32 m, n, kind, rank, the m row and n column positions,
 //           then the leaf's values (m*n dense, or m*k + k*n factors) as doubles
@@ -16,10 +16,10 @@ int main(int argc, char** argv) {
     if (argc != 3) return 2;
     FILE* in = fopen(argv[1], "rb");
     if (!in) return 3;
-    int32_t hdr[4];
+    int32_t hdr[5];
     double par[2];
-    if (fread(hdr, 4, 4, in) != 4 || fread(par, 8, 2, in) != 2) return 4;
-    const int N = hdr[0], nb = hdr[1], F = hdr[2], n_min = hdr[3];
+    if (fread(hdr, 4, 5, in) != 5 || fread(par, 8, 2, in) != 2) return 4;
+    const int N = hdr[0], nb = hdr[1], F = hdr[2], n_min = hdr[3], threads = hdr[4];
     std::vector<double> xyz(3 * (size_t)N);
     std::vector<int32_t> bidx((size_t)nb), tris(3 * (size_t)F);
     if (fread(xyz.data(), 8, xyz.size(), in) != xyz.size()) return 5;
@@ -28,7 +28,7 @@ int main(int argc, char** argv) {
     fclose(in);
     lbm::HMatrixHost H;
     const std::string why =
-        lbm::host_hmatrix_build(N, xyz.data(), nb, bidx.data(), F, tris.data(), par[0], n_min, par[1], H);
+        lbm::host_hmatrix_build(N, xyz.data(), nb, bidx.data(), F, tris.data(), par[0], n_min, par[1], threads, H);
     FILE* out = fopen(argv[2], "wb");
     if (!out) return 8;
     if (!why.empty()) {

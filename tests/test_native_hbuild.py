@@ -41,11 +41,11 @@ def driver():
     shutil.rmtree(tmp, ignore_errors=True)
 
 
-def _run(exe, xyz, bnd, tris, eta, n_min, eps):
+def _run(exe, xyz, bnd, tris, eta, n_min, eps, threads=4):
     with tempfile.TemporaryDirectory() as tmp:
         fin, fout = os.path.join(tmp, "in.bin"), os.path.join(tmp, "out.bin")
         with open(fin, "wb") as f:
-            f.write(struct.pack("iiii", xyz.shape[0], bnd.size, tris.shape[0], n_min))
+            f.write(struct.pack("iiiii", xyz.shape[0], bnd.size, tris.shape[0], n_min, threads))
             f.write(struct.pack("dd", eta, eps))
             f.write(np.ascontiguousarray(xyz, np.float64).tobytes())
             f.write(np.ascontiguousarray(bnd, np.int32).tobytes())
@@ -117,6 +117,17 @@ def test_native_hmatrix_meets_the_bound_on_the_dense_matrix(driver, eps):
         best = hm.build_hmatrix(hm.dense_blocks(B), xyz, bnd, tris, eps=eps, eta=eta, n_min=n_min).stored()
         assert stored <= 1.15 * best, (name, stored / best)
     assert n_low > 0
+
+
+def test_native_hmatrix_is_independent_of_the_thread_count(driver):
+    c = cube_mesh(10, 1.0)
+    lat = c.nodes.astype(np.float64)
+    one, fb1 = _run(driver, lat, c.bnd, c.tris, 2.0, 16, 1e-6, threads=1)
+    many, fb7 = _run(driver, lat, c.bnd, c.tris, 2.0, 16, 1e-6, threads=7)
+    assert fb1 == fb7 and len(one) == len(many)
+    for a, b in zip(one, many):
+        assert a[2] == b[2] and np.array_equal(a[3], b[3])
+        assert (a[4] is None and b[4] is None) or np.array_equal(a[4], b[4])
 
 
 def test_native_hmatrix_rejects_bad_input(driver):
