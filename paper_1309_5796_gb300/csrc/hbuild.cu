@@ -231,13 +231,16 @@ double dot(const double* a, const double* b, int n) {
     return s;
 }
 
-// cross approximation with full pivoting of the m x n block A (row-major, overwritten)
-void full_pivot(double* A, int m, int n, double eps, std::vector<double>& U, std::vector<double>& V, int& k) {
+// cross approximation with full pivoting of the m x n block A (row-major,
+// overwritten); it stops early, one term past the size at which the factors
+// stop being smaller than the block.  Returns whether the tolerance was met.
+bool full_pivot(double* A, int m, int n, double eps, std::vector<double>& U, std::vector<double>& V, int& k) {
     double norm2 = 0.0;
     for (size_t e = 0; e < (size_t)m * n; ++e) norm2 += A[e] * A[e];
     std::vector<std::vector<double>> us, vs;
     double r2 = norm2;
-    while (r2 > eps * eps * norm2 && (int)us.size() < std::min(m, n)) {
+    const int kcap = std::min(std::min(m, n), (int)(((size_t)m * n - 1) / (size_t)(m + n)) + 1);
+    while (r2 > eps * eps * norm2 && (int)us.size() < kcap) {
         size_t best = 0;
         for (size_t e = 1; e < (size_t)m * n; ++e)
             if (std::fabs(A[e]) > std::fabs(A[best])) best = e;
@@ -264,6 +267,7 @@ void full_pivot(double* A, int m, int n, double eps, std::vector<double>& U, std
         for (int a = 0; a < m; ++a) U[(size_t)a * k + l] = us[l][a];
         for (int b = 0; b < n; ++b) V[(size_t)l * n + b] = vs[l][b];
     }
+    return r2 <= eps * eps * norm2;
 }
 
 // A = Q R for A (m x k, row-major): Q orthonormal columns (a column that
@@ -412,7 +416,9 @@ void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& 
     std::vector<double> row(n), col(m);
     double norm2 = 0.0;
     int i = 0;
-    const int kmax = std::min(m, n);
+    // beyond kmax terms the factors would hold as many values as the block itself
+    const int kmax = std::min(std::min(m, n), (int)(((size_t)m * n - 1) / (size_t)(m + n)));
+    bool converged = false;
     while ((int)us.size() < kmax) {
         used[i] = 1;
         S.eval(R + i, 1, C, n, row.data());
@@ -425,7 +431,10 @@ void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& 
             int nxt = -1;
             for (int a = 0; a < m; ++a)
                 if (!used[a]) { nxt = a; break; }
-            if (nxt < 0) break;
+            if (nxt < 0) {
+                converged = true;                           // every row is reproduced exactly
+                break;
+            }
             i = nxt;
             continue;
         }
@@ -443,13 +452,23 @@ void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& 
         norm2 += 2.0 * cross + uu * vv;
         us.push_back(std::move(u));
         vs.push_back(std::move(v));
-        if (std::sqrt(uu * vv) <= 0.25 * eps * std::sqrt(std::max(norm2, 0.0))) break;
+        if (std::sqrt(uu * vv) <= 0.25 * eps * std::sqrt(std::max(norm2, 0.0))) {
+            converged = true;
+            break;
+        }
         int nxt = -1;
         double best = -1.0;
         for (int a = 0; a < m; ++a)
             if (!used[a] && std::fabs(us.back()[a]) > best) { best = std::fabs(us.back()[a]); nxt = a; }
-        if (nxt < 0) break;
+        if (nxt < 0) {
+            converged = true;                               // every row has been a pivot row
+            break;
+        }
         i = nxt;
+    }
+    if (!converged && (int)us.size() >= kmax && kmax < std::min(m, n)) {
+        store_dense();                                      // not compressible enough to pay
+        return;
     }
     int k = (int)us.size();
     // sampled check of the residual
@@ -470,8 +489,13 @@ void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& 
         exact.resize((size_t)m * n);
         S.eval(R, m, C, n, exact.data());
         std::vector<double> blk(exact);
-        full_pivot(blk.data(), m, n, eps, Uf, Vf, k);
         out.fallback = 1;
+        if (!full_pivot(blk.data(), m, n, eps, Uf, Vf, k)) {
+            out.kind = 0;                                   // not compressible enough to pay: exact
+            out.rank = 0;
+            out.values.swap(exact);
+            return;
+        }
     } else {
         Uf.assign((size_t)m * k, 0.0);
         Vf.assign((size_t)k * n, 0.0);
