@@ -7,17 +7,20 @@
 //     evaluated.  Start from the first row; take the column of the residual
 //     row's largest entry as pivot, append u = residual column, v = residual
 //     row / pivot, and go on from the unused row where |u| is largest, until
-//     |u| |v| <= (eps/4) |S_k|_F (S_k the current approximation, its norm
-//     updated exactly from the new terms; the factor 4 covers the gap between
-//     the last term and the whole residual).  A residual row that vanishes
-//     moves on to the next unused row.
+//     |u| |v| <= (eps/2) |S_k|_F (S_k the current approximation, its norm
+//     updated exactly from the new terms) or, tested every 8 terms, the
+//     residual at 32 sampled entries is that small.  A residual row that
+//     vanishes moves on to the next unused row.
 //   * partial pivoting can miss a part of a block that none of its pivot rows
 //     sees (on a polyhedron the coplanar pairs of a face are exact zeros), so
-//     every low-rank leaf is checked at 32 pseudo-random entries; when the
-//     sampled residual, scaled to the block, exceeds eps |S_k|_F, the leaf is
-//     assembled exactly
-//     and compressed by cross approximation with full pivoting, whose bound
-//     |A - U V|_F <= eps |A|_F then holds by construction;
+//     every low-rank leaf is checked at 32 fresh pseudo-random entries (a
+//     statistical check, not a bound); when the sampled residual, scaled to
+//     the block, exceeds eps |S_k|_F, the
+//     approximation resumes from the worst sampled row and is checked again at
+//     fresh entries (up to four times); a leaf that still fails is assembled
+//     exactly and, if it has at most 65 536 entries, compressed by cross
+//     approximation with full pivoting, whose bound |A - U V|_F <= eps |A|_F
+//     holds by construction (larger ones stay exact and dense);
 //   * the factors of a low-rank leaf are then recompressed to the fewest terms
 //     the tolerance needs: U = Qu Ru, V^T = Qv Rv (Gram-Schmidt), the SVD of the
 //     k x k core Ru Rv^T by one-sided Jacobi rotations (Hestenes), truncated
@@ -25,7 +28,8 @@
 //   * a leaf whose factors would not be smaller than the block stays dense.
 // Entries: B_ij = (1/4pi) sum_{t contains j} I_t,j(x_i) + (Omega_i/4pi - 1) delta_ij,
 // I the closed-form double layer of the linear hat on a flat triangle (the same
-// formula as the device assembly in csrc/mesh.cu, written here for the host:
+// formula as the device assembly in csrc/mesh.cu, written here for the host, with
+// the edge integral's logarithm in log1p form:
 //   I_k(x) = -phi_k(p) Omega_t + h grad phi_k . sum_e nu_e P_e,
 // h the height of x over the plane, p its foot, Omega_t the signed solid angle of
 // the triangle (Van Oosterom-Strackee), P_e = int_e dl/|y - x|, nu_e the outward
@@ -87,7 +91,9 @@ void hat_double_layer_host(const double x[3], const double* y0, const double* y1
         const double s = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
         const double nu[3] = {(e[1] * n[2] - e[2] * n[1]) / s, (e[2] * n[0] - e[0] * n[2]) / s,
                               (e[0] * n[1] - e[1] * n[0]) / s};
-        const double P = std::log((eta[k] + eta[k1] + s) / (eta[k] + eta[k1] - s));
+        // ln((a + s)/(a - s)) as log1p(2s/(a - s)): far from the triangle the ratio is
+        // 1 + O(s/r), whose logarithm loses a factor r/s of relative accuracy
+        const double P = std::log1p(2.0 * s / (eta[k] + eta[k1] - s));
         for (int d = 0; d < 3; ++d) es[d] += nu[d] * P;
     }
     for (int k = 0; k < 3; ++k) {
@@ -386,13 +392,97 @@ void recompress(std::vector<double>& U, std::vector<double>& V, int m, int n, in
     k = keep;
 }
 
+struct AcaTerms {
+    std::vector<std::vector<double>> us, vs;        // A ~ sum_l us[l] vs[l]^T
+    std::vector<char> used;                         // rows that have been pivot (or zero) rows
+    double norm2 = 0.0;                             // |sum_l us[l] vs[l]^T|_F^2
+};
+
+// Residual of the current terms at 32 pseudo-random entries of the block (seed
+// `seed`), scaled to the whole block: an estimate of |A - S_k|_F^2; `worst_row`
+// receives the row of the largest sampled residual.
+double sampled_residual(Surface& S, const int* R, int m, const int* C, int n, const AcaTerms& T, uint64_t seed,
+                        int* worst_row) {
+    const int samples = 32, k = (int)T.us.size();
+    double res2 = 0.0, worst = -1.0;
+    for (int s = 0; s < samples; ++s) {
+        const uint64_t hsh = splitmix64(seed + (uint64_t)s);
+        const int a = (int)(hsh % (uint64_t)m), b = (int)((hsh >> 32) % (uint64_t)n);
+        double exact;
+        S.eval(R + a, 1, C + b, 1, &exact);
+        double approx = 0.0;
+        for (int l = 0; l < k; ++l) approx += T.us[l][a] * T.vs[l][b];
+        const double r = exact - approx;
+        res2 += r * r;
+        if (worst_row && std::fabs(r) > worst) {
+            worst = std::fabs(r);
+            *worst_row = a;
+        }
+    }
+    return res2 * ((double)m * n / samples);
+}
+
+// Partial-pivot cross approximation terms appended to T from row `start` on,
+// until |u| |v| <= (eps/2) |S_k|_F or, tested every 8 terms, the residual at 32
+// sampled entries (seed `seed`) is within (eps/2) |S_k|_F -- near the tolerance
+// the last term overstates the residual by up to sqrt(n) --, or kmax terms, or no
+// unused row is left.  Returns true unless it stopped at kmax.
+bool aca_extend(Surface& S, const int* R, int m, const int* C, int n, double eps, int kmax, int start,
+                uint64_t seed, AcaTerms& T) {
+    std::vector<double> row(n), col(m);
+    int i = start;
+    while ((int)T.us.size() < kmax) {
+        T.used[i] = 1;
+        S.eval(R + i, 1, C, n, row.data());
+        for (size_t l = 0; l < T.us.size(); ++l)
+            for (int b = 0; b < n; ++b) row[b] -= T.us[l][i] * T.vs[l][b];
+        int j = 0;
+        for (int b = 1; b < n; ++b)
+            if (std::fabs(row[b]) > std::fabs(row[j])) j = b;
+        if (row[j] == 0.0) {
+            int nxt = -1;
+            for (int a = 0; a < m; ++a)
+                if (!T.used[a]) { nxt = a; break; }
+            if (nxt < 0) return true;                       // every row is reproduced exactly
+            i = nxt;
+            continue;
+        }
+        std::vector<double> v(n), u(m);
+        for (int b = 0; b < n; ++b) v[b] = row[b] / row[j];
+        S.eval(R, m, C + j, 1, col.data());
+        for (int a = 0; a < m; ++a) {
+            double x = col[a];
+            for (size_t l = 0; l < T.us.size(); ++l) x -= T.vs[l][j] * T.us[l][a];
+            u[a] = x;
+        }
+        const double uu = dot(u.data(), u.data(), m), vv = dot(v.data(), v.data(), n);
+        double cross = 0.0;
+        for (size_t l = 0; l < T.us.size(); ++l)
+            cross += dot(u.data(), T.us[l].data(), m) * dot(T.vs[l].data(), v.data(), n);
+        T.norm2 += 2.0 * cross + uu * vv;
+        T.us.push_back(std::move(u));
+        T.vs.push_back(std::move(v));
+        const double goal2 = 0.25 * eps * eps * std::max(T.norm2, 0.0);
+        if (uu * vv <= goal2) return true;
+        if (T.us.size() % 8 == 0 && sampled_residual(S, R, m, C, n, T, seed, nullptr) <= goal2) return true;
+        int nxt = -1;
+        double best = -1.0;
+        for (int a = 0; a < m; ++a)
+            if (!T.used[a] && std::fabs(T.us.back()[a]) > best) { best = std::fabs(T.us.back()[a]); nxt = a; }
+        if (nxt < 0) return true;                           // every row has been a pivot row
+        i = nxt;
+    }
+    return false;
+}
+
 struct LeafOut {
     int kind = 0, rank = 0, fallback = 0;
     std::vector<double> values;                   // dense m*n, or U (m*k) then V (k*n)
 };
 
 // One leaf of the block tree: exact entries (dense), or cross approximation,
-// sampled check, fallback and recompression (low rank).
+// sampled check (resumed from the worst sampled row up to four times), exact
+// fallback and recompression (low rank).
 void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& out) {
     const HLeaf& lf = P.leaves[li];
     const HCluster& ct = P.clusters[lf.row];
@@ -410,88 +500,36 @@ void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& 
         store_dense();
         return;
     }
-    // adaptive cross approximation with partial pivoting
-    std::vector<std::vector<double>> us, vs;
-    std::vector<char> used(m, 0);
-    std::vector<double> row(n), col(m);
-    double norm2 = 0.0;
-    int i = 0;
-    // beyond kmax terms the factors would hold as many values as the block itself
+    // adaptive cross approximation with partial pivoting, checked at sampled
+    // entries; a failed check resumes it from the worst sampled row
     const int kmax = std::min(std::min(m, n), (int)(((size_t)m * n - 1) / (size_t)(m + n)));
-    bool converged = false;
-    while ((int)us.size() < kmax) {
-        used[i] = 1;
-        S.eval(R + i, 1, C, n, row.data());
-        for (size_t l = 0; l < us.size(); ++l)
-            for (int b = 0; b < n; ++b) row[b] -= us[l][i] * vs[l][b];
-        int j = 0;
-        for (int b = 1; b < n; ++b)
-            if (std::fabs(row[b]) > std::fabs(row[j])) j = b;
-        if (row[j] == 0.0) {
-            int nxt = -1;
-            for (int a = 0; a < m; ++a)
-                if (!used[a]) { nxt = a; break; }
-            if (nxt < 0) {
-                converged = true;                           // every row is reproduced exactly
-                break;
-            }
-            i = nxt;
-            continue;
-        }
-        std::vector<double> v(n), u(m);
-        for (int b = 0; b < n; ++b) v[b] = row[b] / row[j];
-        S.eval(R, m, C + j, 1, col.data());
-        for (int a = 0; a < m; ++a) {
-            double x = col[a];
-            for (size_t l = 0; l < us.size(); ++l) x -= vs[l][j] * us[l][a];
-            u[a] = x;
-        }
-        const double uu = dot(u.data(), u.data(), m), vv = dot(v.data(), v.data(), n);
-        double cross = 0.0;
-        for (size_t l = 0; l < us.size(); ++l) cross += dot(u.data(), us[l].data(), m) * dot(vs[l].data(), v.data(), n);
-        norm2 += 2.0 * cross + uu * vv;
-        us.push_back(std::move(u));
-        vs.push_back(std::move(v));
-        if (std::sqrt(uu * vv) <= 0.25 * eps * std::sqrt(std::max(norm2, 0.0))) {
-            converged = true;
+    AcaTerms T;
+    T.used.assign(m, 0);
+    const uint64_t stop_seed = ((uint64_t)li << 12) | 0xF00u;  // samples of the stopping test
+    bool conv = aca_extend(S, R, m, C, n, eps, kmax, 0, stop_seed, T);
+    bool ok = false;
+    int checks = 0;
+    for (int attempt = 0; attempt < 4 && (conv || (int)T.us.size() < kmax); ++attempt) {
+        ++checks;
+        int worst_row = 0;
+        const double est = sampled_residual(S, R, m, C, n, T, ((uint64_t)li << 12) + ((uint64_t)attempt << 6),
+                                            &worst_row);
+        if (est <= eps * eps * std::max(T.norm2, 0.0) && !(T.us.empty() && est > 0.0)) {
+            ok = true;
             break;
         }
-        int nxt = -1;
-        double best = -1.0;
-        for (int a = 0; a < m; ++a)
-            if (!used[a] && std::fabs(us.back()[a]) > best) { best = std::fabs(us.back()[a]); nxt = a; }
-        if (nxt < 0) {
-            converged = true;                               // every row has been a pivot row
-            break;
-        }
-        i = nxt;
+        conv = aca_extend(S, R, m, C, n, eps, kmax, worst_row, stop_seed + 0x100u * (uint64_t)(attempt + 1), T);
     }
-    if (!converged && (int)us.size() >= kmax && kmax < std::min(m, n)) {
-        store_dense();                                      // not compressible enough to pay
-        return;
-    }
-    int k = (int)us.size();
-    // sampled check of the residual
-    double res2 = 0.0;
-    const int samples = 32;
-    for (int s = 0; s < samples; ++s) {
-        const uint64_t hsh = splitmix64(((uint64_t)li << 8) + (uint64_t)s);
-        const int a = (int)(hsh % (uint64_t)m), b = (int)((hsh >> 32) % (uint64_t)n);
-        double exact;
-        S.eval(R + a, 1, C + b, 1, &exact);
-        double approx = 0.0;
-        for (int l = 0; l < k; ++l) approx += us[l][a] * vs[l][b];
-        res2 += (exact - approx) * (exact - approx);
-    }
-    const double est = res2 * ((double)m * n / samples);
     std::vector<double> Uf, Vf, exact;
-    if (est > eps * eps * std::max(norm2, 0.0) || (k == 0 && res2 > 0.0)) {
+    int k = (int)T.us.size();
+    if (!ok) {
+        // exact entries; compressed by full pivoting when the block is small enough
+        out.fallback = checks > 0;                          // the sampled check failed (else: incompressible)
         exact.resize((size_t)m * n);
         S.eval(R, m, C, n, exact.data());
         std::vector<double> blk(exact);
-        out.fallback = 1;
-        if (!full_pivot(blk.data(), m, n, eps, Uf, Vf, k)) {
-            out.kind = 0;                                   // not compressible enough to pay: exact
+        if ((size_t)m * n > ((size_t)1 << 16) || !full_pivot(blk.data(), m, n, eps, Uf, Vf, k)) {
+            out.kind = 0;
             out.rank = 0;
             out.values.swap(exact);
             return;
@@ -500,8 +538,8 @@ void fill_leaf(Surface& S, const HPartition& P, size_t li, double eps, LeafOut& 
         Uf.assign((size_t)m * k, 0.0);
         Vf.assign((size_t)k * n, 0.0);
         for (int l = 0; l < k; ++l) {
-            for (int a = 0; a < m; ++a) Uf[(size_t)a * k + l] = us[l][a];
-            for (int b = 0; b < n; ++b) Vf[(size_t)l * n + b] = vs[l][b];
+            for (int a = 0; a < m; ++a) Uf[(size_t)a * k + l] = T.us[l][a];
+            for (int b = 0; b < n; ++b) Vf[(size_t)l * n + b] = T.vs[l][b];
         }
     }
     recompress(Uf, Vf, m, n, k, 0.5 * eps);
