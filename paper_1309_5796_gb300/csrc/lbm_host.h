@@ -76,7 +76,7 @@ struct HMatrixHost {
     std::vector<int> rank;             // per leaf: k of a low-rank leaf, 0 otherwise
     std::vector<size_t> off;           // per leaf: offset of its values in data
     std::vector<double> data;
-    int fallbacks = 0;                 // low-rank leaves assembled exactly after the sampled check
+    int fallbacks = 0;                 // admissible leaves assembled exactly after failing the sampled check
 };
 // B_H of the surface (xyz: node coordinates, any length unit; bidx: surface nodes,
 // ascending; tris: outward surface triangles) for tolerance eps, filled by `threads`
@@ -84,6 +84,18 @@ struct HMatrixHost {
 // why the input was refused.
 std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
                                int n_min, double eps, int threads, HMatrixHost& H);
+
+// ---- open boundary by space transformation: host set-up (csrc/shell.cu) -------------
+struct ShellGrid {
+    int nt = 0;                        // cells a side of the grid (magnet + air + shell)
+    double R1 = 0.0, R2 = 0.0;         // max-norm radii of the air box and the outer face (lattice units)
+    std::vector<int> rowptr, col;      // CSR of the element adjacency, columns ascending
+    std::vector<double> K;             // sum_e c_i^T M_e c_j / (6 |det_e|), SI (m)
+    std::vector<int> outer;            // grid nodes on the outer face (Dirichlet u = 0), ascending
+    std::vector<int> magnet;           // grid node of every magnet node (magnet's own numbering)
+    size_t shell_tets = 0;             // tetrahedra whose centroid lies in the shell
+};
+std::string host_shell_setup(int n, int a, int s, double cell, ShellGrid& G);
 
 // ---- device view of one mesh --------------------------------------------------------
 struct MeshView {
