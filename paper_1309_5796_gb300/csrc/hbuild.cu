@@ -122,17 +122,23 @@ struct Surface {
     int nb;
     const int* bidx;
     const int* tris;
-    std::vector<int> inc_ptr, inc_tri, inc_slot;   // boundary position -> (triangle, slot)
+    std::vector<int> pos;                          // node id -> boundary position or -1
+    std::vector<int> inc_ptr, inc_tri;             // boundary position -> triangles that contain it
     std::vector<double> omega;                     // interior solid angle per position
-    std::vector<int> mark, local;                  // scratch of the block evaluation
-    int stamp = 0;
+    std::vector<int> mark, local, in_cols;         // scratch of the block evaluation
+    int stamp = 0, col_stamp = 0;
 
-    // out[a * cols.size() + b] = B[rows[a], cols[b]]
-    void block(const int* rows, int m, const int* cols, int n, double* out) {
+    // out[a * n + b] = B[rows[a], cols[b]] (boundary positions)
+    void eval(const int* rows, int m, const int* cols, int n, double* out) {
         if (m <= 0 || n <= 0) return;
+        ++col_stamp;
+        for (int b = 0; b < n; ++b) {
+            in_cols[cols[b]] = col_stamp;
+            local[cols[b]] = b;
+        }
         std::fill(out, out + (size_t)m * n, 0.0);
+        // the triangles around the columns, in ascending order
         ++stamp;
-        for (int b = 0; b < n; ++b) local[cols[b]] = b;
         std::vector<int> tl;
         for (int b = 0; b < n; ++b)
             for (int q = inc_ptr[cols[b]]; q < inc_ptr[cols[b] + 1]; ++q) {
@@ -148,39 +154,19 @@ struct Surface {
             const double* x = xyz + 3 * (size_t)id;
             for (int t : tl) {
                 const int* v = tris + 3 * (size_t)t;
-                if (v[0] == id || v[1] == id || v[2] == id) continue;
+                if (v[0] == id || v[1] == id || v[2] == id) continue;   // contains x: 0
                 double I[3];
                 hat_double_layer_host(x, xyz + 3 * (size_t)v[0], xyz + 3 * (size_t)v[1], xyz + 3 * (size_t)v[2], I);
                 for (int k = 0; k < 3; ++k) {
-                    const int p = pos_of(v[k]);
-                    if (p >= 0 && member(p, cols, n)) out[(size_t)a * n + local[p]] += I[k];
+                    const int p = pos[v[k]];
+                    if (p >= 0 && in_cols[p] == col_stamp) out[(size_t)a * n + local[p]] += I[k];
                 }
             }
         }
         const double s = 0.25 / kPi;
         for (size_t e = 0; e < (size_t)m * n; ++e) out[e] *= s;
-        for (int a = 0; a < m; ++a) {
-            const int b = member(rows[a], cols, n) ? local[rows[a]] : -1;
-            if (b >= 0) out[(size_t)a * n + b] += omega[rows[a]] * s - 1.0;
-        }
-    }
-
-    std::vector<int> pos;                          // node id -> boundary position or -1
-    std::vector<int> in_cols;                      // position -> stamp of the current column set
-    int col_stamp = 0;
-    int pos_of(int node) const { return pos[node]; }
-    bool member(int p, const int* cols, int n) const {
-        (void)cols;
-        (void)n;
-        return in_cols[p] == col_stamp;
-    }
-    void set_cols(const int* cols, int n) {
-        ++col_stamp;
-        for (int b = 0; b < n; ++b) in_cols[cols[b]] = col_stamp;
-    }
-    void eval(const int* rows, int m, const int* cols, int n, double* out) {
-        set_cols(cols, n);
-        block(rows, m, cols, n, out);
+        for (int a = 0; a < m; ++a)
+            if (in_cols[rows[a]] == col_stamp) out[(size_t)a * n + local[rows[a]]] += omega[rows[a]] * s - 1.0;
     }
 };
 
@@ -583,15 +569,10 @@ std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx
         for (int k = 0; k < 3; ++k) ++S.inc_ptr[S.pos[tris[3 * t + k]] + 1];
     for (int q = 0; q < nb; ++q) S.inc_ptr[q + 1] += S.inc_ptr[q];
     S.inc_tri.resize(3 * (size_t)F);
-    S.inc_slot.resize(3 * (size_t)F);
     {
         std::vector<int> fill(S.inc_ptr.begin(), S.inc_ptr.end() - 1);
         for (int t = 0; t < F; ++t)
-            for (int k = 0; k < 3; ++k) {
-                const int q = S.pos[tris[3 * t + k]];
-                S.inc_tri[fill[q]] = t;
-                S.inc_slot[fill[q]++] = k;
-            }
+            for (int k = 0; k < 3; ++k) S.inc_tri[fill[S.pos[tris[3 * t + k]]]++] = t;
     }
     S.mark.assign(F, 0);
     S.local.assign(nb, -1);
