@@ -199,6 +199,24 @@ int lbm_mesh_export(lbm_ctx* ctx, lbm_mesh mesh, int32_t* tets, int32_t* rowptr,
  * u2|S = B u1|S of the hybrid FEM/BEM open boundary (Sec. 3.1). */
 int lbm_bem_rows(lbm_ctx* ctx, lbm_mesh mesh, int64_t row0, int64_t nrows, double* out);
 
+/* Storage of the hierarchical (H-matrix) form of a mesh's double-layer matrix B
+ * (Sec. 3.1 names hierarchical matrices for the boundary element method of the
+ * comparison solver), built on the host without a GPU: the surface of the mesh
+ * as lbm_mesh_upload finds it, its boundary nodes split by geometric bisection
+ * into clusters of at most n_min, a block (rows tau, columns sigma) kept in low
+ * rank when min(diam tau, diam sigma) <= eta dist(tau, sigma) (boxes of the
+ * collocation points and of the hat functions' supports), each such block
+ * approximated by adaptive cross approximation to the relative Frobenius
+ * tolerance eps, checked at sampled entries and recompressed; the others keep
+ * their exact entries.
+ *   xyz, n_nodes, tets, n_tets  HOST, as for lbm_mesh_upload (copied; same checks)
+ *   eps      0 < eps < 1;  eta > 0 (2 is a common choice);  n_min >= 1 (e.g. 16)
+ *   threads  host threads (>= 1; the result does not depend on their number)
+ *   out      HOST [4]: stored values, nb*nb (the dense matrix's), leaves, low-rank leaves
+ * Returns LBM_OK, or LBM_E_INVALID with a message (bad mesh or parameters). */
+int lbm_hmatrix_plan(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets, double eps,
+                     double eta, int32_t n_min, int32_t threads, int64_t out[4]);
+
 /* ---- instances (Eq. 1: min phi_t(m) s.t. |m| = 1) ----------------------------- */
 
 /* A batch of `batch` independent problems on one mesh, solved together

@@ -90,6 +90,8 @@ SIGNATURES = [
     ("lbm_mesh_info", C.c_int, [_P, _I64, C.POINTER(_I64)]),
     ("lbm_mesh_export", C.c_int, [_P, _I64] + [_IP] * 9),
     ("lbm_bem_rows", C.c_int, [_P, _I64, _I64, _I64, _DP]),
+    ("lbm_hmatrix_plan", C.c_int, [_DP, _I64, _IP, _I64, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                   C.POINTER(_I64)]),
     ("lbm_instance_create", C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(_I64)]),
     ("lbm_instance_destroy", C.c_int, [_P, _I64]),
     ("lbm_set_material", C.c_int, [_P, _I64, C.POINTER(Material)]),
@@ -159,6 +161,17 @@ def default_opts(precision=LBM_FP64, **kw) -> SolveOpts:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def hmatrix_plan(xyz, tets, eps: float = 1e-6, eta: float = 2.0, n_min: int = 16, threads: int | None = None) -> dict:
+    """Storage of the hierarchical form of the mesh's boundary matrix (lbm_hmatrix_plan;
+    host only, no GPU): stored values, the dense matrix's nb^2, leaves, low-rank leaves."""
+    x = np.ascontiguousarray(np.asarray(xyz, np.float64))
+    t = np.ascontiguousarray(np.asarray(tets, np.int32))
+    out = (C.c_int64 * 4)()
+    th = threads if threads is not None else max(1, os.cpu_count() or 1)
+    _check(lib().lbm_hmatrix_plan(_dptr(x), x.shape[0], _iptr(t), t.shape[0], eps, eta, n_min, th, out))
+    return dict(stored=out[0], dense=out[1], leaves=out[2], low_rank=out[3], fraction=out[0] / out[1])
 
 
 class Context:

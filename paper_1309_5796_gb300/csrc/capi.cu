@@ -1023,6 +1023,37 @@ int lbm_bem_rows(lbm_ctx* ctx, lbm_mesh mesh, int64_t row0, int64_t nrows, doubl
     LBM_CATCH
 }
 
+int lbm_hmatrix_plan(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets, double eps, double eta,
+                     int32_t n_min, int32_t threads, int64_t out[4]) {
+    LBM_TRY
+    if (!xyz || !tets || !out) return fail(LBM_E_INVALID, "lbm_hmatrix_plan: null argument");
+    if (n_nodes < 4 || n_nodes > LBM_UPLOAD_MAX_NODES || n_tets < 1 || n_tets > LBM_UPLOAD_MAX_TETS)
+        return fail(LBM_E_INVALID, "lbm_hmatrix_plan: mesh size out of range");
+    for (int64_t k = 0; k < 3 * n_nodes; ++k)
+        if (!std::isfinite(xyz[k])) return fail(LBM_E_INVALID, "lbm_hmatrix_plan: non-finite coordinate");
+    if (!(eps > 0.0 && eps < 1.0) || !(eta > 0.0) || !std::isfinite(eta) || n_min < 1 || threads < 1)
+        return fail(LBM_E_INVALID,
+                    "lbm_hmatrix_plan: eps must lie in (0, 1), eta be positive, n_min and threads at least 1");
+    GeneralTopology g;
+    const std::string why = host_general_topology((int)n_nodes, (int)n_tets, tets, xyz, g);
+    if (!why.empty()) return fail(LBM_E_INVALID, "lbm_hmatrix_plan: %s", why.c_str());
+    std::vector<double> xl(3 * (size_t)n_nodes);                 // in units of the length unit, as uploads
+    for (size_t k = 0; k < xl.size(); ++k) xl[k] = xyz[k] / g.L;
+    HMatrixHost H;
+    const int nb = (int)g.bidx.size(), F = (int)(g.tris.size() / 3);
+    const std::string w2 = host_hmatrix_build((int)n_nodes, xl.data(), nb, g.bidx.data(), F, g.tris.data(), eta,
+                                              n_min, eps, threads, H);
+    if (!w2.empty()) return fail(LBM_E_INVALID, "lbm_hmatrix_plan: %s", w2.c_str());
+    int64_t low = 0;
+    for (int k : H.kind) low += k;
+    out[0] = (int64_t)H.data.size();
+    out[1] = (int64_t)nb * nb;
+    out[2] = (int64_t)H.kind.size();
+    out[3] = low;
+    return LBM_OK;
+    LBM_CATCH
+}
+
 int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t precision, lbm_inst* out) {
     LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
