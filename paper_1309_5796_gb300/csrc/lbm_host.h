@@ -85,6 +85,25 @@ struct HMatrixHost {
 std::string host_hmatrix_build(int N, const double* xyz, int nb, const int* bidx, int F, const int* tris, double eta,
                                int n_min, double eps, int threads, HMatrixHost& H);
 
+// The operator packed for a device product (csrc/hpack.cu).
+struct HPackedLeaf {
+    int row_begin, m;                  // row cluster: idx[row_begin, row_begin + m)
+    int col_begin, n;                  // column cluster: idx[col_begin, col_begin + n)
+    int kind, rank;                    // 0 dense, 1 low rank (rank k)
+    size_t val;                        // offset in values: m*n dense, or V (k x n) then U (m x k)
+    size_t slot;                       // first of the leaf's m output slots
+};
+struct HPacked {
+    int nb = 0;
+    std::vector<HPackedLeaf> leaves;   // dense first, then low rank, each by (rows, columns)
+    std::vector<int> idx;              // cluster positions (as HPartition::idx)
+    std::vector<float> values;
+    size_t n_slots = 0;
+    std::vector<size_t> row_ptr;       // [nb + 1]: slots of each boundary position,
+    std::vector<size_t> row_slots;     //   in block-tree order of their leaves
+};
+std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P);
+
 // ---- open boundary by space transformation: host set-up (csrc/shell.cu) -------------
 struct ShellGrid {
     int nt = 0;                        // cells a side of the grid (magnet + air + shell)
