@@ -1,16 +1,18 @@
 // Packing of a built hierarchical boundary matrix (csrc/hbuild.cu) into the
-// flat FP32 layout a device product reads, y = B_H x for B instances at once:
-//   * leaves in the order (kind, rows, columns, block-tree position): dense leaves
-//     first, then low-rank ones, each group by size, so that a launch can give
-//     leaves of one shape to one kind of thread group;
-//   * values in FP32: a dense leaf's m x n entries (row-major); a low-rank leaf's
-//     V (k x n, row-major) followed by U (m x k, row-major), in the order the
-//     product uses them (t = V x_sigma, then y_tau += U t);
-//   * every leaf writes its m rows of the product to its own output slots (no two
-//     leaves share a slot), and a second pass adds, for every boundary position,
-//     the slots of the leaves whose row cluster holds it, in block-tree order:
-//     the sum's order is fixed by the block tree, whatever order the leaves run in.
-// Host code only; no kernel lives here.
+// flat FP32 layout a device product reads, y = B_H x for B instances at once,
+// in two passes:
+//   1. t_l = V_l x_sigma(l) for every low-rank leaf l (k_l x B values: small);
+//   2. every leaf of the cluster tree (a "row owner": at most n_min positions,
+//      together they partition the positions) forms its rows of y as the sum,
+//      in block-tree order, of the contributions of all block-tree leaves whose
+//      row cluster contains it -- rows of a dense leaf times x_sigma, or rows of
+//      U_l times t_l -- and writes them once.  No two owners share a position,
+//      so the result needs no atomics and its summation order is fixed.
+// Layout: the leaves in the order (kind, rows, columns, block-tree position),
+// dense first, each group by size (one shape per thread group); FP32 values, a
+// dense leaf's m x n entries row-major, a low-rank leaf's V (k x n) then U (m x k),
+// both row-major; per owner its entries (leaf, offset of its local rows in
+// row_map), in block-tree order.  Host code only; no kernel lives here.
 #include <algorithm>
 #include <numeric>
 #include <string>
@@ -26,6 +28,7 @@ std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P) {
     if (H.kind.size() != L || H.rank.size() != L || H.off.size() != L) return "inconsistent operator";
     P = HPacked{};
     P.nb = nb;
+    P.idx = H.P.idx;
     std::vector<size_t> order(L);
     std::iota(order.begin(), order.end(), 0);
     auto shape = [&](size_t l) {
@@ -33,11 +36,12 @@ std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P) {
         return std::make_tuple(H.kind[l], H.P.clusters[lf.row].size, H.P.clusters[lf.col].size);
     };
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return shape(a) < shape(b); });
+    std::vector<int> packed_of(L);                   // block-tree leaf -> packed index
     P.leaves.resize(L);
-    size_t vals = 0, slots = 0;
-    std::vector<size_t> slot_of(L);                  // first output slot of each leaf (block-tree index)
+    size_t vals = 0, ts = 0;
     for (size_t q = 0; q < L; ++q) {
         const size_t l = order[q];
+        packed_of[l] = (int)q;
         const HLeaf& lf = H.P.leaves[l];
         const HCluster& ct = H.P.clusters[lf.row];
         const HCluster& cs = H.P.clusters[lf.col];
@@ -49,12 +53,11 @@ std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P) {
         e.kind = H.kind[l];
         e.rank = H.rank[l];
         e.val = vals;
-        e.slot = slots;
-        slot_of[l] = slots;
+        e.t_off = ts;
         vals += e.kind ? (size_t)e.rank * (e.m + e.n) : (size_t)e.m * e.n;
-        slots += e.m;
+        if (e.kind) ts += (size_t)e.rank;
     }
-    P.idx = H.P.idx;
+    P.n_t = ts;
     P.values.resize(vals);
     for (size_t q = 0; q < L; ++q) {
         const size_t l = order[q];
@@ -69,21 +72,46 @@ std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P) {
             for (size_t i = 0; i < nu; ++i) dst[nv + i] = (float)src[i];        // then U
         }
     }
-    P.n_slots = slots;
-    // boundary position -> its slots, in block-tree order of the leaves
-    std::vector<std::vector<size_t>> per(nb);
-    for (size_t l = 0; l < L; ++l) {
-        const HCluster& ct = H.P.clusters[H.P.leaves[l].row];
-        for (int a = 0; a < ct.size; ++a) {
-            const int p = H.P.idx[ct.begin + a];
-            if (p < 0 || p >= nb) return "position out of range";
-            per[p].push_back(slot_of[l] + a);
+    // row owners: the leaves of the cluster tree, in cluster order
+    std::vector<int> owner_of_cluster(H.P.clusters.size(), -1);
+    for (size_t c = 0; c < H.P.clusters.size(); ++c)
+        if (H.P.clusters[c].child[0] < 0) {
+            owner_of_cluster[c] = (int)P.owner_begin.size();
+            P.owner_begin.push_back(H.P.clusters[c].begin);
+            P.owner_size.push_back(H.P.clusters[c].size);
+        }
+    std::vector<std::vector<HPackedEntry>> per(P.owner_begin.size());
+    std::vector<int> stack;
+    for (size_t l = 0; l < L; ++l) {                 // block-tree order
+        const int tau = H.P.leaves[l].row;
+        const HCluster& ct = H.P.clusters[tau];
+        const int* tb = H.P.idx.data() + ct.begin;
+        stack.assign(1, tau);
+        while (!stack.empty()) {                     // the cluster-tree leaves under tau
+            const int c = stack.back();
+            stack.pop_back();
+            const HCluster& cc = H.P.clusters[c];
+            if (cc.child[0] >= 0) {
+                stack.push_back(cc.child[1]);
+                stack.push_back(cc.child[0]);
+                continue;
+            }
+            HPackedEntry en;
+            en.leaf = packed_of[l];
+            en.rows = P.row_map.size();
+            for (int a = 0; a < cc.size; ++a) {      // local row in tau of each owned position
+                const int p = H.P.idx[cc.begin + a];
+                const int* it = std::lower_bound(tb, tb + ct.size, p);
+                if (it == tb + ct.size || *it != p) return "cluster tree is not nested";
+                P.row_map.push_back((int)(it - tb));
+            }
+            per[owner_of_cluster[c]].push_back(en);
         }
     }
-    P.row_ptr.assign(nb + 1, 0);
-    for (int p = 0; p < nb; ++p) P.row_ptr[p + 1] = P.row_ptr[p] + per[p].size();
-    P.row_slots.resize(P.row_ptr[nb]);
-    for (int p = 0; p < nb; ++p) std::copy(per[p].begin(), per[p].end(), P.row_slots.begin() + P.row_ptr[p]);
+    P.owner_ptr.assign(per.size() + 1, 0);
+    for (size_t o = 0; o < per.size(); ++o) P.owner_ptr[o + 1] = P.owner_ptr[o] + per[o].size();
+    P.entries.reserve(P.owner_ptr.back());
+    for (const auto& v : per) P.entries.insert(P.entries.end(), v.begin(), v.end());
     return {};
 }
 

@@ -91,16 +91,22 @@ struct HPackedLeaf {
     int col_begin, n;                  // column cluster: idx[col_begin, col_begin + n)
     int kind, rank;                    // 0 dense, 1 low rank (rank k)
     size_t val;                        // offset in values: m*n dense, or V (k x n) then U (m x k)
-    size_t slot;                       // first of the leaf's m output slots
+    size_t t_off;                      // low rank: offset of t = V x (k x B) in the first pass's output
+};
+struct HPackedEntry {
+    int leaf;                          // packed leaf
+    size_t rows;                       // offset in row_map of the owner's rows within the leaf's rows
 };
 struct HPacked {
     int nb = 0;
     std::vector<HPackedLeaf> leaves;   // dense first, then low rank, each by (rows, columns)
     std::vector<int> idx;              // cluster positions (as HPartition::idx)
     std::vector<float> values;
-    size_t n_slots = 0;
-    std::vector<size_t> row_ptr;       // [nb + 1]: slots of each boundary position,
-    std::vector<size_t> row_slots;     //   in block-tree order of their leaves
+    size_t n_t = 0;                    // sum of the ranks (rows of the first pass's output)
+    std::vector<int> owner_begin, owner_size;   // row owners (cluster-tree leaves): idx ranges
+    std::vector<size_t> owner_ptr;     // [owners + 1]: their entries, in block-tree order
+    std::vector<HPackedEntry> entries;
+    std::vector<int> row_map;
 };
 std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P);
 

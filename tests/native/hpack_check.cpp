@@ -1,8 +1,9 @@
 // Builds and packs the library's hierarchical boundary matrix for a surface read
 // from a binary file, then applies it to B vectors through the packed layout with
-// a plain reference product written here (per leaf: dense rows, or t = V x_sigma
-// and U t, into the leaf's output slots; then, per boundary position, the sum of
-// its slots in the order the layout lists them) and writes the leaf table and y.
+// a plain reference product written here (t = V x_sigma for every low-rank leaf;
+// then every row owner sums its entries in the listed order -- dense rows times
+// x_sigma, or rows of U times t -- and writes its rows) and writes the leaf table
+// and y.
 //   input : int32 N, nb, F, n_min, threads, B; double eta, eps; double xyz[N*3];
 //           int32 bidx[nb]; int32 tris[F*3]; double x[nb*B] (position-major)
 //   output: "error <message>\n", or "ok" then int32 n_leaves; per leaf int32 row_begin, m,
@@ -43,40 +44,45 @@ int main(int argc, char** argv) {
         fclose(out);
         return 0;
     }
-    std::vector<double> slot(P.n_slots * (size_t)B, 0.0), y((size_t)nb * B, 0.0);
+    // pass 1: t = V x_sigma of every low-rank leaf
+    std::vector<double> t(P.n_t * (size_t)B, 0.0), y((size_t)nb * B, 0.0);
     for (const auto& e : P.leaves) {
-        const float* v = P.values.data() + e.val;
-        const int* R = P.idx.data() + e.row_begin;
+        if (!e.kind) continue;
+        const float* V = P.values.data() + e.val;
         const int* Cc = P.idx.data() + e.col_begin;
-        (void)R;
-        if (!e.kind) {
-            for (int a = 0; a < e.m; ++a)
+        for (int l = 0; l < e.rank; ++l)
+            for (int c = 0; c < B; ++c) {
+                double s = 0.0;
+                for (int b = 0; b < e.n; ++b) s += (double)V[(size_t)l * e.n + b] * x[(size_t)Cc[b] * B + c];
+                t[(e.t_off + l) * B + c] = s;
+            }
+    }
+    // pass 2: every row owner sums its entries in order and writes its rows once
+    for (size_t o = 0; o + 1 < P.owner_ptr.size(); ++o) {
+        const int* own = P.idx.data() + P.owner_begin[o];
+        const int rows = P.owner_size[o];
+        std::vector<double> acc((size_t)rows * B, 0.0);
+        for (size_t q = P.owner_ptr[o]; q < P.owner_ptr[o + 1]; ++q) {
+            const auto& en = P.entries[q];
+            const auto& e = P.leaves[en.leaf];
+            const int* rm = P.row_map.data() + en.rows;
+            const float* v = P.values.data() + e.val;
+            const int* Cc = P.idx.data() + e.col_begin;
+            for (int a = 0; a < rows; ++a)
                 for (int c = 0; c < B; ++c) {
                     double s = 0.0;
-                    for (int b = 0; b < e.n; ++b) s += (double)v[(size_t)a * e.n + b] * x[(size_t)Cc[b] * B + c];
-                    slot[(e.slot + a) * B + c] = s;
-                }
-        } else {
-            const float* V = v;
-            const float* U = v + (size_t)e.rank * e.n;
-            std::vector<double> t((size_t)e.rank * B, 0.0);
-            for (int l = 0; l < e.rank; ++l)
-                for (int c = 0; c < B; ++c) {
-                    double s = 0.0;
-                    for (int b = 0; b < e.n; ++b) s += (double)V[(size_t)l * e.n + b] * x[(size_t)Cc[b] * B + c];
-                    t[(size_t)l * B + c] = s;
-                }
-            for (int a = 0; a < e.m; ++a)
-                for (int c = 0; c < B; ++c) {
-                    double s = 0.0;
-                    for (int l = 0; l < e.rank; ++l) s += (double)U[(size_t)a * e.rank + l] * t[(size_t)l * B + c];
-                    slot[(e.slot + a) * B + c] = s;
+                    if (!e.kind) {
+                        for (int b = 0; b < e.n; ++b) s += (double)v[(size_t)rm[a] * e.n + b] * x[(size_t)Cc[b] * B + c];
+                    } else {
+                        const float* U = v + (size_t)e.rank * e.n;
+                        for (int l = 0; l < e.rank; ++l) s += (double)U[(size_t)rm[a] * e.rank + l] * t[(e.t_off + l) * B + c];
+                    }
+                    acc[(size_t)a * B + c] += s;
                 }
         }
+        for (int a = 0; a < rows; ++a)
+            for (int c = 0; c < B; ++c) y[(size_t)own[a] * B + c] = acc[(size_t)a * B + c];
     }
-    for (int p = 0; p < nb; ++p)
-        for (size_t q = P.row_ptr[p]; q < P.row_ptr[p + 1]; ++q)
-            for (int c = 0; c < B; ++c) y[(size_t)p * B + c] += slot[P.row_slots[q] * B + c];
     fwrite("ok", 1, 2, out);
     const int32_t nl = (int32_t)P.leaves.size();
     fwrite(&nl, 4, 1, out);

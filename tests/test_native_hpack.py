@@ -1,6 +1,6 @@
 """The library's packing of the hierarchical boundary matrix for a device
 product (csrc/hpack.cu: leaf table sorted by kind and size, FP32 values with V
-before U, one output slot per leaf row and a position-to-slots table in
+before U, a first pass t = V x and row owners that sum their entries in
 block-tree order), applied to B vectors by a plain reference product in a C++
 driver, against the oracle's dense matrix on the CPU: the leaves tile the matrix,
 are sorted as stated, and |y - B x|_F <= (eps + FP32 rounding) |B|_F |x|_F."""
