@@ -234,3 +234,29 @@ def test_demag_energy_and_field_with_the_hmatrix(eps):
     assert np.abs(eh.h - e.h).max() <= eps * np.abs(e.h).max()
     for k in ("ex", "an", "z"):
         assert eh.terms[k] == e.terms[k]
+
+
+def test_minimiser_with_the_hmatrix_follows_the_dense_one():
+    """The full minimisation with B_H (eps 1e-6) in place of the dense B takes the
+    same steps and ends at the same energy and torque, to far below the solver's
+    1e-6 (two instances of the batched workload's distribution on a 10^3 cube)."""
+    import copy
+    from oracle.minimise import minimise
+    from synth.inputs import A_JM, JS_T, K1_JM3, batched_case
+    insts = batched_case(10, 2, seed=4)
+    dense = CubeProblem(10, JS_T, A_JM, K1_JM3, insts[0].axis)
+    c = dense.mesh
+    H = hm.build_hmatrix(hm.dense_blocks(dense.B), c.nodes.astype(np.float64), c.bnd, c.tris, eps=1e-6,
+                         eta=2.0, n_min=16)
+    assert any(L.low_rank for L in H.leaves)
+    compressed = copy.copy(dense)
+    compressed.B = H
+    scale = dense.Kd * dense.V.sum()
+    for inst in insts:
+        for p in (dense, compressed):
+            p.axis = inst.axis / np.linalg.norm(inst.axis)
+        a = minimise(dense, inst.m0, inst.h_ext, tol=1e-6, max_iter=5000)
+        b = minimise(compressed, inst.m0, inst.h_ext, tol=1e-6, max_iter=5000)
+        assert a.status == b.status == 0 and a.evaluations == b.evaluations
+        assert abs(a.E - b.E) <= 1e-9 * scale
+        assert abs(dense.evaluate(b.m, inst.h_ext).torque - b.torque) <= 1e-8
