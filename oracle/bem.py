@@ -34,13 +34,17 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def hat_double_layer(x: np.ndarray, tri: np.ndarray, exclude: np.ndarray | None = None) -> np.ndarray:
+def hat_double_layer(x: np.ndarray, tri: np.ndarray, exclude: np.ndarray | None = None,
+                     log1p_edges: bool = False) -> np.ndarray:
     """I[p, t, k] = int_t phi_k(y) (x_p - y).n_t / |x_p - y|^3 dS_y.
 
     x: (P, 3) targets; tri: (T, 3, 3) vertices ordered counter-clockwise seen
     from the outside (normal (y2-y1) x (y3-y1) outward).  exclude: optional
     (P, T) mask of pairs known to be coplanar (x_p a vertex of t), which give
-    0 whatever rounding does to h."""
+    0 whatever rounding does to h.  log1p_edges: evaluate P_e = ln((a+s)/(a-s)),
+    a = eta_k + eta_k+1, as log1p(2s/(a-s)) -- the same value; far from the
+    triangle the ratio is 1 + O(s/r) and its plain logarithm loses a factor r/s
+    of relative accuracy."""
     x = np.asarray(x, dtype=np.float64)[:, None, :]          # (P, 1, 3)
     y = np.asarray(tri, dtype=np.float64)[None, :, :, :]      # (1, T, 3, 3)
     y1, y2, y3 = y[..., 0, :], y[..., 1, :], y[..., 2, :]
@@ -71,7 +75,10 @@ def hat_double_layer(x: np.ndarray, tri: np.ndarray, exclude: np.ndarray | None 
         nu = np.cross(e, nrm) / s[..., None]
         ea, eb = eta[k], eta[(k + 1) % 3]
         with np.errstate(divide="ignore", invalid="ignore"):
-            P = np.log((ea + eb + s) / (ea + eb - s))
+            if log1p_edges:
+                P = np.log1p(2.0 * s / (ea + eb - s))
+            else:
+                P = np.log((ea + eb + s) / (ea + eb - s))
         P = np.where(coplanar, 0.0, P)
         edge_sum = edge_sum + nu * P[..., None]
     out = np.empty(h.shape + (3,))
