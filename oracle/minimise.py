@@ -90,6 +90,27 @@ class BBState:
     k: int = 0                    # BB steps taken (parity for "alternate")
 
 
+# Adaptive rule constants (Sec. 2.3 names the rule, not its constants; see the
+# module docstring): kappa shrinks by KAPPA_SHRINK when the short step tau^2 is
+# chosen, grows by KAPPA_GROW otherwise; the short step is the smallest of the
+# last m_alpha values of tau^2 (TAU2_PICK).
+KAPPA_SHRINK = 0.9
+KAPPA_GROW = 1.1
+TAU2_PICK = min
+
+
+def armijo_accepts(phit: float, E_ref: float, c1: float, tau: float, gg: float) -> bool:
+    """Sufficient decrease along the curve Y(tau) of Eq. (8): dE/dtau at 0 is
+    -sum |g|^2, so the Armijo test is E(tau) <= E_ref - c1 tau sum |g|^2."""
+    return phit <= E_ref - c1 * tau * gg
+
+
+def nonmonotone_rejects(phit: float, hist: list, memory: int) -> bool:
+    """Sec. 2.3: a BB trial is rejected iff its energy is strictly larger than
+    every one of the last `memory` accepted energies (their maximum)."""
+    return phit > max(hist[-memory:])
+
+
 def next_bb_tau(s, y, tau_restart: float, st: BBState, rule: StepRule) -> float:
     steps = bb_steps(s, y)
     k = st.k
@@ -107,11 +128,11 @@ def next_bb_tau(s, y, tau_restart: float, st: BBState, rule: StepRule) -> float:
         st.tau2.append(t2)
         del st.tau2[:-rule.m_alpha]
         if t2 / t1 <= st.kappa:
-            tau = min(st.tau2)
-            st.kappa *= 0.9
+            tau = TAU2_PICK(st.tau2)
+            st.kappa *= KAPPA_SHRINK
         else:
             tau = t1
-            st.kappa *= 1.1
+            st.kappa *= KAPPA_GROW
     return float(min(max(tau, rule.tau_min), rule.tau_max))
 
 
@@ -167,12 +188,11 @@ def minimise(prob: CubeProblem, m0: np.ndarray, h_ext, tol: float = 1e-6, max_it
         evals += 1
         phit = et.E / E0
         if searching:
-            accept = phit <= E_ref - rule.c1 * tau * gg
+            accept = armijo_accepts(phit, E_ref, rule.c1, tau, gg)
         else:
-            emax = max(hist[-rule.memory:])
-            accept = not (phit > emax)
+            accept = not nonmonotone_rejects(phit, hist, rule.memory)
             if not accept:
-                searching, E_ref = True, emax
+                searching, E_ref = True, max(hist[-rule.memory:])
                 line_searches += 1
                 backtracks = 0
         if not accept:

@@ -8,7 +8,10 @@ solid angle, BB1 and BB2 swapped, a wrong cofactor, reflex dihedral angles
 folded into [0, pi]; and in the hierarchical-matrix boundary operator a cluster
 that loses a node, admissibility by the larger diameter or without the hat
 supports, a truncation one rank short, a wrong residual sign in the cross
-approximation, and low-rank products added into the wrong rows; and in the
+approximation, and low-rank products added into the wrong rows; in the step
+control the kappa factors of the adaptive BB rule swapped, the largest instead
+of the smallest remembered tau^2, and the Armijo test with a flipped sign or
+without c1; and in the
 space-transformation boundary a shell tensor built from J instead of its
 inverse, one without the |det J| factor, and a shell left untransformed.
 """
@@ -280,3 +283,30 @@ def test_shell_left_untransformed(monkeypatch):
     from oracle import spacetrans as st
     monkeypatch.setattr(st, "shell_tensor", lambda x, c, R1, R2: np.broadcast_to(np.eye(3), (len(x), 3, 3)).copy())
     _caught(spins.test_potential_converges_to_the_box_solution_inside_and_outside, _shells(spins.LEVELS))
+
+
+# --- step control (Sec. 2.3) --------------------------------------------------
+
+def test_kappa_factors_swapped(monkeypatch):
+    import oracle.minimise as om
+    monkeypatch.setattr(om, "KAPPA_SHRINK", 1.1)
+    monkeypatch.setattr(om, "KAPPA_GROW", 0.9)
+    _caught(pins.test_adaptive_bb_rule_hand_sequence)
+
+
+def test_tau2_memory_max_for_min(monkeypatch):
+    import oracle.minimise as om
+    monkeypatch.setattr(om, "TAU2_PICK", max)
+    _caught(pins.test_adaptive_bb_rule_hand_sequence)
+
+
+def test_armijo_sign_flipped(monkeypatch):
+    import oracle.minimise as om
+    monkeypatch.setattr(om, "armijo_accepts", lambda phit, E_ref, c1, tau, gg: phit <= E_ref + c1 * tau * gg)
+    _caught(pins.test_first_step_armijo_boundary)
+
+
+def test_armijo_without_c1(monkeypatch):
+    import oracle.minimise as om
+    monkeypatch.setattr(om, "armijo_accepts", lambda phit, E_ref, c1, tau, gg: phit <= E_ref - tau * gg)
+    _caught(pins.test_first_step_armijo_boundary)

@@ -541,3 +541,117 @@ def test_far_field_accuracy_of_the_closed_form():
         # form further out is the O((r/s)^2) cancellation of the solid-angle and edge terms
         gain = {5.0: 0.0, 20.0: 10.0, 60.0: 5.0, 150.0: 2.0}[dist]
         assert e_stable * gain <= e_plain, (dist, e_plain, e_stable)
+
+
+# --- step control of Sec. 2.3, pinned by hand-computed sequences ------------------
+
+# (s, y) pairs on the diagonal quadratic A = diag(2, 8, 32) (y = A s), except the
+# fifth, where s.y < 0.  The expected step, kappa and tau^2 memory after each
+# pair follow from the reading of the adaptive rule (kappa_0 = 1/2; push tau^2
+# into a memory of the last 3; tau^2/tau^1 <= kappa -> min of the memory and
+# kappa * 0.9, else tau^1 and kappa * 1.1; s.y <= 0 -> the restart step, memory
+# and kappa untouched), worked out by hand:
+#   1  s.s=1 s.y=2 y.y=4        tau1=1/2  tau2=1/2    ratio 1     > .5     -> 1/2
+#   2  s.s=2 s.y=10 y.y=68      tau1=1/5  tau2=5/34   ratio 25/34 > .55    -> 1/5
+#   3  s.s=2 s.y=40 y.y=1088    tau1=1/20 tau2=5/136  ratio 25/34 > .605   -> 1/20
+#   4  s.s=2 s.y=34 y.y=1028    tau1=1/17 tau2=17/514 ratio 289/514 <= .6655
+#                               -> min(5/34, 5/136, 17/514) = 17/514
+#   5  s.y = -2 < 0             -> restart step (0.25)
+#   6, 7  as 1                  ratio 1 > kappa        -> 1/2, 1/2
+#   8  s.s=5 s.y=40 y.y=1040    tau1=1/8  tau2=1/26   ratio 4/13 <= .7247
+#                               -> min(1/2, 1/2, 1/26) = 1/26 (17/514 has left the memory)
+_BB_SEQ = [
+    ((1, 0, 0), (2, 0, 0), 1 / 2, 0.55, [1 / 2]),
+    ((1, 1, 0), (2, 8, 0), 1 / 5, 0.605, [1 / 2, 5 / 34]),
+    ((0, 1, 1), (0, 8, 32), 1 / 20, 0.6655, [1 / 2, 5 / 34, 5 / 136]),
+    ((1, 0, 1), (2, 0, 32), 17 / 514, 0.59895, [5 / 34, 5 / 136, 17 / 514]),
+    ((1, 0, 0), (-2, 0, 0), 0.25, 0.59895, [5 / 34, 5 / 136, 17 / 514]),
+    ((1, 0, 0), (2, 0, 0), 1 / 2, 0.658845, [5 / 136, 17 / 514, 1 / 2]),
+    ((1, 0, 0), (2, 0, 0), 1 / 2, 0.7247295, [17 / 514, 1 / 2, 1 / 2]),
+    ((2, 0, 1), (4, 0, 32), 1 / 26, 0.65225655, [1 / 2, 1 / 2, 1 / 26]),
+]
+
+
+def test_adaptive_bb_rule_hand_sequence():
+    """The adaptive BB rule of Sec. 2.3 (reading c4/c4'): exact step, kappa and
+    tau^2 memory after each of eight hand-computed (s, y) pairs."""
+    from oracle.minimise import BBState, StepRule, next_bb_tau
+    rule = StepRule()
+    st = BBState(kappa=rule.kappa0)
+    for k, (s, y, tau, kappa, mem) in enumerate(_BB_SEQ, start=1):
+        got = next_bb_tau(np.array([s], float), np.array([y], float), 0.25, st, rule)
+        assert got == tau, (k, got, tau)
+        assert math.isclose(st.kappa, kappa, rel_tol=1e-14), (k, st.kappa, kappa)
+        assert st.tau2 == mem, (k, st.tau2, mem)
+
+
+def test_adaptive_bb_rule_clamp():
+    """The step is clamped to [tau_min, tau_max] after the rule has chosen it."""
+    from oracle.minimise import BBState, StepRule, next_bb_tau
+    for rule, expect in ((StepRule(tau_min=0.04), [1 / 2, 1 / 5, 1 / 20, 0.04, 0.25, 1 / 2, 1 / 2, 0.04]),
+                         (StepRule(tau_max=0.3), [0.3, 1 / 5, 1 / 20, 17 / 514, 0.25, 0.3, 0.3, 1 / 26])):
+        st = BBState(kappa=rule.kappa0)
+        got = [next_bb_tau(np.array([s], float), np.array([y], float), 0.25, st, rule)
+               for s, y, *_ in _BB_SEQ]
+        assert got == expect, (got, expect)
+
+
+class _OneSpin:
+    """One magnetic moment with E(m) = m_x (unit E0 = 1): grad = (1, 0, 0).
+    From m0 = +z, H = -m x grad = (0, -1, 0), sum |g|^2 = 1, and the Cayley
+    curve of Eq. (8) is the rotation by 2 atan(tau/2) towards -x, so
+    E(tau) = -tau / (1 + tau^2/4) exactly."""
+    E0 = 1.0
+
+    def evaluate(self, m, h_ext):
+        from oracle.micromag import Evaluation
+        grad = np.array([[1.0, 0.0, 0.0]])
+        z = np.zeros(1)
+        return Evaluation(E=float(m[0, 0]), terms={}, h=-grad, grad=grad, torque=1.0, u1=z, u2=z, uT=z)
+
+
+def test_first_step_armijo_boundary():
+    """First step of Sec. 2.3 by Armijo line search: the trial tau0 = 1/max|H| = 1
+    meets E(tau) <= E0 - c1 tau sum|g|^2 iff c1 <= 1/(1 + 1/4) = 0.8.  Just below
+    that c1 the step tau0 is taken (m1 = (-4/5, 0, 3/5)); just above it tau0 is
+    rejected and the halved step tau0/2 is taken (m1 = (-8/17, 0, 15/17))."""
+    from oracle.minimise import StepRule
+    m0 = np.array([[0.0, 0.0, 1.0]])
+    r = minimise(_OneSpin(), m0, None, tol=0.0, max_iter=1, rule=StepRule(c1=0.8 * (1 - 1e-9)))
+    assert r.evaluations == 2 and r.iterations == 1
+    assert np.abs(r.m - np.array([[-0.8, 0.0, 0.6]])).max() < 1e-15
+    r = minimise(_OneSpin(), m0, None, tol=0.0, max_iter=1, rule=StepRule(c1=0.8 * (1 + 1e-9)))
+    assert r.evaluations == 3 and r.iterations == 1
+    assert np.abs(r.m - np.array([[-8 / 17, 0.0, 15 / 17]])).max() < 1e-15
+
+
+def _gg_and_torque(p, m, h):
+    ev = p.evaluate(m, h)
+    # g = m x (-m x grad) is the tangential part of grad for |m| = 1
+    g = ev.grad - np.sum(m * ev.grad, axis=1, keepdims=True) * m
+    return float(np.sum(g * g)), ev.torque
+
+
+def test_grad_tol_stop():
+    """The paper's stop test (Sec. 3.1) sum|g|^2 < tol_g: the minimiser stops at
+    the first iterate whose sum|g|^2 (recomputed here from the energy gradient
+    as its tangential part) is below tol_g.  The bars are chosen at an iterate
+    k where the torque reaches a new minimum but sum|g|^2 does not, so the
+    torque test stops at k and the sum|g|^2 test at an earlier iterate."""
+    p = _problem(2)
+    m0 = _rand_unit(p.mesh.N)
+    h = np.array([0.3, 0.0, -1.5])
+    K = 60
+    full = minimise(p, m0, h, tol=0.0, max_iter=K, record=range(K + 1))
+    seq = [_gg_and_torque(p, m, h) for _, m in full.trajectory]
+    ks = [k for k in range(1, len(seq))
+          if seq[k][1] * (1 + 1e-6) < min(s[1] for s in seq[:k]) and seq[k][0] > min(s[0] for s in seq[:k])]
+    assert ks, "no iterate where the two stop tests disagree"
+    k = ks[-1]
+    G, T = seq[k][0] * (1 + 1e-9), seq[k][1] * (1 + 1e-9)
+    j = next(i for i, s in enumerate(seq) if s[0] < G)
+    assert j < k
+    r = minimise(p, m0, h, tol=1e-30, grad_tol=G)
+    assert r.status == OK and r.iterations == j
+    r2 = minimise(p, m0, h, tol=T)
+    assert r2.status == OK and r2.iterations == k
