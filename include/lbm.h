@@ -307,10 +307,28 @@ int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);
  * stream capture.  All calls share the array, and each call overwrites it
  * (the parts that must start from zero -- the potentials, counters and the
  * barrier word -- are cleared by every call): calls whose work overlaps on the
- * GPU, e.g. from two streams or two contexts on one device, race. */
+ * GPU, e.g. from two streams or two contexts on one device, race.
+ * Failures inside the queued work cannot be returned by this call (it does
+ * not wait): when a device wait ran out (LBM_E_TIMEOUT in the other calls) or
+ * the field is not finite (LBM_E_NAN), all five energies in d_energy and
+ * d_h[0] are set to NaN, so a caller that reads either sees the failure.  The
+ * BEM product uses its default launch shape (never an autotuned one), so the
+ * result does not depend on earlier calls. */
 int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_material* mat, const double h_ext[3],
                          const lbm_solve_opts* opt, const double* d_m, double* d_h, double* d_u,
                          double* d_energy);
+
+/* ---- device waits ------------------------------------------------------------
+ * Every device-side wait of this context's kernels (the grid barrier of the
+ * cooperative potential solves) gives up after a time limit, sets the
+ * context's error word and returns; the call that queued the work then
+ * returns LBM_E_TIMEOUT and the context stays usable.  The paper has no
+ * counterpart.  seconds: the limit (0 restores the default of 2 s; at most
+ * 60).  unreachable != 0 is a test hook: every grid barrier then waits for one
+ * arrival more than the grid makes, so each wait runs out after `seconds`
+ * (no fault, no trap) -- it exercises the error path; pass 0 to clear it.
+ * Waits for the queued work first.  Returns LBM_E_INVALID for a bad argument. */
+int lbm_set_wait_limit(lbm_ctx* ctx, double seconds, int32_t unreachable);
 
 /* ---- serving: continuous batching of minimisation requests ---------------------
  * A worker thread of the context owns the device while serving.  Requests

@@ -108,6 +108,7 @@ SIGNATURES = [
     ("lbm_profile_read", C.c_int, [_P, C.POINTER(ProfileStats), C.c_int32]),
     ("lbm_evaluate_noalloc", C.c_int, [_P, _I64, C.POINTER(Material), _DP, C.POINTER(SolveOpts),
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("lbm_set_wait_limit", C.c_int, [_P, C.c_double, C.c_int32]),
     ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
     ("lbm_serve_start", C.c_int, [_P, C.POINTER(ServeOpts)]),
     ("lbm_submit", C.c_int, [_P, C.POINTER(Request), C.POINTER(_I64)]),
@@ -276,6 +277,12 @@ class Context:
                                           C.byref(opts) if opts else None, C.c_void_p(d_m),
                                           C.c_void_p(d_h or None), C.c_void_p(d_u or None),
                                           C.c_void_p(d_energy or None)))
+
+    def set_wait_limit(self, seconds: float, unreachable: bool = False):
+        """lbm_set_wait_limit: the device-wait limit of this context's kernels
+        (0: the default 2 s); `unreachable` makes every grid barrier's wait run
+        out (a test of the timeout path)."""
+        _check(lib().lbm_set_wait_limit(self._h, float(seconds), 1 if unreachable else 0))
 
     # -- serving (continuous batching) ---------------------------------------
     def serve_start(self, **kw):

@@ -1345,10 +1345,18 @@ __global__ void k_noalloc_setup(InstState* st, InstConst* ic, InstConst c) {
     *ic = c;
 }
 
-__global__ void k_noalloc_energy(const InstState* st, const InstConst* ic, double* e) {
+// Energies of the evaluated point; a failed evaluation (a device wait that ran
+// out: the error word; a non-finite field: status LBM_E_NAN) is made visible
+// without a host round trip: NaN in every energy and in the first field value.
+__global__ void k_noalloc_finish(const InstState* st, const InstConst* ic, const int* err, double* e, double* h0) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int k = 0; k < 4; ++k) e[k] = st->terms[k] * ic->Eunit;
-    e[4] = st->E * ic->Eunit;
+    const bool bad = err[0] != 0 || st->status == 4;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (e) {
+        for (int k = 0; k < 4; ++k) e[k] = bad ? nan : st->terms[k] * ic->Eunit;
+        e[4] = bad ? nan : st->E * ic->Eunit;
+    }
+    if (h0 && bad) h0[0] = nan;
 }
 
 }  // namespace
@@ -1356,6 +1364,7 @@ __global__ void k_noalloc_energy(const InstState* st, const InstConst* ic, doubl
 extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_material* mat, const double h_ext[3],
                                     const lbm_solve_opts* opt, const double* d_m, double* d_h, double* d_u,
                                     double* d_energy) {
+    LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M || !mat || !h_ext || !d_m) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: bad argument");
     if ((size_t)M->N > NOALLOC_MAX_NODES || (size_t)M->nb > NOALLOC_MAX_SURFACE)
@@ -1367,8 +1376,8 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     if (opt) o = *opt; else lbm_default_opts(&o, LBM_FP64);
     int rc = check_opts(o);
     if (rc) return rc;
-    CK(cudaSetDevice(ctx->device));
     if (ctx->device < 0 || ctx->device >= 64) return fail(LBM_E_INVALID, "device index out of range");
+    CK(cudaSetDevice(ctx->device));
     double* base;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -1402,7 +1411,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     InstState* st = (InstState*)take((sizeof(InstState) + 7) / 8);
     InstConst* ic = (InstConst*)take((sizeof(InstConst) + 7) / 8);
     unsigned* bar = (unsigned*)take(1);
-    int* err = (int*)take(1);
+    int* err = (int*)take(2);   // error word, wait limit, test hook (as the context's)
     unsigned long long* sweeps = (unsigned long long*)take(4);
     if (off > NOALLOC_DOUBLES) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: static scratch too small");
     const size_t need_part = (size_t)4 * ctx->num_sms * NQ > pcg_part_elems(ctx->num_sms, 1)
@@ -1413,7 +1422,8 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     CK(cudaMemsetAsync(U1, 0, sizeof(double) * 2 * N, s));
     CK(cudaMemsetAsync(U2, 0, sizeof(double) * 2 * N, s));
     CK(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
-    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
+    CK(cudaMemcpyAsync(err + 1, ctx->err + 1, 2 * sizeof(int), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(sweeps, 0, 4 * sizeof(unsigned long long), s));
     CK(cudaMemcpyAsync(m, d_m, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
     const double Kd = mat->Js * mat->Js / (2.0 * MU0);
@@ -1465,13 +1475,27 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     field_eval<double>(L, mv, V, o.demag);
     decide<double>(L, mv, V, so, field_blocks(L, mv, 1));
     if (d_h || d_u) unpack_field<double>(L, mv, V, d_h, d_u);
-    if (d_energy) {
-        k_noalloc_energy<<<1, 1, 0, s>>>(st, ic, d_energy);
+    if (d_energy || d_h) {
+        k_noalloc_finish<<<1, 1, 0, s>>>(st, ic, err, d_energy, d_h);
         ctx->launches += 1;
     }
     CK(cudaGetLastError());
     return LBM_OK;
+    LBM_CATCH
 }
+
+extern "C" int lbm_set_wait_limit(lbm_ctx* ctx, double seconds, int32_t unreachable) {
+    LBM_TRY
+    if (!ctx || !(seconds >= 0.0) || seconds > 60.0) return fail(LBM_E_INVALID, "lbm_set_wait_limit: bad argument");
+    CK(cudaSetDevice(ctx->device));
+    const int cfg[2] = {(int)llround(seconds * 1e3), unreachable ? 1 : 0};
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->err + 1, cfg, sizeof cfg, cudaMemcpyHostToDevice));
+    return LBM_OK;
+    LBM_CATCH
+}
+
+
 
 // ============================================================================
 // Serving: continuous batching of minimisation requests.

@@ -212,4 +212,11 @@ int bem_product_tc(const Launch& L, int nb, const float* A32, const float* A32T,
 int field_blocks(const Launch& L, const MeshView& M, int B);
 size_t pcg_part_elems(int num_sms, int B);
 
+// Kernel attributes are per device: set a kernel's dynamic shared-memory limit
+// once per (kernel, current device), under a lock (several host threads may
+// launch); with `blocks_per_sm` also return the kernel's occupancy at `threads`
+// threads and `smem` bytes, cached the same way.
+cudaError_t kernel_smem_attr(const void* fn, int smem_limit, int threads = 0, size_t smem = 0,
+                             int* blocks_per_sm = nullptr);
+
 }  // namespace lbm

@@ -84,8 +84,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // Software grid barrier for cooperative launches.  `count` must be zero at
 // launch; each block's thread 0 keeps its own epoch.  The wait gives up after
-// 2 s (or when another block has flagged an error), sets DEV_ERR_TIMEOUT and
-// returns false; callers then leave the kernel.
+// err[1] milliseconds (2 s when err[1] is 0), or when another block has flagged
+// an error, sets DEV_ERR_TIMEOUT and returns false; callers then leave the
+// kernel.  err[2] is a test hook: when nonzero every barrier waits for one
+// arrival more than the grid makes, so the wait runs out by design (the error
+// path is then exercised without any fault).  err points at >= 4 ints.
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -95,7 +98,10 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned nblocks, uns
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1u;
-        const unsigned target = epoch * nblocks;
+        const int lim_ms = *(volatile int*)(err + 1);
+        const unsigned extra = *(volatile int*)(err + 2) ? 1u : 0u;
+        const uint64_t limit = lim_ms > 0 ? (uint64_t)lim_ms * 1000000ull : 2000000000ull;
+        const unsigned target = epoch * nblocks + extra;
         // release: the block's writes (ordered before this by the barrier above)
         // become visible to every block whose acquire load sees the increment
         red_release_add(count, 1u);
@@ -105,7 +111,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned nblocks, uns
         while (ld_acquire_u32(count) < target) {
             if ((++spins & 31u) == 0u) {
                 if (*(volatile int*)err) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > 2000000000ull) { atomicOr(err, DEV_ERR_TIMEOUT); ok = 0; break; }
+                if (globaltimer_ns() - t0 > limit) { atomicOr(err, DEV_ERR_TIMEOUT); ok = 0; break; }
             }
         }
         s_ok = ok;   // the acquire loads above order the other blocks' writes before the barrier below

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <type_traits>
 
@@ -30,6 +31,33 @@ constexpr int PCG_SINGLE_THREADS = 512;  // one-CTA variant for small batches
 constexpr int FIELD_THREADS = 256;
 constexpr int MAXR = 16;                 // row length served by the unrolled gather (Kuhn rows: 15)
 constexpr long long SINGLE_CTA_MAX_WORK = 24576;   // N * B up to which one CTA solves
+
+cudaError_t kernel_smem_attr(const void* fn, int smem_limit, int threads, size_t smem, int* blocks_per_sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, size_t>, int> occ_cache;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count({fn, dev})) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+        if (e != cudaSuccess) return e;
+        done.insert({fn, dev});
+    }
+    if (blocks_per_sm) {
+        const auto key = std::make_tuple(fn, dev, threads, smem);
+        auto it = occ_cache.find(key);
+        if (it == occ_cache.end()) {
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+            if (e != cudaSuccess) return e;
+            it = occ_cache.emplace(key, occ).first;
+        }
+        *blocks_per_sm = it->second;
+    }
+    return cudaSuccess;
+}
 
 template <typename T, bool CG> __device__ __forceinline__ T ld_vec(const T* p) {
     if constexpr (CG) return __ldcg(p);
@@ -876,17 +904,11 @@ static cudaError_t launch_pcg(const Launch& L, const MeshView& M, PcgArgs<T>& a,
     const int G = C / VEC, RB = bd / G;
     const int nrow_red = (G <= 32 && (32 % G) == 0) ? (bd >> 5) : RB;
     const size_t smem = sizeof(double) * (4 * (size_t)nrow_red * C + 9 * (size_t)C) + sizeof(int) * 5 * C;
-    static bool attr_set = false;
-    static int occ = 0;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_pcg<T, SINGLE, VEC, GEN, MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (!SINGLE) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg<T, SINGLE, VEC, GEN, MP>, bd, 200 * 1024);
-            if (occ < 1) occ = 1;
-            if (occ > 1) occ = 1;   // the partials buffer holds one block per SM
-        }
-        attr_set = true;
-    }
+    const void* fn = (const void*)k_pcg<T, SINGLE, VEC, GEN, MP>;
+    int occ = 1;
+    cudaError_t ea = kernel_smem_attr(fn, 200 * 1024, bd, 200 * 1024, SINGLE ? nullptr : &occ);
+    if (ea != cudaSuccess) return ea;
+    occ = 1;   // the partials buffer holds one block per SM
     void* args[] = {&a};
     if (SINGLE) return cudaLaunchKernel((void*)k_pcg<T, SINGLE, VEC, GEN, MP>, dim3(1), dim3(bd), args, smem, L.stream);
     int nblk = (M.N + RB - 1) / RB;
@@ -1065,12 +1087,14 @@ static std::map<std::tuple<int, int, int, int>, int> g_chunks;
 template <typename F>
 static int tuned_chunks(const Launch& L, int nb, int key_a, int key_b, F&& launch_with) {
     const auto key = std::make_tuple(nb, key_a, key_b, L.num_sms);
+    // without tuning (a call that must not wait) the default shape, whatever an
+    // earlier call tuned: its summation order then does not depend on history
+    if (!L.tune) return bem_chunks(nb, L.num_sms);
     {
         std::lock_guard<std::mutex> lk(g_chunks_mu);
         auto it = g_chunks.find(key);
         if (it != g_chunks.end()) return it->second;
     }
-    if (!L.tune) return bem_chunks(nb, L.num_sms);
     int best = bem_chunks(nb, L.num_sms);
     float best_ms = -1.f;
     cudaEvent_t e0, e1;
@@ -1268,12 +1292,8 @@ template <typename T>
 void field_eval(const Launch& L, const MeshView& M, const BatchView<T>& V, int demag) {
     const int nblk = field_blocks(L, M, V.B);
     const size_t smem = sizeof(double) * Q_COUNT * (FIELD_THREADS + V.B);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_field<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        cudaFuncSetAttribute(k_field<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        attr_set = true;
-    }
+    kernel_smem_attr((const void*)k_field<T, false>, 96 * 1024);
+    kernel_smem_attr((const void*)k_field<T, true>, 96 * 1024);
     if (M.gen) k_field<T, true><<<nblk, FIELD_THREADS, smem, L.stream>>>(M, V, demag);
     else k_field<T, false><<<nblk, FIELD_THREADS, smem, L.stream>>>(M, V, demag);
     *L.launches += 1;

@@ -394,11 +394,7 @@ int bem_product_tc(const Launch& L, int nb, const float* A32, const float* A32T,
     float* xhi = scratch;
     float* xlo = scratch + (size_t)C * ldp;
     float* ypart = scratch + (size_t)2 * C * ldp;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tc::k_bem_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-        attr = true;
-    }
+    if (kernel_smem_attr((const void*)tc::k_bem_tc, tc::SMEM_BYTES) != cudaSuccess) return -3;
     const int total = nb * C;
     tc::k_tc_split<T><<<(total + 255) / 256, 256, 0, L.stream>>>(ub_in, nb, C, ldp, xhi, xlo);
     const int mt = (nb + tc::BM - 1) / tc::BM, nkb = (nb + tc::BK - 1) / tc::BK;

@@ -7,8 +7,10 @@ nothing here touches the CUDA path.  Outputs JSON files beside this script:
                      (64 instances on the 30^3-cell cube, seed 4)
   sweep_n20.json     the hysteresis sweep of the 20^3-cell cube (seed 2),
                      +8 -> -8 T in 0.1 T steps, warm-started
+  sphere_paper.json  the minimisation on the paper-size 20 nm sphere (87 880
+                     tetrahedra) from a random state (seed 8) at -3 T along z
 
-Usage: python tests/golden/make_golden.py [batched|sweep] [--procs P]
+Usage: python tests/golden/make_golden.py [batched|sweep|sphere] [--procs P]
 """
 from __future__ import annotations
 
@@ -65,6 +67,22 @@ def sweep():
               open(os.path.join(HERE, "sweep_n20.json"), "w"), indent=1)
 
 
+def sphere():
+    from oracle.micromag import mesh_problem
+    from synth.inputs import m_random_sphere
+    from synth.meshes import ball_mesh
+    xyz, tets = ball_mesh(26, 20e-9)
+    p = mesh_problem(xyz, tets, JS_T, A_JM, K1_JM3, [0.0, 0.0, 1.0])
+    m0 = m_random_sphere(p.mesh.N, 8)
+    h = np.array([0.0, 0.0, -3.0])
+    t0 = time.time()
+    r = minimise(p, m0, h, tol=1e-6, max_iter=20000)
+    json.dump(dict(mesh="ball_mesh(26, 20e-9)", seed=8, h_ext=h.tolist(), tol=1e-6, status=r.status,
+                   iterations=r.iterations, evaluations=r.evaluations, E=r.E, terms=r.terms,
+                   torque=r.torque, mean_m=p.mean_m(r.m).tolist(), seconds=time.time() - t0),
+              open(os.path.join(HERE, "sphere_paper.json"), "w"), indent=1)
+
+
 if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "batched"
     procs = int(sys.argv[sys.argv.index("--procs") + 1]) if "--procs" in sys.argv else os.cpu_count()
@@ -72,3 +90,5 @@ if __name__ == "__main__":
         batched(procs)
     elif what == "sweep":
         sweep()
+    elif what == "sphere":
+        sphere()

@@ -178,8 +178,9 @@ def test_general_minimisation_batch(ctx, prec):
 
 def test_paper_size_sphere(ctx):
     """The 20 nm sphere with 87 880 tetrahedra (0.77 nm spacing, the paper's
-    grain, Sec. 3.1): sampled BEM rows against the oracle; a mixed-precision
-    minimisation from a random state converges and agrees with FP64 to 1e-6."""
+    grain, Sec. 3.1): sampled BEM rows against the oracle; mixed-precision and
+    FP64 minimisations from a random state converge and their energies agree
+    with the oracle's minimisation (golden, written by the oracle) to 1e-6."""
     xyz, tets = ball_mesh(26, 20e-9)
     assert tets.shape[0] == 87880
     o = tet_mesh(xyz, tets)
@@ -203,6 +204,12 @@ def test_paper_size_sphere(ctx):
         inst.destroy()
     scale = (JS_T ** 2 / (2 * 4e-7 * np.pi)) * o.ops.V.sum()
     assert abs(out[lbm.LBM_MIXED] - out[lbm.LBM_FP64]) / max(abs(out[lbm.LBM_FP64]), scale) < 1e-6
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "sphere_paper.json")))
+    assert g["status"] == 0 and g["seed"] == 8 and g["h_ext"] == list(h_ext)
+    for prec, E in out.items():
+        assert abs(E - g["E"]) / max(abs(g["E"]), scale) < 1e-6, (prec, E, g["E"])
     ctx.mesh_destroy(mesh)
 
 
