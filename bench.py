@@ -67,6 +67,8 @@ def parse():
                          "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix)")
     ap.add_argument("--n", type=int, default=80, help="cells per side of the large workload")
     ap.add_argument("--max-iter", type=int, default=100000, help="iteration cap of the large workload")
+    ap.add_argument("--pcg-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="potential-solve kernel (lbm_solve_opts.pcg_kernel): 0 choose, 1 grid-wide, 2 clusters")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals/s (0: 0.8 x calibrated capacity)")
     return ap.parse_args()
@@ -382,7 +384,7 @@ def run_ours(args, ws, rank, local):
     inst.set_field(fields)
     m0_host = np.stack([i.m0 for i in insts])
     m0_dev = torch.from_numpy(m0_host).to(f"cuda:{local}")
-    opts = lbm.default_opts(prec)
+    opts = lbm.default_opts(prec, pcg_kernel=args.pcg_kernel)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
     def step():

@@ -112,6 +112,14 @@ typedef struct {
                                FP32 phase of a mixed run then hands the instance to the
                                FP64 phase (which ignores it).  0 = never.  Default 200
                                for the mixed precisions, 0 for LBM_FP64 */
+    int32_t pcg_kernel;     /* potential-solve kernel: 0 (default) chooses; 1 the
+                               grid-wide kernel (one CTA for small work, else a
+                               cooperative grid); 2 prefers one thread-block cluster
+                               per group of systems (taken when the batch has a
+                               multiple of 4, at least 16 instances, FP32 work vectors
+                               and z of a cluster's systems fits its shared memory;
+                               otherwise as 1).  0 takes 2 where it qualifies.
+                               Results agree to rounding, not bit for bit */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -289,7 +297,7 @@ int lbm_profile_read(lbm_ctx* ctx, lbm_profile_stats* out, int32_t reset);
  * touching the CUDA allocator is not allowed.  It computes what lbm_evaluate
  * computes for one instance in FP64 (energy terms, effective field, forward
  * potentials at the given m) but keeps every intermediate vector in one
- * fixed device array built into the library (about 4.9 MB on every device that
+ * fixed device array built into the library (about 5.0 MB on every device that
  * loads it, held until the process exits).  It calls no cudaMalloc or cudaFree.
  *
  *   mesh      a mesh (lbm_mesh_cube or lbm_mesh_upload) with at most 16384

@@ -36,7 +36,8 @@ class SolveOpts(C.Structure):
                 ("m_alpha", C.c_int32), ("tau_min", C.c_double), ("tau_max", C.c_double),
                 ("demag", C.c_int32), ("check_every", C.c_int32), ("switch_tol", C.c_double),
                 ("cg_tol_polish", C.c_double), ("cg_mixed_iter", C.c_int32), ("bb_rule", C.c_int32),
-                ("method", C.c_int32), ("omega", C.c_double), ("stall_iters", C.c_int32)]
+                ("method", C.c_int32), ("omega", C.c_double), ("stall_iters", C.c_int32),
+                ("pcg_kernel", C.c_int32)]
 
 
 class ProfileStats(C.Structure):

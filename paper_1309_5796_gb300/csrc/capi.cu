@@ -203,7 +203,7 @@ void prof_harvest(lbm_ctx* ctx) {
 // Byte offsets of the per-instance arrays inside one allocation; every array
 // starts on a 256-byte boundary (the PCG reads 8- and 16-byte vectors).
 struct VecLayout {
-    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, m32, total;
+    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, m32, bvec, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -226,6 +226,7 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.ub_out = take(tsize * nb * C);
     L.bem_part = take(8 * 32 * nb);   // 32 x nb partial sums of the transposed product
     L.m32 = tsize == 4 ? take(4 * N * 3 * B) : 0;
+    L.bvec = take(8 * N * B);
     L.total = o;
     return L;
 }
@@ -250,6 +251,7 @@ BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool w
     v.ub_out = (T*)(base + L.ub_out);
     v.bem_part = (T*)(base + L.bem_part);
     v.m32 = sizeof(T) == 4 ? (float*)(base + L.m32) : nullptr;
+    v.bvec = (double*)(base + L.bvec);
     v.part = I.part;
     v.st = I.st;
     v.ic = I.ic;
@@ -348,7 +350,8 @@ int check_opts(const lbm_solve_opts& o) {
         o.m_alpha > MALPHA_MAX || o.max_backtracks < 0 || o.cg_max_iter < 1 || !(o.cg_tol > 0) ||
         o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
         !(o.cg_tol_polish > 0) || o.bb_rule < 0 || o.bb_rule > 3 || o.method < 0 || o.method > 1 ||
-        (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)) || o.stall_iters < 0)
+        (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)) || o.stall_iters < 0 || o.pcg_kernel < 0 ||
+        o.pcg_kernel > 2)
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -363,6 +366,7 @@ int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, cons
         const int k64 = sizeof(T) == 8 ? 5 : 0;
         {
             ProfScope ps(ctx, 1 + k64, L.stream);
+            rhs_eval<T>(L, mv, V);
             e = pcg_solve<T>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, o.cg_mixed_iter != 0);
         }
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
@@ -427,6 +431,7 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
     const auto t0 = std::chrono::steady_clock::now();
     BatchView<T> V = batch_view<T>(ctx, M, *I, evaluate_only && hout);
     Launch L = ctx->launch();
+    L.pcg_kernel = o.pcg_kernel;
     MeshView mv = M.view();
     lbm_solve_opts oo = o;
     if (evaluate_only) oo.max_iter = 0;
@@ -1327,9 +1332,10 @@ constexpr size_t NOALLOC_MAX_SURFACE = 4096;    // surface nodes (24^3 cells: 3 
 constexpr size_t NOALLOC_PART = 16384;          // per-block partial sums (doubles)
 constexpr size_t NOALLOC_FIN = 4096;            // grid-reduction results (doubles)
 // doubles: m, grad phi (2 x 3N each), field (3N), U1, U2, r, z, p, q (2N each),
-// surface in/out (2 nb each), column-split partials (32 nb), partials, fin,
-// plus state, constants and the barrier/error words (a few hundred bytes)
-constexpr size_t NOALLOC_DOUBLES = 27 * NOALLOC_MAX_NODES + 36 * NOALLOC_MAX_SURFACE + NOALLOC_PART + NOALLOC_FIN + 1024;
+// the divergence right-hand side (N), surface in/out (2 nb each), column-split
+// partials (32 nb), partials, fin, plus state, constants and the barrier/error
+// words (a few hundred bytes)
+constexpr size_t NOALLOC_DOUBLES = 28 * NOALLOC_MAX_NODES + 36 * NOALLOC_MAX_SURFACE + NOALLOC_PART + NOALLOC_FIN + 1024;
 
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
@@ -1403,6 +1409,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     double* z = take(2 * N);
     double* p = take(2 * N);
     double* q = take(2 * N);
+    double* bv = take(N);
     double* ubi = take(2 * nb);
     double* ubo = take(2 * nb);
     double* bpart = take(32 * nb);
@@ -1410,7 +1417,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     double* fin = take(NOALLOC_FIN);
     InstState* st = (InstState*)take((sizeof(InstState) + 7) / 8);
     InstConst* ic = (InstConst*)take((sizeof(InstConst) + 7) / 8);
-    unsigned* bar = (unsigned*)take(1);
+    unsigned* bar = (unsigned*)take(2);
     int* err = (int*)take(2);   // error word, wait limit, test hook (as the context's)
     unsigned long long* sweeps = (unsigned long long*)take(4);
     if (off > NOALLOC_DOUBLES) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: static scratch too small");
@@ -1458,6 +1465,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     V.st = st;
     V.ic = ic;
     V.m32 = nullptr;   // FP64 evaluation: no FP32 copy of the trial point
+    V.bvec = bv;
     Launch L{s, ctx->num_sms, bar, err, &ctx->launches, sweeps, fin, 0};
     L.tune = false;   // no waiting inside this call (and it may be captured)
     const MeshView mv = M->view();
@@ -1466,6 +1474,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     const StepOpts so = step_opts(oo);
     trial_update<double>(L, mv, V);
     if (o.demag) {
+        rhs_eval<double>(L, mv, V);
         int e = pcg_solve<double>(L, mv, V, 0, o.cg_tol, o.cg_max_iter, false);
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
         bem_product<double>(L, mv, V);
@@ -1828,6 +1837,7 @@ void serve_loop(Server* Sp) {
         const int maxb = S.opt.max_pcg_blocks;
         for (Group* G : active) {
             Launch L = group_launch(ctx, *G, maxb);
+            L.pcg_kernel = o.pcg_kernel;
             Mesh& M = *ctx->meshes[G->mesh_id];
             G->last_used = now_s();
             bool any32 = false, any64 = false;

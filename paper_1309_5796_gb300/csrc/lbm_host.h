@@ -168,6 +168,7 @@ struct BatchView {
     const InstConst* ic;       // [B]
     double* hout;              // optional [N][3][B] effective field (nullable)
     float* m32 = nullptr;      // FP32 batches: [N][3][B] FP32 copy of the trial point (else null)
+    double* bvec = nullptr;    // [N][B] divergence right-hand side b = G m at the trial point (rhs_eval)
 };
 
 struct Launch {
@@ -180,13 +181,22 @@ struct Launch {
     double* fin;                 // device scratch for grid reductions (>= 4 * 512 doubles)
     int max_blocks;              // cap on the cooperative PCG grid (0: one block per SM)
     bool tune = true;            // launch-shape autotuning allowed (it waits on events)
+    int pcg_kernel = 0;          // 0 choose, 1 grid-wide kernel, 2 prefer clusters (lbm_solve_opts)
 };
 
+// Thread-block-cluster variant of the potential solves (pcg_cluster.cu): 1 when
+// launched (*err its status), 0 when the batch does not qualify.
+template <typename T>
+int pcg_solve_cluster(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
+                      bool mixed_iter, cudaError_t* err);
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
               bool mixed_iter);
 template <typename T>
 void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V);
+// b = G m at every active instance's trial point into V.bvec (before the potential solves)
+template <typename T>
+void rhs_eval(const Launch& L, const MeshView& M, const BatchView<T>& V);
 template <typename T>
 void field_eval(const Launch& L, const MeshView& M, const BatchView<T>& V, int demag);
 template <typename T>

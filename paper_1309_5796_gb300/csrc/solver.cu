@@ -22,357 +22,42 @@
 #include <tuple>
 #include <type_traits>
 
-#include "lbm_host.h"
+#include "solver_common.cuh"
 
 namespace lbm {
 
 constexpr int PCG_THREADS = 512;        // grid-wide (cooperative) variant
 constexpr int PCG_SINGLE_THREADS = 512;  // one-CTA variant for small batches
 constexpr int FIELD_THREADS = 256;
-constexpr int MAXR = 16;                 // row length served by the unrolled gather (Kuhn rows: 15)
 constexpr long long SINGLE_CTA_MAX_WORK = 24576;   // N * B up to which one CTA solves
 
 cudaError_t kernel_smem_attr(const void* fn, int smem_limit, int threads, size_t smem, int* blocks_per_sm) {
     static std::mutex mu;
     static std::map<std::tuple<const void*, int, int, size_t>, int> occ_cache;
-    static std::set<std::pair<const void*, int>> done;
+    static std::map<std::pair<const void*, int>, int> limit_set;   // largest limit set so far
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
-    if (!done.count({fn, dev})) {
+    auto it = limit_set.find({fn, dev});
+    if (it == limit_set.end() || it->second < smem_limit) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
         if (e != cudaSuccess) return e;
-        done.insert({fn, dev});
+        limit_set[{fn, dev}] = smem_limit;
     }
     if (blocks_per_sm) {
         const auto key = std::make_tuple(fn, dev, threads, smem);
-        auto it = occ_cache.find(key);
-        if (it == occ_cache.end()) {
+        auto oc = occ_cache.find(key);
+        if (oc == occ_cache.end()) {
             int occ = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
             if (e != cudaSuccess) return e;
-            it = occ_cache.emplace(key, occ).first;
+            oc = occ_cache.emplace(key, occ).first;
         }
-        *blocks_per_sm = it->second;
+        *blocks_per_sm = oc->second;
     }
     return cudaSuccess;
 }
-
-template <typename T, bool CG> __device__ __forceinline__ T ld_vec(const T* p) {
-    if constexpr (CG) return __ldcg(p);
-    else return *p;
-}
-
-// Deterministic per-instance block reduction of NQV values per thread.  Thread
-// tid holds row lane rl = tid / B of instance b = tid % B; the totals land in
-// out[q*B + b].  Bit q of maxmask selects max instead of sum.
-template <int NQV>
-__device__ __forceinline__ void block_reduce_inst(double (&v)[NQV], double* scratch, double* out, int B, int RB,
-                                                  unsigned maxmask) {
-    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    if (B <= 32 && (32 % B) == 0) {
-        for (int off = 16; off >= B; off >>= 1)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q) {
-                const double o = __shfl_xor_sync(0xffffffffu, v[q], off);
-                v[q] = ((maxmask >> q) & 1u) ? fmax(v[q], o) : v[q] + o;
-            }
-        if (lane < B)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q) scratch[q * bd + warp * B + lane] = v[q];
-        __syncthreads();
-        const int nw = bd >> 5;
-        if (tid < B)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q) {
-                double acc = scratch[q * bd + tid];
-                for (int w = 1; w < nw; ++w) {
-                    const double o = scratch[q * bd + w * B + tid];
-                    acc = ((maxmask >> q) & 1u) ? fmax(acc, o) : acc + o;
-                }
-                out[q * B + tid] = acc;
-            }
-    } else {
-#pragma unroll
-        for (int q = 0; q < NQV; ++q) scratch[q * bd + tid] = (tid < RB * B) ? v[q] : 0.0;
-        __syncthreads();
-        if (tid < B)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q) {
-                double acc = scratch[q * bd + tid];
-                for (int r = 1; r < RB; ++r) {
-                    const double o = scratch[q * bd + r * B + tid];
-                    acc = ((maxmask >> q) & 1u) ? fmax(acc, o) : acc + o;
-                }
-                out[q * B + tid] = acc;
-            }
-    }
-    __syncthreads();
-}
-
-// Column sums for threads that each hold VEC consecutive columns: thread tid is
-// row lane rl = tid / G of column group g = tid % G (columns g*VEC .. +VEC-1,
-// C = G*VEC).  Fixed summation order; totals in out[q*C + c] (FP64).  The sums
-// inside the block are taken in R (FP32 for the per-iteration dot products of
-// the FP32 solves, whose per-thread partials are FP32 already: GB300 issues
-// FP64 at a small fraction of the FP32 rate).  `scratch` holds at least
-// NQV * max(bd/32, RB) * C values of R.
-template <int NQV, int VEC, typename R = double>
-__device__ __forceinline__ void block_reduce_cols(R (&v)[NQV][VEC], R* scratch, double* out, int C, int G,
-                                                  int RB) {
-    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, g = tid % G;
-    int nrow;
-    if (G <= 32 && (32 % G) == 0) {
-        // lanes of one column group differ by multiples of G within the warp
-        for (int off = 16; off >= G; off >>= 1)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q)
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) v[q][k] += __shfl_xor_sync(0xffffffffu, v[q][k], off);
-        nrow = bd >> 5;
-        if (lane < G)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q)
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) scratch[(q * nrow + warp) * C + g * VEC + k] = v[q][k];
-    } else {
-        nrow = RB;
-        const int rl = tid / G;
-        if (tid < RB * G)
-#pragma unroll
-            for (int q = 0; q < NQV; ++q)
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) scratch[(q * nrow + rl) * C + g * VEC + k] = v[q][k];
-    }
-    __syncthreads();
-    for (int t = tid; t < NQV * C; t += bd) {
-        const int q = t / C, c = t % C;
-        R acc = R(0);
-        for (int r = 0; r < nrow; ++r) acc += scratch[(q * nrow + r) * C + c];
-        out[q * C + c] = (double)acc;
-    }
-    __syncthreads();
-}
-
-// Totals over blocks of partials part[blk][C][4] (quantities q0..q0+NQV-1), in a
-// fixed order, into out[q*C + c] (threads hold VEC columns each, as above).
-template <int NQV, int VEC>
-__device__ __forceinline__ void cross_reduce_cols(const double* part, int q0, int nblk, int C, int G, int RB,
-                                                  double* scratch, double* out) {
-    const int tid = threadIdx.x, g = tid % G, rl = tid / G;
-    double v[NQV][VEC];
-#pragma unroll
-    for (int q = 0; q < NQV; ++q)
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) v[q][k] = 0.0;
-    if (tid < RB * G) {
-#pragma unroll 2
-        for (int blk = rl; blk < nblk; blk += RB)
-#pragma unroll
-            for (int k = 0; k < VEC; ++k)
-#pragma unroll
-                for (int q = 0; q < NQV; ++q) v[q][k] += __ldcg(&part[((size_t)blk * C + g * VEC + k) * 4 + q0 + q]);
-    }
-    block_reduce_cols<NQV, VEC>(v, scratch, out, C, G, RB);
-}
-
-template <typename T, int VEC> struct VecOf;
-template <> struct VecOf<float, 4> { using type = float4; };
-template <> struct VecOf<float, 2> { using type = float2; };
-template <> struct VecOf<double, 2> { using type = double2; };
-
-template <typename T, int VEC, bool CG>
-__device__ __forceinline__ void vload(T (&d)[VEC], const T* p) {
-    using V = typename VecOf<T, VEC>::type;
-    V x;
-    if constexpr (CG) x = __ldcg(reinterpret_cast<const V*>(p));
-    else x = *reinterpret_cast<const V*>(p);
-    if constexpr (VEC == 4) { d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w; }
-    else { d[0] = x.x; d[1] = x.y; }
-}
-
-template <typename T, int VEC>
-__device__ __forceinline__ void vstore(T* p, const T (&d)[VEC]) {
-    using V = typename VecOf<T, VEC>::type;
-    V x;
-    if constexpr (VEC == 4) { x.x = d[0]; x.y = d[1]; x.z = d[2]; x.w = d[3]; }
-    else { x.x = d[0]; x.y = d[1]; }
-    *reinterpret_cast<V*>(p) = x;
-}
-
-constexpr double MP_INNER = 1e-4;   // residual reduction of one FP32 cycle of a mixed-iteration solve
-constexpr int MP_MAX_CYCLES = 16;
-constexpr int MAXK = 8;   // stiffness entries served by the unrolled gather (interior Kuhn rows: 7)
-
-// Value tables of a general mesh in the precision of the kernel.
-template <typename T> struct GenTab;
-template <> struct GenTab<float> {
-    using V4 = float4;
-    static __device__ __forceinline__ const float4* A(const MeshView& M) { return M.gA32; }
-    static __device__ __forceinline__ const float4* Bt(const MeshView& M) { return M.gB32; }
-    static __device__ __forceinline__ const float* k(const MeshView& M) { return M.gk32; }
-    static __device__ __forceinline__ const float* d(const MeshView& M) { return M.gd32; }
-};
-template <> struct GenTab<double> {
-    using V4 = Dbl4;
-    static __device__ __forceinline__ const Dbl4* A(const MeshView& M) { return M.gA64; }
-    static __device__ __forceinline__ const Dbl4* Bt(const MeshView& M) { return M.gB64; }
-    static __device__ __forceinline__ const double* k(const MeshView& M) { return M.gk64; }
-    static __device__ __forceinline__ const double* d(const MeshView& M) { return M.gd64; }
-};
-
-// acc[k] = sum_j K_ij (v_j - v_i) (DIFF) or sum_j K_ij v_j for VEC consecutive
-// columns of one row of the stiffness-only CSR.  The packed entries are read
-// first -- one load per lane and a warp broadcast when the whole warp works on
-// this row (warp_row) -- then every vector gather of the row is issued before
-// any arithmetic.  warp_row requires the full warp to take part.
-// General meshes (GEN): the values come from kval, and rows of any length are
-// served MAXK entries at a time.
-template <typename T, int VEC, bool CG, bool DIFF, bool GEN>
-__device__ __forceinline__ void row_kv(const int* __restrict__ kent, const T* __restrict__ kval, int e0, int e1,
-                                       const T* v, int C, int c0, const T (&vi)[VEC], T (&acc)[VEC],
-                                       bool warp_row) {
-    if constexpr (GEN) {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] = T(0);
-        for (int base = e0; base < e1; base += MAXK) {
-            int w[MAXK];
-            T kv[MAXK];
-            if (warp_row) {
-                const int lane = threadIdx.x & 31;
-                const bool has = lane < MAXK && base + lane < e1;
-                const int mine = has ? __ldg(&kent[base + lane]) : 0;
-                const T mk = has ? __ldg(&kval[base + lane]) : T(0);
-#pragma unroll
-                for (int t = 0; t < MAXK; ++t) {
-                    w[t] = __shfl_sync(0xffffffffu, mine, t);
-                    kv[t] = __shfl_sync(0xffffffffu, mk, t);
-                }
-            } else {
-#pragma unroll
-                for (int t = 0; t < MAXK; ++t) {
-                    const bool has = base + t < e1;
-                    w[t] = has ? __ldg(&kent[base + t]) : 0;
-                    kv[t] = has ? __ldg(&kval[base + t]) : T(0);
-                }
-            }
-            T vj[MAXK][VEC];
-#pragma unroll
-            for (int t = 0; t < MAXK; ++t) {
-                if (w[t] != 0) vload<T, VEC, CG>(vj[t], &v[(size_t)((unsigned)w[t] >> 8) * C + c0]);
-                else
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
-            }
-#pragma unroll
-            for (int t = 0; t < MAXK; ++t)
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) acc[k] += kv[t] * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
-        }
-        return;
-    }
-    int w[MAXK];
-    if (warp_row) {
-        const int lane = threadIdx.x & 31;
-        const int mine = (lane < MAXK && e0 + lane < e1) ? __ldg(&kent[e0 + lane]) : 0;
-#pragma unroll
-        for (int t = 0; t < MAXK; ++t) w[t] = __shfl_sync(0xffffffffu, mine, t);
-    } else {
-#pragma unroll
-        for (int t = 0; t < MAXK; ++t) w[t] = (e0 + t < e1) ? __ldg(&kent[e0 + t]) : 0;
-    }
-    T vj[MAXK][VEC];
-#pragma unroll
-    for (int t = 0; t < MAXK; ++t) {
-        if (w[t] != 0) vload<T, VEC, CG>(vj[t], &v[(size_t)((unsigned)w[t] >> 8) * C + c0]);
-        else
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
-    }
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) acc[k] = T(0);
-#pragma unroll
-    for (int t = 0; t < MAXK; ++t) {
-        const T kk = T(sbyte(w[t], 0));
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] += kk * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
-    }
-    for (int e = e0 + MAXK; e < e1; ++e) {
-        const int ww = __ldg(&kent[e]);
-        T x[VEC];
-        vload<T, VEC, CG>(x, &v[(size_t)((unsigned)ww >> 8) * C + c0]);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) acc[k] += T(sbyte(ww, 0)) * (DIFF ? (x[k] - vi[k]) : x[k]);
-    }
-}
-
-// As row_kv for a warp that owns the row, with the row's packed entries
-// already in registers (lane l holds entry e0 + l, l < 32: `mine`, and its
-// value `mk` for general meshes), so that no index load sits on the row's
-// critical path; entries beyond the 32nd are loaded here.
-template <typename T, int VEC, bool CG, bool DIFF, bool GEN>
-__device__ __forceinline__ void row_kv_warp(int mine, T mk, int e0, int e1, const int* __restrict__ kent,
-                                            const T* __restrict__ kval, const T* v, int C, int c0,
-                                            const T (&vi)[VEC], T (&acc)[VEC]) {
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) acc[k] = T(0);
-    const int cnt = e1 - e0;
-    for (int base = 0; base < cnt; base += MAXK) {
-        int w[MAXK];
-        T kv[MAXK];
-#pragma unroll
-        for (int t = 0; t < MAXK; ++t) {
-            const int idx = base + t;   // warp-uniform
-            if (idx < 32) {
-                w[t] = __shfl_sync(0xffffffffu, mine, idx);
-                kv[t] = GEN ? __shfl_sync(0xffffffffu, mk, idx) : T(0);
-            } else {
-                const bool has = idx < cnt;
-                w[t] = has ? __ldg(&kent[e0 + idx]) : 0;
-                kv[t] = (GEN && has) ? __ldg(&kval[e0 + idx]) : T(0);
-            }
-            if (!GEN) kv[t] = T(sbyte(w[t], 0));
-        }
-        T vj[MAXK][VEC];
-#pragma unroll
-        for (int t = 0; t < MAXK; ++t) {
-            if (w[t] != 0) vload<T, VEC, CG>(vj[t], &v[(size_t)((unsigned)w[t] >> 8) * C + c0]);
-            else
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) vj[t][k] = vi[k];
-        }
-#pragma unroll
-        for (int t = 0; t < MAXK; ++t)
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) acc[k] += kv[t] * (DIFF ? (vj[t][k] - vi[k]) : vj[t][k]);
-    }
-}
-
-// The trial point of an instance whose base point is `cur`, in T.
-template <typename T>
-__device__ __forceinline__ const T* trial_m(const BatchView<T>& V, int cur, int N) {
-    if constexpr (sizeof(T) == 4) {
-        (void)cur;
-        (void)N;
-        return V.m32;
-    } else {
-        return V.m + (size_t)(1 - cur) * N * 3 * V.B;
-    }
-}
-
-template <typename T>
-struct PcgArgs {
-    MeshView M;
-    BatchView<T> V;
-    int mode;          // 0: stage 1 (u1 | w), 1: stage 2 (u2 | uT)
-    double tol2;       // squared relative residual
-    int max_iter;
-    unsigned* bar;
-    int* err;
-    unsigned long long* sweeps;
-    double* fin;
-};
 
 template <bool SINGLE>
 __device__ __forceinline__ bool pcg_sync(unsigned* bar, unsigned& epoch, int* err) {
@@ -407,26 +92,6 @@ __device__ __forceinline__ bool grid_reduce(const double* part, int q0, int C, d
     for (int t = threadIdx.x; t < P; t += blockDim.x) out[(t % NQV) * C + t / NQV] = __ldcg(&fin[t]);
     __syncthreads();
     return true;
-}
-
-// b_i = (1/4) sum_j Gint_ij . m_j (the divergence right-hand side) at the trial point
-// meval: the trial point in T (FP32 kernels: its FP32 copy)
-template <typename T, bool GEN>
-__device__ __forceinline__ double rhs_b(const int* __restrict__ col, const int* __restrict__ pkA,
-                                        const typename GenTab<T>::V4* __restrict__ gA, int e0, int e1,
-                                        const T* meval, int B, int b) {
-    T acc = T(0);
-    for (int e = e0; e < e1; ++e) {
-        const size_t mj = (size_t)(__ldg(&col[e]) & 0x7fffffff) * 3 * B + b;
-        if constexpr (GEN) {
-            const typename GenTab<T>::V4 a = gA[e];
-            acc += a.y * meval[mj] + a.z * meval[mj + B] + a.w * meval[mj + 2 * B];
-        } else {
-            const int w = __ldg(&pkA[e]);
-            acc += T(sbyte(w, 1)) * meval[mj] + T(sbyte(w, 2)) * meval[mj + B] + T(sbyte(w, 3)) * meval[mj + 2 * B];
-        }
-    }
-    return 0.25 * (double)acc;
 }
 
 // Jacobi-PCG on Kint for the 2B systems of one stage of the forward and adjoint
@@ -589,8 +254,7 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                     // f: the right-hand side (b in every system but the stage-2 forward one)
                     double f = 0.0;
                     if (!(mode == 1 && !neu[k]) && actk[k])
-                        f = rhs_b<T, GEN>(col, pkA, gA, e0, e1, trial_m(A.V, s_cur[c0 + k], N), B,
-                                          bk[k]);
+                        f = A.V.bvec[(size_t)row * B + bk[k]];
                     if (mode == 1 && neu[k] && bp) f += (double)A.V.ub_out[(size_t)(bp - 1) * C + c0 + k];
                     double ref = f;   // norm reference: f (Neumann), f - K_IS x_S (Dirichlet)
                     if (!neu[k])
@@ -888,12 +552,40 @@ __global__ void __launch_bounds__(SINGLE ? PCG_SINGLE_THREADS : PCG_THREADS, 1) 
                     if (mode == 0 && bp) A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] = xv[k];
                 } else if (mode == 0 && bp) {
                     A.V.ub_in[(size_t)(bp - 1) * C + c0 + k] =
-                        T(rhs_b<T, GEN>(col, pkA, gA, rowptr[row], rowptr[row + 1],
-                                        trial_m(A.V, s_cur[c0 + k], N), B, bk[k])) - kw[k];
+                        T(A.V.bvec[(size_t)row * B + bk[k]]) - kw[k];
                 }
             }
             vstore<T, VEC>(&x[ib], xv);
         }
+}
+
+// b_i = (1/4) sum_j Gint_ij . m_j at the trial point of every active instance
+// (one thread per row and instance, instances fastest): computed once per
+// evaluation and read by both potential-solve stages (forward and adjoint
+// right-hand sides, the adjoint's surface hand-off), by the same arithmetic
+// (rhs_b) the solves used inline before.
+template <typename T, bool GEN>
+__global__ void k_rhs(MeshView M, BatchView<T> V) {
+    const int B = V.B;
+    const size_t total = (size_t)M.N * B;
+    const typename GenTab<T>::V4* __restrict__ gA = GEN ? GenTab<T>::A(M) : nullptr;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t % B);
+        const int row = (int)(t / B);
+        const InstState& s = V.st[b];
+        if (s.phase == PH_DONE) continue;
+        V.bvec[t] = rhs_b<T, GEN>(M.col, M.pkA, gA, M.rowptr[row], M.rowptr[row + 1], trial_m(V, s.cur, M.N), B, b);
+    }
+}
+
+template <typename T>
+void rhs_eval(const Launch& L, const MeshView& M, const BatchView<T>& V) {
+    const size_t total = (size_t)M.N * V.B;
+    size_t blocks = (total + 255) / 256;
+    if (blocks > (size_t)8 * L.num_sms) blocks = (size_t)8 * L.num_sms;
+    if (M.gen) k_rhs<T, true><<<(unsigned)blocks, 256, 0, L.stream>>>(M, V);
+    else k_rhs<T, false><<<(unsigned)blocks, 256, 0, L.stream>>>(M, V);
+    *L.launches += 1;
 }
 
 size_t pcg_part_elems(int num_sms, int B) { return (size_t)2 * num_sms * (2 * B) * 4; }
@@ -931,6 +623,10 @@ static cudaError_t dispatch_pcg(const Launch& L, const MeshView& M, PcgArgs<T>& 
 template <typename T>
 int pcg_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
               bool mixed_iter) {
+    if (L.pcg_kernel != 1) {
+        cudaError_t ce;
+        if (pcg_solve_cluster<T>(L, M, V, mode, tol, max_iter, mixed_iter, &ce)) return ce == cudaSuccess ? 0 : (int)ce;
+    }
     const int C = 2 * V.B;
     PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps, L.fin};
     // one CTA is fastest for small FP32 work (no grid barriers); FP64 arithmetic
@@ -1617,6 +1313,7 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
 #define LBM_INSTANTIATE(T)                                                                               \
     template int pcg_solve<T>(const Launch&, const MeshView&, const BatchView<T>&, int, double, int, bool); \
     template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&);                     \
+    template void rhs_eval<T>(const Launch&, const MeshView&, const BatchView<T>&);                        \
     template void field_eval<T>(const Launch&, const MeshView&, const BatchView<T>&, int);                 \
     template void trial_update<T>(const Launch&, const MeshView&, const BatchView<T>&);                    \
     template void decide<T>(const Launch&, const MeshView&, const BatchView<T>&, const StepOpts&, int);    \
