@@ -68,6 +68,7 @@ constexpr double MU0 = 4e-7 * 3.14159265358979323846;
 
 struct Mesh {
     int n = 0, N = 0, nb = 0, nnz = 0, F = 0, T = 0;
+    int num_sms = 0;                         // of the context's device (sizes split-K scratch)
     double cell = 0;
     int *rowptr = nullptr, *col = nullptr, *pkA = nullptr, *pkB = nullptr, *node = nullptr, *bidx = nullptr;
     int *tris = nullptr, *inc_ptr = nullptr, *inc_slot = nullptr;
@@ -75,6 +76,7 @@ struct Mesh {
     int nnzK = 0;
     double* B64 = nullptr;
     float* B32 = nullptr;
+    float* B32lo = nullptr;                   // fp32(B64 - B32) for FP64 batches of >1 instance (lazy)
     float *tcA = nullptr, *tcAT = nullptr;   // padded FP32 B and B^T for the tensor-core path (lazy)
     // general meshes (lbm_mesh_upload; n == 0)
     bool gen = false;
@@ -91,7 +93,7 @@ struct Mesh {
         v.n = n; v.N = N; v.nb = nb; v.nnz = nnz; v.F = F;
         v.rowptr = rowptr; v.col = col; v.pkA = pkA; v.pkB = pkB; v.node = node; v.bidx = bidx;
         v.kptr = kptr; v.kent = kent;
-        v.B64 = B64; v.B32 = B32;
+        v.B64 = B64; v.B32 = B32; v.B32lo = B32lo;
         v.vsum = gen ? vsum : 24.0 * (double)n * n * n;
         v.cell = cell;
         v.gen = gen ? 1 : 0;
@@ -224,7 +226,10 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.q = take(tsize * N * C);
     L.ub_in = take(tsize * nb * C);
     L.ub_out = take(tsize * nb * C);
-    L.bem_part = take(8 * 32 * nb);   // 32 x nb partial sums of the transposed product
+    // 32 x nb partial sums of the transposed single-instance product; FP64
+    // batches also the K-split partials of the batched product (S x nb x 2B)
+    const size_t df = (tsize == 8 && B > 1) ? (size_t)bem_df_splits((int)nb, B, M.num_sms) * nb * C : 0;
+    L.bem_part = take(8 * (32 * nb > df ? 32 * nb : df));
     L.m32 = tsize == 4 ? take(4 * N * 3 * B) : 0;
     L.bvec = take(8 * N * B);
     L.total = o;
@@ -287,7 +292,7 @@ Inst* get_inst(lbm_ctx* ctx, lbm_inst h) {
 
 void free_mesh(Mesh* m) {
     void* ptrs[] = {m->rowptr, m->col, m->pkA, m->pkB, m->node, m->bidx, m->tris, m->inc_ptr, m->inc_slot,
-                    m->kptr, m->kent, m->B64, m->B32, m->tcA, m->tcAT, m->tets, m->xyz, m->gA64, m->gB64,
+                    m->kptr, m->kent, m->B64, m->B32, m->B32lo, m->tcA, m->tcAT, m->tets, m->xyz, m->gA64, m->gB64,
                     m->gA32, m->gB32, m->gk64, m->gV, m->gd64, m->gk32, m->gd32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -684,6 +689,7 @@ int lbm_mesh_cube(lbm_ctx* ctx, double cell_m, int32_t n, lbm_mesh* out) {
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     Mesh* M = new Mesh();
+    M->num_sms = ctx->num_sms;
     M->n = n;
     M->cell = cell_m;
     const int n1 = n + 1, N = n1 * n1 * n1;
@@ -789,6 +795,7 @@ int lbm_mesh_upload(lbm_ctx* ctx, const double* xyz, int64_t n_nodes, const int3
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     Mesh* M = new Mesh();
+    M->num_sms = ctx->num_sms;
     M->gen = true;
     M->n = 0;
     M->N = N;
@@ -1111,6 +1118,19 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
             return fail(LBM_E_OOM, "tensor-core scratch");
         }
         I->use_tc = true;
+    }
+    if (batch > 1 && !M->B32lo) {
+        // the low FP32 part of the FP64 matrix, for the FP64-accurate batched
+        // products of FP64 batches (the FP64 phase of mixed runs included)
+        const size_t nb2 = (size_t)M->nb * M->nb;
+        if (cudaMalloc(&M->B32lo, sizeof(float) * nb2) != cudaSuccess) {
+            M->B32lo = nullptr;
+            free_inst(I);
+            return fail(LBM_E_OOM, "low part of the boundary matrix");
+        }
+        launch_bem_lo(M->B64, M->B32, M->B32lo, nb2, ctx->stream);
+        ctx->launches += 1;
+        M->bytes += sizeof(float) * nb2;
     }
     lbm_material nd = {1.61, 7.7e-12, 4.3e6, {0.0, 0.0, 1.0}};
     I->mats.assign(batch, nd);

@@ -135,6 +135,7 @@ struct MeshView {
     const int* bidx;     // nb;  boundary node ids, ascending
     const double* B64;   // nb x nb row-major
     const float* B32;    // nb x nb row-major
+    const float* B32lo;  // nb x nb: fp32(B64 - B32), for the FP64-accurate batched product (null: not built)
     double vsum;         // sum_i Vint_i = 24 n^3 (general meshes: sum of gV)
     double cell;         // cell edge h (m); general meshes: the length unit L
     // General meshes (gen != 0): the same tables as FP64/FP32 values in the same
@@ -220,6 +221,11 @@ template <typename T>
 int bem_product_tc(const Launch& L, int nb, const float* A32, const float* A32T, const T* ub_in, T* ub_out, int B,
                    float* scratch);
 int field_blocks(const Launch& L, const MeshView& M, int B);
+// FP64-accurate batched BEM product on the FP32 units: K-split count and the
+// doubles of its partial-sum scratch (S * nb * 2B)
+int bem_df_splits(int nb, int B, int num_sms);
+// B_lo = fp32(B64 - B32) (nb x nb)
+void launch_bem_lo(const double* B64, const float* B32, float* B32lo, size_t n, cudaStream_t st);
 size_t pcg_part_elems(int num_sms, int B);
 
 // Kernel attributes are per device: set a kernel's dynamic shared-memory limit

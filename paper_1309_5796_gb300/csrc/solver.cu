@@ -757,6 +757,124 @@ __global__ void __launch_bounds__(256) k_gemm(const TA* __restrict__ A, const T*
         }
 }
 
+// ---- FP64-accurate batched BEM products on the FP32 units ------------------------------
+// Y = op(B) X for the FP64 vectors of FP64 batches (the FP64 phase of mixed
+// runs included), with B = B_hi + B_lo (B_hi the FP32 copy of B, B_lo the FP32
+// rounding of B - B_hi: together B to about 2^-48 relative) and x = x_hi + x_lo
+// the same way.  Per term a_hi x_hi is exact as p + e (e = fma(a_hi, x_hi, -p));
+// p is added to the high word of a double-FP32 accumulator with Knuth's TwoSum,
+// whose rounding error is exact; that error, e and the cross terms a_hi x_lo +
+// a_lo x_hi go into the low word (the a_lo x_lo term is 2^-48 of the term); the
+// two words are combined in FP64.  (Kahan compensation in FP32 is not enough:
+// it keeps each term to about FP32 precision.)  GB300 issues FP32 arithmetic
+// at many times its FP64 rate, so twelve FP32 instructions per term beat one
+// FP64 fused multiply-add.  The sum over K is split across blocks (blockIdx.z); the
+// partials part[z][row][c] (FP64) are added in a fixed order by k_sum_splits.
+__global__ void k_bem_lo(const double* __restrict__ B64, const float* __restrict__ B32, float* __restrict__ lo,
+                         size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        lo[i] = (float)(B64[i] - (double)B32[i]);
+}
+
+void launch_bem_lo(const double* B64, const float* B32, float* B32lo, size_t n, cudaStream_t st) {
+    k_bem_lo<<<1024, 256, 0, st>>>(B64, B32, B32lo, n);
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(256) k_gemm_df(const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                                 const double* __restrict__ X, int ldx, double* __restrict__ part,
+                                                 int ldp, int nb, int ncols, int kchunk) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ float Ah[BK][BM + 4], Al[BK][BM + 4], Xh[BK][BN + 4], Xl[BK][BN + 4];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kbeg = blockIdx.z * kchunk, kend = min(nb, kbeg + kchunk);
+    float sh[4][4], sl[4][4];   // high and low words of the accumulators
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[i][j] = sl[i][j] = 0.f;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int l = tid; l < BM * BK; l += 256) {
+            int mm, kk;
+            if (TRANS) { kk = l / BM; mm = l % BM; } else { mm = l / BK; kk = l % BK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            float h = 0.f, w = 0.f;
+            if (gm < nb && gk < kend) {
+                const size_t idx = TRANS ? (size_t)gk * nb + gm : (size_t)gm * nb + gk;
+                h = Ahi[idx];
+                w = Alo[idx];
+            }
+            Ah[kk][mm] = h;
+            Al[kk][mm] = w;
+        }
+        for (int l = tid; l < BK * BN; l += 256) {
+            const int kk = l / BN, nn = l % BN;
+            const int gk = k0 + kk, gn = n0 + nn;
+            const double v = (gk < kend && gn < ncols) ? X[(size_t)gk * ldx + gn] : 0.0;
+            const float h = (float)v;
+            Xh[kk][nn] = h;
+            Xl[kk][nn] = (float)(v - (double)h);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float ah[4], al[4], xh[4], xl[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ah[i] = Ah[kk][ty * 4 + i];
+                al[i] = Al[kk][ty * 4 + i];
+                xh[i] = Xh[kk][tx * 4 + i];
+                xl[i] = Xl[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = __fmul_rn(ah[i], xh[j]);
+                    float e = __fmaf_rn(ah[i], xh[j], -p);   // exact: a_hi x_hi = p + e
+                    e = __fmaf_rn(ah[i], xl[j], e);
+                    e = __fmaf_rn(al[i], xh[j], e);
+                    // TwoSum: t + err = sh + p exactly
+                    const float t = __fadd_rn(sh[i][j], p);
+                    const float bp = __fsub_rn(t, sh[i][j]);
+                    const float ap = __fsub_rn(t, bp);
+                    const float err = __fadd_rn(__fsub_rn(sh[i][j], ap), __fsub_rn(p, bp));
+                    sh[i][j] = t;
+                    sl[i][j] = __fadd_rn(sl[i][j], __fadd_rn(err, e));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+            if (gm < nb && gn < ncols)
+                part[((size_t)blockIdx.z * nb + gm) * ldp + gn] = (double)sh[i][j] + (double)sl[i][j];
+        }
+}
+
+// y[row][c] = sum over the S splits of part[s][row][c], in split order (C = 2B columns)
+__global__ void k_sum_splits(const double* __restrict__ part, int S, int nb, int C, double* __restrict__ y) {
+    const size_t total = (size_t)nb * C;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int z = 0; z < S; ++z) acc += part[(size_t)z * total + i];
+        y[i] = acc;
+    }
+}
+
+// K splits so that the two products fill about four waves of two blocks per SM
+int bem_df_splits(int nb, int B, int num_sms) {
+    const int tiles = ((nb + 63) / 64) * ((B + 63) / 64) * 2;
+    int S = (8 * num_sms + tiles - 1) / tiles;
+    if (S > 16) S = 16;
+    if (S < 1) S = 1;
+    return S;
+}
+
 template <typename T> __host__ __device__ inline const T* bem_ptr(const MeshView& M);
 template <> __host__ __device__ inline const double* bem_ptr<double>(const MeshView& M) { return M.B64; }
 template <> __host__ __device__ inline const float* bem_ptr<float>(const MeshView& M) { return M.B32; }
@@ -842,6 +960,25 @@ static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const B
                                                                              nb, C, rpc);
         k_sum_parts<T><<<(nb + 255) / 256, 256, 0, L.stream>>>((const double*)V.bem_part, S, nb, V.ub_out + 1, C);
         *L.launches += 3;
+    } else if constexpr (std::is_same<TA, double>::value && std::is_same<T, double>::value) {
+        if (M.B32lo) {
+            // FP64 batches: the FP64-accurate product on the FP32 units
+            const int S = bem_df_splits(nb, B, L.num_sms);
+            const int kchunk = (((nb + S - 1) / S) + 15) / 16 * 16;
+            dim3 grid((nb + 63) / 64, (B + 63) / 64, S);
+            double* part = reinterpret_cast<double*>(V.bem_part);
+            k_gemm_df<false><<<grid, 256, 0, L.stream>>>(M.B32, M.B32lo, V.ub_in, C, part, C, nb, B, kchunk);
+            k_gemm_df<true><<<grid, 256, 0, L.stream>>>(M.B32, M.B32lo, V.ub_in + B, C, part + B, C, nb, B, kchunk);
+            size_t blocks = ((size_t)nb * C + 255) / 256;
+            if (blocks > (size_t)8 * L.num_sms) blocks = (size_t)8 * L.num_sms;
+            k_sum_splits<<<(unsigned)blocks, 256, 0, L.stream>>>(part, S, nb, C, V.ub_out);
+            *L.launches += 3;
+        } else {
+            dim3 grid((nb + 63) / 64, (B + 63) / 64);
+            k_gemm<TA, T, false><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in, C, V.ub_out, C, nb, B);
+            k_gemm<TA, T, true><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in + B, C, V.ub_out + B, C, nb, B);
+            *L.launches += 2;
+        }
     } else {
         dim3 grid((nb + 63) / 64, (B + 63) / 64);
         k_gemm<TA, T, false><<<grid, 256, 0, L.stream>>>(Bm, V.ub_in, C, V.ub_out, C, nb, B);
