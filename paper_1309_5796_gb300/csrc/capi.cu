@@ -49,6 +49,8 @@ int fail(int code, const char* fmt, ...) {
     } while (0)
 
 constexpr double MU0 = 4e-7 * 3.14159265358979323846;
+// The FP64 phase of a mixed run stops at this fraction of the requested torque
+constexpr double POLISH_MARGIN = 0.9;
 
 // No C++ exception crosses the C interface: every entry point runs inside
 // LBM_TRY / LBM_CATCH, which turn host allocation failures into LBM_E_OOM and
@@ -431,7 +433,7 @@ void fill_result(const InstState& s, const InstConst& c, lbm_result& r, double w
 
 template <typename T>
 int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res, bool evaluate_only,
-                 double* hout, double* uout, std::vector<InstState>* states_out = nullptr) {
+                 double* hout, double* uout, std::vector<InstState>* states_out = nullptr, bool warm = false) {
     Mesh& M = *ctx->meshes[I->mesh];
     const auto t0 = std::chrono::steady_clock::now();
     BatchView<T> V = batch_view<T>(ctx, M, *I, evaluate_only && hout);
@@ -441,7 +443,7 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
     lbm_solve_opts oo = o;
     if (evaluate_only) oo.max_iter = 0;
     const StepOpts so = step_opts(oo);
-    reset_states(L, I->st, I->B, so, 0);
+    reset_states(L, I->st, I->B, so, 0, warm ? 1 : 0);
     const int nblk_field = field_blocks(L, mv, I->B);
     std::vector<InstState> hs(I->B);
     const int64_t max_loops = (int64_t)(oo.max_iter + 1) * (oo.max_backtracks + 2) + 2;
@@ -558,7 +560,13 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
         lbm_solve_opts o2 = o;
         o2.cg_tol = o.cg_tol_polish;
         o2.stall_iters = 0;   // the FP64 phase runs to tol or max_iter
-        rc = run_minimise<double>(ctx, P, o2, nullptr, false, nullptr, nullptr, &s2);
+        // a 10 % margin below tol: the phase's torque comes from solves to
+        // cg_tol_polish, the exact problem's may differ by that much
+        o2.tol = POLISH_MARGIN * o.tol;
+        // the FP64 phase continues the FP32 phase's step state (BB step, kappa,
+        // tau^2 memory) after one FP64 evaluation of the point, instead of
+        // starting over with a line search
+        rc = run_minimise<double>(ctx, P, o2, nullptr, false, nullptr, nullptr, &s2, true);
         if (rc) return rc;
         CK(cudaMemcpyAsync(I->vec, P->vec, sizeof(double) * 2 * N * 3 * B, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(I->st, P->st, sizeof(InstState) * B, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1539,7 +1547,21 @@ __global__ void k_slot_reset(InstState* st, int b, int phase) {
     s.cur = 0;
     s.iters = s.evals = s.line_searches = s.backtracks = 0;
     s.nhist = s.hpos = s.ntau2 = 0;
+    s.warm = 0;
     s.cg1 = s.cg2 = 0;
+}
+
+// slot d of the FP64 batch continues the step state (BB step, kappa, tau^2
+// memory) of slot b of the FP32 batch after its first FP64 evaluation
+__global__ void k_slot_warm(InstState* dst, int d, const InstState* src, int b) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    InstState& t = dst[d];
+    const InstState& f = src[b];
+    t.tau = f.tau;
+    t.kappa = f.kappa;
+    t.ntau2 = f.ntau2;
+    for (int k = 0; k < MALPHA_MAX; ++k) t.tau2[k] = f.tau2[k];
+    t.warm = 1;
 }
 
 __global__ void k_slots_done(InstState* st, int B) {
@@ -1819,6 +1841,7 @@ void serve_loop(Server* Sp) {
     lbm_solve_opts o2 = o;
     o2.cg_tol = o.cg_tol_polish;
     o2.stall_iters = 0;
+    o2.tol = POLISH_MARGIN * o.tol;   // as lbm_minimise's FP64 phase
     const StepOpts so1 = step_opts(o1), so2 = step_opts(o2);
     lbm_solve_opts o64 = o;        // plain FP64 requests
     for (;;) {
@@ -1918,7 +1941,8 @@ void serve_loop(Server* Sp) {
                     (const float*)((const char*)G->I32->vec + L32.U1), (const float*)((const char*)G->I32->vec + L32.U2),
                     (double*)G->I64->vec, G->I64->B, d, (double*)((char*)G->I64->vec + L64.U1),
                     (double*)((char*)G->I64->vec + L64.U2), M.N);
-                ctx->launches += 2;
+                k_slot_warm<<<1, 1, 0, G->stream>>>(G->I64->st, d, G->I32->st, b);
+                ctx->launches += 3;
                 set_slot_consts(G->I64, d, G->I32->mats[b], &G->I32->h[3 * b], G->cell, G->stream);
                 T.s32 = G->h32[b];
                 T.has32 = true;

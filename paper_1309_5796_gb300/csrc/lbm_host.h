@@ -211,7 +211,9 @@ void unpack_m(const Launch& L, const MeshView& M, const BatchView<T>& V, double*
 template <typename T>
 void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, double* staged_h,
                   double* staged_u);
-void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0);
+// warm: keep each instance's step state (tau, kappa, tau^2 memory) for the
+// first step after the first evaluation (a new precision phase at the same point)
+void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0, int warm = 0);
 
 // ---- tensor-core BEM products (tc_gemm.cu) ------------------------------------------
 int tc_ld(int nb);

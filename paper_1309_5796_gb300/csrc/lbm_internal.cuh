@@ -61,6 +61,8 @@ struct InstState {
     double Eacc;                   // base energy carried by exact differences (decisions)
     double best_torque;            // smallest torque of the accepted points so far
     int best_iter;                 // the iteration where it was reached
+    int warm;                      // 1: the first evaluation resumes the step state (tau, kappa,
+                                   // tau^2 memory) of a previous phase instead of a line search
     double terms[4];
     double mean_m[3];
     double hist[HIST_MAX];

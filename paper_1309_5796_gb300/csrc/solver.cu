@@ -1216,18 +1216,30 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     s.mean_m[2] = v[Q_MZ] / vsum;
     const int mem = so.memory < HIST_MAX ? so.memory : HIST_MAX;
     if (init) {
+        const bool warm = s.warm != 0 && so.method == 0;
+        s.warm = 0;
         s.hist[0] = E;
         s.nhist = 1;
         s.hpos = 1 % mem;
         s.iters = 0;
         s.line_searches = 0;
         s.backtracks = 0;
-        s.ntau2 = 0;
-        s.kappa = so.kappa0;
+        if (!warm) {
+            s.ntau2 = 0;
+            s.kappa = so.kappa0;
+        }
         s.best_torque = torque;
         s.best_iter = 0;
         if (conv) { s.status = 0; s.phase = PH_DONE; return; }
         if (so.max_iter <= 0) { s.status = 3; s.phase = PH_DONE; return; }
+        if (warm) {
+            // a new precision phase at the point where the previous one stopped:
+            // its next BB step (and kappa, tau^2 memory) continues the iteration;
+            // the nonmonotone test against this evaluation's energy guards it
+            s.tau = fmin(fmax(s.tau, so.tau_min), so.tau_max);
+            s.phase = PH_BB;
+            return;
+        }
         if (so.method == 1) {
             s.tau = so.omega;
             s.phase = PH_LB;
@@ -1370,7 +1382,7 @@ void trial_update(const Launch& L, const MeshView& M, const BatchView<T>& V) {
 }
 
 // ---- state reset and layout conversion -------------------------------------------------
-__global__ void k_reset(InstState* st, int B, int set_cur0) {
+__global__ void k_reset(InstState* st, int B, int set_cur0, int warm) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     InstState& s = st[b];
@@ -1378,13 +1390,15 @@ __global__ void k_reset(InstState* st, int B, int set_cur0) {
     s.status = 3;
     if (set_cur0) s.cur = 0;
     s.iters = s.evals = s.line_searches = s.backtracks = 0;
-    s.nhist = s.hpos = s.ntau2 = 0;
+    s.nhist = s.hpos = 0;
+    if (!warm) s.ntau2 = 0;   // warm: tau, kappa and the tau^2 memory are kept
+    s.warm = warm;
     s.cg1 = s.cg2 = 0;
 }
 
-void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0) {
+void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0, int warm) {
     (void)so;
-    k_reset<<<(B + 127) / 128, 128, 0, L.stream>>>(st, B, set_cur0);
+    k_reset<<<(B + 127) / 128, 128, 0, L.stream>>>(st, B, set_cur0, warm);
     *L.launches += 1;
 }
 

@@ -4,12 +4,12 @@ FP64 problem, not only that of the mixed path's own arithmetic.
 64 instances on the 30^3-cell cube are minimised in LBM_MIXED_TC (FP32 phase,
 then an FP64 phase whose potential solves stop at a 1e-10 relative residual),
 and the final states are re-evaluated with plain FP64 solves (1e-13) and the
-FP64 boundary matrix.  The stop test max|m x h|/Js < 1e-6 is taken on the FP64
-phase's own field; the re-evaluated torque differs from it by the field error
-of those solves (measured ~1e-10 on this workload), so the bar here is
-1e-6 + 1e-9.  This file is collected last: it depends on the tail of a
-distribution (the largest torque measured was 9.91e-7), and a run that stops at
-the first failure has already run every other test.
+FP64 boundary matrix.  The FP64 phase stops at 0.9 of the requested torque
+(1e-6), on its own field; the re-evaluated torque differs from it by the field
+error of those solves (measured ~1e-10 on this workload), so every final state
+keeps a 10 % margin against the requested 1e-6 in the exact problem: the bar
+here is 0.9e-6 + 1e-9.  This file is collected last, so that a run that stops
+at the first failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -46,5 +46,5 @@ def test_mixed_final_states_converged_in_the_fp64_problem():
     finally:
         ctx.close()
     for a, b in zip(res, r64):
-        assert a["status"] == lbm.LBM_OK and a["torque"] < 1e-6
-        assert b["torque"] < 1e-6 + 1e-9
+        assert a["status"] == lbm.LBM_OK and a["torque"] < 0.9e-6
+        assert b["torque"] < 0.9e-6 + 1e-9
