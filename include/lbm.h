@@ -326,6 +326,34 @@ int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_material* mat, c
                          const lbm_solve_opts* opt, const double* d_m, double* d_h, double* d_u,
                          double* d_energy);
 
+/* ---- hierarchical (H-matrix) boundary operator ------------------------------------
+ * Sec. 3.1: the hybrid FEM/BEM boundary operator of the paper's LLG comparison
+ * solver is accelerated by hierarchical matrices.  Builds B_H for the mesh's
+ * surface on `threads` host threads (cluster tree by geometric bisection,
+ * admissibility min(diam) <= eta * dist, leaves of at most n_min positions;
+ * inadmissible leaves exact, admissible ones by adaptive cross approximation
+ * to |A - U V|_F <= eps |A|_F, then recompressed), and its transpose; uploads
+ * both (FP32 and FP64 values) and makes every BEM product of the mesh's
+ * instances use them, u2_S = B_H u1_S and c_S = B_H^T t_S, in place of the
+ * dense matrix (which stays allocated).  eps <= 0 returns the mesh to the
+ * dense matrix.  info (nullable): [stored values, nb^2, leaves, low-rank
+ * leaves].  Waits for the context's queued work.  Returns LBM_E_INVALID for a
+ * bad argument (eps >= 1, eta <= 0, n_min or threads < 1), LBM_E_OOM when
+ * device memory runs out. */
+int lbm_mesh_hmatrix(lbm_ctx* ctx, lbm_mesh mesh, double eps, double eta, int32_t n_min, int32_t threads,
+                     int64_t info[4]);
+
+/* The boundary operator of the mesh (dense, or the hierarchical form when
+ * built) applied to `batch` host vectors, as the solver applies it (Sec. 3.1,
+ * the a3 step): y = B x and yt = B^T x.  precision: LBM_FP64 (FP64 vectors and
+ * matrix) or LBM_MIXED (FP32 vectors, the FP32 matrix or values).
+ * x: [nb][batch] host, position-major (position = index into the ascending
+ * surface node ids); y, yt (nullable): [nb][batch] host.  Allocates and frees
+ * its device buffers; waits for the result.  The paper has no counterpart: it
+ * serves tests and diagnostics of the product. */
+int lbm_bem_apply(lbm_ctx* ctx, lbm_mesh mesh, int32_t precision, int32_t batch, const double* x, double* y,
+                  double* yt);
+
 /* ---- device waits ------------------------------------------------------------
  * Every device-side wait of this context's kernels (the grid barrier of the
  * cooperative potential solves) gives up after a time limit, sets the

@@ -110,6 +110,8 @@ SIGNATURES = [
     ("lbm_evaluate_noalloc", C.c_int, [_P, _I64, C.POINTER(Material), _DP, C.POINTER(SolveOpts),
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_set_wait_limit", C.c_int, [_P, C.c_double, C.c_int32]),
+    ("lbm_mesh_hmatrix", C.c_int, [_P, _I64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(_I64)]),
+    ("lbm_bem_apply", C.c_int, [_P, _I64, C.c_int32, C.c_int32, _DP, _DP, _DP]),
     ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
     ("lbm_serve_start", C.c_int, [_P, C.POINTER(ServeOpts)]),
     ("lbm_submit", C.c_int, [_P, C.POINTER(Request), C.POINTER(_I64)]),
@@ -278,6 +280,26 @@ class Context:
                                           C.byref(opts) if opts else None, C.c_void_p(d_m),
                                           C.c_void_p(d_h or None), C.c_void_p(d_u or None),
                                           C.c_void_p(d_energy or None)))
+
+    def mesh_hmatrix(self, mesh: int, eps: float, eta: float = 2.0, n_min: int = 16, threads: int | None = None) -> dict:
+        """lbm_mesh_hmatrix: build and use the hierarchical form of the mesh's
+        boundary matrix (eps <= 0: back to the dense matrix)."""
+        out = (C.c_int64 * 4)()
+        th = threads if threads is not None else max(1, os.cpu_count() or 1)
+        _check(lib().lbm_mesh_hmatrix(self._h, mesh, float(eps), float(eta), int(n_min), int(th), out))
+        return dict(stored=out[0], dense=out[1], leaves=out[2], low_rank=out[3],
+                    fraction=(out[0] / out[1]) if out[1] else 0.0)
+
+    def bem_apply(self, mesh: int, x, precision=LBM_FP64):
+        """lbm_bem_apply: (B x, B^T x) for x of shape [nb] or [nb, batch]."""
+        xa = np.ascontiguousarray(np.asarray(x, np.float64))
+        one = xa.ndim == 1
+        if one:
+            xa = xa[:, None].copy()
+        nb, batch = xa.shape
+        y, yt = np.empty_like(xa), np.empty_like(xa)
+        _check(lib().lbm_bem_apply(self._h, mesh, precision, batch, _dptr(xa), _dptr(y), _dptr(yt)))
+        return (y[:, 0], yt[:, 0]) if one else (y, yt)
 
     def set_wait_limit(self, seconds: float, unreachable: bool = False):
         """lbm_set_wait_limit: the device-wait limit of this context's kernels

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -79,6 +80,8 @@ struct Mesh {
     double* B64 = nullptr;
     float* B32 = nullptr;
     float* B32lo = nullptr;                   // fp32(B64 - B32) for FP64 batches of >1 instance (lazy)
+    HMDevice* hm = nullptr;                   // hierarchical form of B (lbm_mesh_hmatrix), or null
+    std::vector<void*> hm_mem;                // its device allocations
     float *tcA = nullptr, *tcAT = nullptr;   // padded FP32 B and B^T for the tensor-core path (lazy)
     // general meshes (lbm_mesh_upload; n == 0)
     bool gen = false;
@@ -96,6 +99,7 @@ struct Mesh {
         v.rowptr = rowptr; v.col = col; v.pkA = pkA; v.pkB = pkB; v.node = node; v.bidx = bidx;
         v.kptr = kptr; v.kent = kent;
         v.B64 = B64; v.B32 = B32; v.B32lo = B32lo;
+        v.hm = hm;
         v.vsum = gen ? vsum : 24.0 * (double)n * n * n;
         v.cell = cell;
         v.gen = gen ? 1 : 0;
@@ -292,7 +296,30 @@ Inst* get_inst(lbm_ctx* ctx, lbm_inst h) {
     return it == ctx->insts.end() ? nullptr : it->second;
 }
 
+void free_hm(Mesh* m) {
+    for (void* p : m->hm_mem) cudaFree(p);
+    m->hm_mem.clear();
+    if (m->hm && m->hm->t) cudaFree(m->hm->t);
+    delete m->hm;
+    m->hm = nullptr;
+}
+
+// The first-pass scratch of the hierarchical products for batches of B instances.
+int hm_reserve(lbm_ctx* ctx, Mesh* M, int B) {
+    if (!M->hm) return LBM_OK;
+    const size_t need = sizeof(double) * 2 * (size_t)(M->hm->fwd.n_t > 0 ? M->hm->fwd.n_t : 1) * B;
+    if (M->hm->t_bytes >= need) return LBM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (M->hm->t) cudaFree(M->hm->t);
+    M->hm->t = nullptr;
+    M->hm->t_bytes = 0;
+    CK(cudaMalloc(&M->hm->t, need));
+    M->hm->t_bytes = need;
+    return LBM_OK;
+}
+
 void free_mesh(Mesh* m) {
+    free_hm(m);
     void* ptrs[] = {m->rowptr, m->col, m->pkA, m->pkB, m->node, m->bidx, m->tris, m->inc_ptr, m->inc_slot,
                     m->kptr, m->kent, m->B64, m->B32, m->B32lo, m->tcA, m->tcAT, m->tets, m->xyz, m->gA64, m->gB64,
                     m->gA32, m->gB32, m->gk64, m->gV, m->gd64, m->gk32, m->gd32};
@@ -379,7 +406,7 @@ int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, cons
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
         {
             ProfScope ps(ctx, 2, L.stream);
-            if (I.use_tc && M.tcA && I.tc_scratch) {
+            if (I.use_tc && M.tcA && I.tc_scratch && !M.hm) {
                 e = bem_product_tc<T>(L, M.nb, M.tcA, M.tcAT, V.ub_in, V.ub_out, V.B, I.tc_scratch);
                 if (e) return fail(LBM_E_CUDA, "tensor-core BEM product failed (%d)", e);
             } else {
@@ -1074,6 +1101,199 @@ int lbm_hmatrix_plan(const double* xyz, int64_t n_nodes, const int32_t* tets, in
     LBM_CATCH
 }
 
+// Upload one packed operator: leaf table, positions, values (FP32 and FP64),
+// the first pass's row table, the owners' slots and entries.
+static int hm_upload(lbm_ctx* ctx, Mesh* M, const HPacked& P, HMView& v) {
+    auto up = [&](const void* src, size_t bytes) -> void* {
+        void* d = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+        M->hm_mem.push_back(d);
+        if (src && cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return nullptr;
+        return d;
+    };
+    std::vector<HLeafDev> lv(P.leaves.size());
+    std::vector<int> trow_leaf, trow_l;
+    for (size_t q = 0; q < P.leaves.size(); ++q) {
+        const HPackedLeaf& e = P.leaves[q];
+        lv[q] = HLeafDev{e.row_begin, e.m, e.col_begin, e.n, e.kind, e.rank, (long long)e.val, (long long)e.t_off};
+        if (e.kind)
+            for (int l = 0; l < e.rank; ++l) {
+                trow_leaf.push_back((int)q);
+                trow_l.push_back(l);
+            }
+    }
+    // output rows: every owner's positions, owners in order; they must cover
+    // every surface position exactly once
+    std::vector<int> slot_owner, slot_a, seen(P.nb, 0);
+    for (size_t o = 0; o < P.owner_begin.size(); ++o)
+        for (int a = 0; a < P.owner_size[o]; ++a) {
+            const size_t at = (size_t)P.owner_begin[o] + a;
+            const int pos = at < P.idx.size() ? P.idx[at] : -1;
+            if (pos < 0 || pos >= P.nb || seen[pos]++)
+                return fail(LBM_E_INVALID, "lbm_mesh_hmatrix: row owners do not partition the surface");
+            slot_owner.push_back((int)o);
+            slot_a.push_back(a);
+        }
+    if ((int)slot_owner.size() != P.nb) return fail(LBM_E_INVALID, "lbm_mesh_hmatrix: row owners do not cover the surface");
+    std::vector<long long> optr(P.owner_ptr.begin(), P.owner_ptr.end()), erows(P.entries.size());
+    std::vector<int> eleaf(P.entries.size());
+    for (size_t e = 0; e < P.entries.size(); ++e) {
+        eleaf[e] = P.entries[e].leaf;
+        erows[e] = (long long)P.entries[e].rows;
+    }
+    v.nb = P.nb;
+    v.nleaf = (int)lv.size();
+    v.n_t = (int)P.n_t;
+    v.leaves = (const HLeafDev*)up(lv.data(), sizeof(HLeafDev) * lv.size());
+    v.idx = (const int*)up(P.idx.data(), sizeof(int) * P.idx.size());
+    v.v32 = (const float*)up(P.values.data(), sizeof(float) * P.values.size());
+    v.v64 = (const double*)up(P.values64.data(), sizeof(double) * P.values64.size());
+    v.trow_leaf = (const int*)up(trow_leaf.data(), sizeof(int) * trow_leaf.size());
+    v.trow_l = (const int*)up(trow_l.data(), sizeof(int) * trow_l.size());
+    v.slot_owner = (const int*)up(slot_owner.data(), sizeof(int) * slot_owner.size());
+    v.slot_a = (const int*)up(slot_a.data(), sizeof(int) * slot_a.size());
+    v.owner_begin = (const int*)up(P.owner_begin.data(), sizeof(int) * P.owner_begin.size());
+    v.owner_ptr = (const long long*)up(optr.data(), sizeof(long long) * optr.size());
+    v.ent_leaf = (const int*)up(eleaf.data(), sizeof(int) * eleaf.size());
+    v.ent_rows = (const long long*)up(erows.data(), sizeof(long long) * erows.size());
+    v.row_map = (const int*)up(P.row_map.data(), sizeof(int) * P.row_map.size());
+    if (!v.leaves || !v.idx || !v.v32 || !v.v64 || !v.trow_leaf || !v.trow_l || !v.slot_owner || !v.slot_a || !v.owner_begin ||
+        !v.owner_ptr || !v.ent_leaf || !v.ent_rows || !v.row_map)
+        return fail(LBM_E_OOM, "lbm_mesh_hmatrix: device allocation failed");
+    CK(cudaStreamSynchronize(ctx->stream));   // the host vectors go out of scope
+    return LBM_OK;
+}
+
+int lbm_mesh_hmatrix(lbm_ctx* ctx, lbm_mesh mesh, double eps, double eta, int32_t n_min, int32_t threads,
+                     int64_t info[4]) {
+    LBM_TRY
+    Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
+    if (!M) return fail(LBM_E_INVALID, "lbm_mesh_hmatrix: unknown mesh");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_hm(M);
+    if (eps <= 0.0) {   // back to the dense matrix
+        if (info) info[0] = info[1] = info[2] = info[3] = 0;
+        return LBM_OK;
+    }
+    if (!(eps < 1.0) || !(eta > 0.0) || !std::isfinite(eta) || n_min < 1 || threads < 1)
+        return fail(LBM_E_INVALID, "lbm_mesh_hmatrix: eps must lie in (0, 1), eta be positive, n_min and threads at "
+                    "least 1");
+    // the surface as the mesh holds it: node coordinates (lattice units for a
+    // Kuhn cube, the length unit for an upload), surface ids, triangles
+    const int N = M->N, nb = M->nb, F = M->F;
+    std::vector<double> xyz(3 * (size_t)N);
+    if (M->gen) {
+        CK(cudaMemcpy(xyz.data(), M->xyz, sizeof(double) * xyz.size(), cudaMemcpyDeviceToHost));
+    } else {
+        const int s = M->n + 1;
+        for (int id = 0; id < N; ++id) {
+            xyz[3 * (size_t)id] = id % s;
+            xyz[3 * (size_t)id + 1] = (id / s) % s;
+            xyz[3 * (size_t)id + 2] = id / (s * s);
+        }
+    }
+    std::vector<int> bidx(nb), tris(3 * (size_t)F);
+    CK(cudaMemcpy(bidx.data(), M->bidx, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(tris.data(), M->tris, sizeof(int) * tris.size(), cudaMemcpyDeviceToHost));
+    HMatrixHost H, Ht;
+    std::string why = host_hmatrix_build(N, xyz.data(), nb, bidx.data(), F, tris.data(), eta, n_min, eps, threads, H);
+    if (!why.empty()) return fail(LBM_E_INVALID, "lbm_mesh_hmatrix: %s", why.c_str());
+    host_hmatrix_transpose(H, Ht);
+    HPacked Pf, Pa;
+    why = host_hmatrix_pack(H, nb, Pf);
+    if (why.empty()) why = host_hmatrix_pack(Ht, nb, Pa);
+    if (!why.empty()) return fail(LBM_E_INVALID, "lbm_mesh_hmatrix: %s", why.c_str());
+    M->hm = new HMDevice();
+    int rc = hm_upload(ctx, M, Pf, M->hm->fwd);
+    if (!rc) rc = hm_upload(ctx, M, Pa, M->hm->adj);
+    int bmax = 1;
+    for (auto& kv : ctx->insts)
+        if (kv.second->mesh == mesh) bmax = std::max(bmax, kv.second->B);
+    if (!rc) rc = hm_reserve(ctx, M, bmax);
+    if (rc) {
+        free_hm(M);
+        return rc;
+    }
+    if (info) {
+        int64_t low = 0;
+        for (int k : H.kind) low += k;
+        info[0] = (int64_t)H.data.size();
+        info[1] = (int64_t)nb * nb;
+        info[2] = (int64_t)H.kind.size();
+        info[3] = low;
+    }
+    return LBM_OK;
+    LBM_CATCH
+}
+
+int lbm_bem_apply(lbm_ctx* ctx, lbm_mesh mesh, int32_t precision, int32_t batch, const double* x, double* y,
+                  double* yt) {
+    LBM_TRY
+    Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
+    if (!M || !x || batch < 1 || batch > 256 || (precision != LBM_FP64 && precision != LBM_MIXED))
+        return fail(LBM_E_INVALID, "lbm_bem_apply: bad argument");
+    CK(cudaSetDevice(ctx->device));
+    if (int rc = hm_reserve(ctx, M, batch)) return rc;
+    const int nb = M->nb, B = batch, C = 2 * B;
+    const size_t tsize = precision == LBM_FP64 ? 8 : 4;
+    const size_t S = (size_t)bem_df_splits(nb, B, ctx->num_sms);
+    const size_t part = std::max((size_t)32 * nb, S * nb * C);
+    std::vector<double> xin((size_t)nb * C);
+    for (int q = 0; q < nb; ++q)
+        for (int c = 0; c < B; ++c) xin[(size_t)q * C + c] = xin[(size_t)q * C + B + c] = x[(size_t)q * B + c];
+    void *din = nullptr, *dout = nullptr, *dpart = nullptr;
+    auto cleanup = [&]() {
+        if (din) cudaFree(din);
+        if (dout) cudaFree(dout);
+        if (dpart) cudaFree(dpart);
+    };
+    if (cudaMalloc(&din, tsize * nb * C) != cudaSuccess || cudaMalloc(&dout, tsize * nb * C) != cudaSuccess ||
+        cudaMalloc(&dpart, sizeof(double) * part) != cudaSuccess) {
+        cleanup();
+        return fail(LBM_E_OOM, "lbm_bem_apply: device allocation failed");
+    }
+    std::vector<float> xin32;
+    if (tsize == 4) xin32.assign(xin.begin(), xin.end());
+    const void* src = tsize == 8 ? (const void*)xin.data() : (const void*)xin32.data();
+    cudaError_t e = cudaMemcpyAsync(din, src, tsize * nb * C, cudaMemcpyHostToDevice, ctx->stream);
+    Launch L = ctx->launch();
+    const MeshView mv = M->view();
+    if (tsize == 8) {
+        BatchView<double> V{};
+        V.B = B;
+        V.ub_in = (double*)din;
+        V.ub_out = (double*)dout;
+        V.bem_part = (double*)dpart;
+        bem_product<double>(L, mv, V);
+    } else {
+        BatchView<float> V{};
+        V.B = B;
+        V.ub_in = (float*)din;
+        V.ub_out = (float*)dout;
+        V.bem_part = (float*)dpart;
+        bem_product<float>(L, mv, V);
+    }
+    std::vector<double> out((size_t)nb * C);
+    std::vector<float> out32(tsize == 4 ? (size_t)nb * C : 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tsize == 8 ? (void*)out.data() : (void*)out32.data(), dout, tsize * nb * C,
+                            cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(LBM_E_CUDA, "lbm_bem_apply: %s", cudaGetErrorString(e));
+    if (tsize == 4) out.assign(out32.begin(), out32.end());
+    for (int q = 0; q < nb; ++q)
+        for (int c = 0; c < B; ++c) {
+            if (y) y[(size_t)q * B + c] = out[(size_t)q * C + c];
+            if (yt) yt[(size_t)q * B + c] = out[(size_t)q * C + B + c];
+        }
+    return LBM_OK;
+    LBM_CATCH
+}
+
 int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t precision, lbm_inst* out) {
     LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
@@ -1126,6 +1346,10 @@ int lbm_instance_create(lbm_ctx* ctx, lbm_mesh mesh, int32_t batch, int32_t prec
             return fail(LBM_E_OOM, "tensor-core scratch");
         }
         I->use_tc = true;
+    }
+    if (int rc = hm_reserve(ctx, M, batch)) {
+        free_inst(I);
+        return rc;
     }
     if (batch > 1 && !M->B32lo) {
         // the low FP32 part of the FP64 matrix, for the FP64-accurate batched

@@ -59,19 +59,21 @@ std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P) {
     }
     P.n_t = ts;
     P.values.resize(vals);
+    P.values64.resize(vals);
     for (size_t q = 0; q < L; ++q) {
         const size_t l = order[q];
         const HPackedLeaf& e = P.leaves[q];
         const double* src = H.data.data() + H.off[l];
-        float* dst = P.values.data() + e.val;
+        double* dst = P.values64.data() + e.val;
         if (!e.kind) {
-            for (size_t i = 0; i < (size_t)e.m * e.n; ++i) dst[i] = (float)src[i];
+            for (size_t i = 0; i < (size_t)e.m * e.n; ++i) dst[i] = src[i];
         } else {
             const size_t nu = (size_t)e.m * e.rank, nv = (size_t)e.rank * e.n;
-            for (size_t i = 0; i < nv; ++i) dst[i] = (float)src[nu + i];        // V first
-            for (size_t i = 0; i < nu; ++i) dst[nv + i] = (float)src[i];        // then U
+            for (size_t i = 0; i < nv; ++i) dst[i] = src[nu + i];        // V first
+            for (size_t i = 0; i < nu; ++i) dst[nv + i] = src[i];        // then U
         }
     }
+    for (size_t i = 0; i < vals; ++i) P.values[i] = (float)P.values64[i];
     // row owners: the leaves of the cluster tree, in cluster order
     std::vector<int> owner_of_cluster(H.P.clusters.size(), -1);
     for (size_t c = 0; c < H.P.clusters.size(); ++c)
@@ -113,6 +115,38 @@ std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P) {
     P.entries.reserve(P.owner_ptr.back());
     for (const auto& v : per) P.entries.insert(P.entries.end(), v.begin(), v.end());
     return {};
+}
+
+void host_hmatrix_transpose(const HMatrixHost& H, HMatrixHost& T) {
+    T = HMatrixHost{};
+    T.P = H.P;
+    T.kind = H.kind;
+    T.rank = H.rank;
+    T.fallbacks = H.fallbacks;
+    T.off.resize(H.off.size());
+    T.data.resize(H.data.size());
+    for (size_t l = 0; l < H.P.leaves.size(); ++l) {
+        HLeaf& lf = T.P.leaves[l];
+        std::swap(lf.row, lf.col);
+        const int m = H.P.clusters[H.P.leaves[l].row].size, n = H.P.clusters[H.P.leaves[l].col].size;
+        const double* src = H.data.data() + H.off[l];
+        double* dst = T.data.data() + H.off[l];
+        T.off[l] = H.off[l];
+        if (!H.kind[l]) {                               // m x n -> n x m
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < n; ++j) dst[(size_t)j * m + i] = src[(size_t)i * n + j];
+        } else {                                        // U (m x k), V (k x n) -> V^T (n x k), U^T (k x m)
+            const int k = H.rank[l];
+            const double* U = src;
+            const double* V = src + (size_t)m * k;
+            double* Ut = dst;                           // new U = V^T, n x k
+            double* Vt = dst + (size_t)n * k;           // new V = U^T, k x m
+            for (int j = 0; j < n; ++j)
+                for (int a = 0; a < k; ++a) Ut[(size_t)j * k + a] = V[(size_t)a * n + j];
+            for (int a = 0; a < k; ++a)
+                for (int i = 0; i < m; ++i) Vt[(size_t)a * m + i] = U[(size_t)i * k + a];
+        }
+    }
 }
 
 }  // namespace lbm

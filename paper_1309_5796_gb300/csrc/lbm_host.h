@@ -102,6 +102,7 @@ struct HPacked {
     std::vector<HPackedLeaf> leaves;   // dense first, then low rank, each by (rows, columns)
     std::vector<int> idx;              // cluster positions (as HPartition::idx)
     std::vector<float> values;
+    std::vector<double> values64;      // the same values in FP64 (for FP64 products)
     size_t n_t = 0;                    // sum of the ranks (rows of the first pass's output)
     std::vector<int> owner_begin, owner_size;   // row owners (cluster-tree leaves): idx ranges
     std::vector<size_t> owner_ptr;     // [owners + 1]: their entries, in block-tree order
@@ -109,6 +110,39 @@ struct HPacked {
     std::vector<int> row_map;
 };
 std::string host_hmatrix_pack(const HMatrixHost& H, int nb, HPacked& P);
+// The transpose of a built operator on the same cluster tree: every leaf's row
+// and column clusters swapped, dense entries transposed, U V -> V^T U^T.
+void host_hmatrix_transpose(const HMatrixHost& H, HMatrixHost& T);
+
+// ---- device form of a packed hierarchical operator (uploaded by lbm_mesh_hmatrix) ----
+struct HLeafDev {
+    int row_begin, m, col_begin, n, kind, rank;
+    long long val, t_off;
+};
+struct HMView {
+    int nb = 0, nleaf = 0, n_t = 0;
+    const HLeafDev* leaves = nullptr;
+    const int* idx = nullptr;          // cluster positions -> boundary positions
+    const float* v32 = nullptr;        // values (FP32 products)
+    const double* v64 = nullptr;       // values (FP64 products)
+    const int* trow_leaf = nullptr;    // per row of t: its low-rank leaf
+    const int* trow_l = nullptr;       //   and its index within the leaf's rank
+    const int* slot_owner = nullptr;   // per output row k in [0, nb), owners in order: its row owner
+    const int* slot_a = nullptr;       //   and its index within the owner
+    const int* owner_begin = nullptr;  // per owner: offset of its positions in idx
+    const long long* owner_ptr = nullptr;   // [owners + 1] entries of each owner
+    const int* ent_leaf = nullptr;     // per entry: packed leaf
+    const long long* ent_rows = nullptr;    //   offset of the owner's local rows in row_map
+    const int* row_map = nullptr;
+};
+// Both products of a mesh's BEM matrix in hierarchical form, y = B_H x (forward)
+// and y = B_H^T x (adjoint), and the scratch of their first passes.
+struct HMDevice {
+    HMView fwd, adj;
+    double* t = nullptr;               // first-pass outputs: [2][n_t][B] values of the vector type
+    size_t t_bytes = 0;
+};
+
 
 // ---- open boundary by space transformation: host set-up (csrc/shell.cu) -------------
 struct ShellGrid {
@@ -136,6 +170,7 @@ struct MeshView {
     const double* B64;   // nb x nb row-major
     const float* B32;    // nb x nb row-major
     const float* B32lo;  // nb x nb: fp32(B64 - B32), for the FP64-accurate batched product (null: not built)
+    const HMDevice* hm = nullptr;   // host pointer: the hierarchical form, when built (lbm_mesh_hmatrix)
     double vsum;         // sum_i Vint_i = 24 n^3 (general meshes: sum of gV)
     double cell;         // cell edge h (m); general meshes: the length unit L
     // General meshes (gen != 0): the same tables as FP64/FP32 values in the same
@@ -185,6 +220,10 @@ struct Launch {
     int pcg_kernel = 0;          // 0 choose, 1 grid-wide kernel, 2 prefer clusters (lbm_solve_opts)
 };
 
+// u2_S = B_H u1_S and c_S = B_H^T t_S on the [nb][2B] surface arrays (forward
+// columns [0, B), adjoint columns [B, 2B)) with the hierarchical form of B
+template <typename T>
+void hm_product(const Launch& L, const HMDevice& H, const T* x, T* y, int B);
 // Thread-block-cluster variant of the potential solves (pcg_cluster.cu): 1 when
 // launched (*err its status), 0 when the batch does not qualify.
 template <typename T>

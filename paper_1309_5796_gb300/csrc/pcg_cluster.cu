@@ -79,13 +79,14 @@ __device__ __forceinline__ double ld_peer_f64(uint32_t a) {
 
 // Shared-memory layout of one CTA (offsets in bytes).
 struct ClSmem {
-    size_t z, scratch, out, slots, cold, coli, total;
+    size_t z, dtab, scratch, out, slots, cold, coli, total;
 };
 __host__ __device__ inline ClSmem cl_smem(int rpc, int cpc) {
     ClSmem s;
     size_t o = 0;
     auto take = [&o](size_t b) { const size_t at = o; o = (o + b + 15) & ~(size_t)15; return at; };
     s.z = take(sizeof(float) * (size_t)rpc * cpc);
+    s.dtab = take(sizeof(float) * (size_t)rpc);
     s.scratch = take(sizeof(double) * 4 * CL_NW * cpc);
     s.out = take(sizeof(double) * 4 * cpc);
     s.slots = take(sizeof(double) * 2 * 4 * cpc);
@@ -104,6 +105,8 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
     extern __shared__ __align__(16) unsigned char smraw[];
     const ClSmem lay = cl_smem(rpc, CPC);
     float* zs = reinterpret_cast<float*>(smraw + lay.z);           // [rpc][CPC]
+    // per own row: 1/K_ii (the Jacobi preconditioner), negative on surface rows
+    float* dtab = reinterpret_cast<float*>(smraw + lay.dtab);       // [rpc]
     double* scratch = reinterpret_cast<double*>(smraw + lay.scratch);
     double* out = reinterpret_cast<double*>(smraw + lay.out);       // [4][CPC]
     double* slots = reinterpret_cast<double*>(smraw + lay.slots);   // [2][4][CPC]
@@ -138,6 +141,14 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
         s_done[i] = 0;
         s_tin[i] = 0.0;
         s_rhop[i] = 1.0;
+    }
+    {
+        const int lo0 = (int)cluster_rank() * rpc, hi0 = min(A.M.N, lo0 + rpc);
+        for (int row = lo0 + (int)threadIdx.x; row < hi0; row += CL_THREADS) {
+            const int nd = A.M.node[row];
+            const float dinv = 1.f / (GEN ? GenTab<float>::d(A.M)[row] : float((nd >> 8) & 0xff));
+            dtab[row - lo0] = ((unsigned)nd >> 16) ? -dinv : dinv;
+        }
     }
     __syncthreads();
     bool actk[VEC], any_act = false;
@@ -261,7 +272,6 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                     float zr[VEC];
                     vload<T, VEC, false>(xi, &x[ib]);
                     row_kv<T, VEC, true, true, GEN>(kent, kvalT, kptr[row], kptr[row + 1], x, C, c0, xi, kx, false);
-                    const int e0 = rowptr[row], e1 = rowptr[row + 1];
                     // right-hand side: b (computed once per evaluation, four consecutive
                     // instances), none for the stage-2 forward system; plus the BEM term
                     // c on the surface rows of the stage-2 adjoint (Neumann) system
@@ -303,11 +313,11 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = 0.0;
                 for (int row = lo + rl; row < hi; row += RB) {
-                    const int nd = node[row];
-                    const bool surf = ((unsigned)nd >> 16) != 0;
+                    const float dt = dtab[row - lo];
+                    const bool surf = dt < 0.f;
                     const unsigned go = (unsigned)(row * CPC + cl0);               // grouped work vectors
                     float* zp = zs + (row - lo) * CPC + cl0;
-                    const W dinv = W(1) / (GEN ? kdiagW[row] : W((nd >> 8) & 0xff));
+                    const W dinv = fabsf(dt);
                     W rv[VEC], zv[VEC];
                     vload<W, VEC, false>(rv, &r[go]);
                     const float4 zr = *reinterpret_cast<const float4*>(zp);
@@ -378,7 +388,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                     for (int rb = lo + rl; rb < hi; rb += U * RB) {
                         // U rows per pass: every row's loads are issued before any arithmetic
                         W pvu[U][VEC], qvu[U][VEC];
-                        int ndu[U];
+                        bool surfu[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             const int row = rb + u * RB;
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                                 const unsigned go = (unsigned)(row * CPC + cl0);   // grouped work vectors
                                 vload<W, VEC, false>(pvu[u], &p[go]);
                                 vload<W, VEC, false>(qvu[u], &q[go]);
-                                ndu[u] = node[row];
+                                surfu[u] = dtab[row - lo] < 0.f;
                             }
                         }
 #pragma unroll
@@ -396,8 +406,9 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                             const unsigned go = (unsigned)(row * CPC + cl0);
                             W (&pv)[VEC] = pvu[u];
                             W (&qv)[VEC] = qvu[u];
-                            const int nd = ndu[u];
-                            const float4 zi = *reinterpret_cast<const float4*>(zs + (row - lo) * CPC + cl0);
+                            const bool surf = surfu[u];
+                            const float* zp = zs + (row - lo) * CPC + cl0;
+                            const float4 zi = *reinterpret_cast<const float4*>(zp);
                             float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
                             auto add = [&w4](float kk, const float4& zj) {
                                 w4.x += kk * zj.x;
@@ -405,13 +416,27 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                                 w4.z += kk * zj.z;
                                 w4.w += kk * zj.w;
                             };
-                            if (!GEN && ((unsigned)nd >> 16) == 0) {
+                            if (!GEN && !surf) {
                                 // interior node of the Kuhn cube: the 7-point stencil of P1 on
                                 // this triangulation (36 on the diagonal, -6 for the six axis
                                 // neighbours), in the CSR's ascending column order
                                 const int s2 = A.M.n + 1, s3 = s2 * s2;
-                                const float4 z0 = zrow(row - s3), z1 = zrow(row - s2), z2 = zrow(row - 1);
-                                const float4 z4 = zrow(row + 1), z5 = zrow(row + s2), z6 = zrow(row + s3);
+                                float4 z0, z1, z2, z4, z5, z6;
+                                if (row - s3 >= lo && row + s3 < hi) {   // all in this CTA's slab
+                                    z0 = *reinterpret_cast<const float4*>(zp - s3 * CPC);
+                                    z1 = *reinterpret_cast<const float4*>(zp - s2 * CPC);
+                                    z2 = *reinterpret_cast<const float4*>(zp - CPC);
+                                    z4 = *reinterpret_cast<const float4*>(zp + CPC);
+                                    z5 = *reinterpret_cast<const float4*>(zp + s2 * CPC);
+                                    z6 = *reinterpret_cast<const float4*>(zp + s3 * CPC);
+                                } else {
+                                    z0 = zrow(row - s3);
+                                    z1 = zrow(row - s2);
+                                    z2 = zrow(row - 1);
+                                    z4 = zrow(row + 1);
+                                    z5 = zrow(row + s2);
+                                    z6 = zrow(row + s3);
+                                }
                                 add(-6.f, z0);
                                 add(-6.f, z1);
                                 add(-6.f, z2);
@@ -440,7 +465,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                                 }
                             }
                             const float zv[VEC] = {zi.x, zi.y, zi.z, zi.w}, wv[VEC] = {w4.x, w4.y, w4.z, w4.w};
-                            const bool frozen = !neu && ((unsigned)nd >> 16) != 0;
+                            const bool frozen = !neu && surf;
 #pragma unroll
                             for (int k = 0; k < VEC; ++k) {
                                 pv[k] = zv[k] + beta[k] * pv[k];
@@ -475,7 +500,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                                 vload<W, VEC, false>(rau[u], &r[go]);
                                 vload<W, VEC, false>(pau[u], &p[go]);
                                 vload<W, VEC, false>(qau[u], &q[go]);
-                                dinvu[u] = GEN ? kdiagW[row] : W((node[row] >> 8) & 0xff);
+                                dinvu[u] = fabsf(dtab[row - lo]);
                             }
                         }
 #pragma unroll
@@ -486,7 +511,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                             W (&xa)[VEC] = xau[u];
                             W (&ra)[VEC] = rau[u];
                             W za[VEC];
-                            const W dinv = W(1) / dinvu[u];
+                            const W dinv = dinvu[u];
 #pragma unroll
                             for (int k = 0; k < VEC; ++k) {
                                 xa[k] += alpha[k] * pau[u][k];

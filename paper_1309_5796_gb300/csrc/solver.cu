@@ -987,11 +987,105 @@ static void bem_launch(const Launch& L, const TA* Bm, const MeshView& M, const B
     }
 }
 
+// ---- BEM products with the hierarchical (H-matrix) form of B -------------------------
+// y = B_H x on columns [coff, coff + B) of the [nb][2B] surface arrays, in the
+// two passes the packed layout is made for: (1) t = V x_sigma for every row of
+// every low-rank leaf; (2) every position's row of y is the sum, over the
+// entries of its row owner in block-tree order, of a dense leaf's row times
+// x_sigma or a U row times t, written once (no atomics, a fixed order).  Values
+// in the vector precision (FP32 or FP64), sums in DotAcc (compensated in FP32).
+template <typename T, typename VT, bool WARP>
+__global__ void k_hm_v(HMView H, const VT* __restrict__ vals, const T* __restrict__ x, int ldx, int coff, int B,
+                       T* __restrict__ t) {
+    if constexpr (WARP) {   // one instance: a warp per row of t, lanes over the columns of V
+        const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+        if (g >= H.n_t) return;
+        const HLeafDev lf = H.leaves[H.trow_leaf[g]];
+        const int l = H.trow_l[g];
+        const VT* Vr = vals + lf.val + (long long)l * lf.n;
+        const int* cols = H.idx + lf.col_begin;
+        DotAcc<T> acc;
+        for (int b = lane; b < lf.n; b += 32) acc.add(T(Vr[b]), x[(size_t)cols[b] * ldx + coff]);
+        double v = acc.value();
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) t[g] = T(v);
+    } else {                // a thread per (row of t, instance): the row of V is broadcast
+        const long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (tt >= (long long)H.n_t * B) return;
+        const int g = (int)(tt / B), c = (int)(tt % B);
+        const HLeafDev lf = H.leaves[H.trow_leaf[g]];
+        const VT* Vr = vals + lf.val + (long long)H.trow_l[g] * lf.n;
+        const int* cols = H.idx + lf.col_begin;
+        DotAcc<T> acc;
+        for (int b = 0; b < lf.n; ++b) acc.add(T(Vr[b]), x[(size_t)cols[b] * ldx + coff + c]);
+        t[(size_t)g * B + c] = T(acc.value());
+    }
+}
+
+template <typename T, typename VT>
+__global__ void k_hm_own(HMView H, const VT* __restrict__ vals, const T* __restrict__ x, int ldx, int coff, int B,
+                         const T* __restrict__ t, T* __restrict__ y) {
+    const long long tt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tt >= (long long)H.nb * B) return;
+    const int sl = (int)(tt / B), c = (int)(tt % B);   // output row (owners in order) and instance
+    const int o = H.slot_owner[sl];
+    const int a = H.slot_a[sl];                        // local row within the owner
+    DotAcc<T> acc;
+    for (long long e = H.owner_ptr[o]; e < H.owner_ptr[o + 1]; ++e) {
+        const HLeafDev lf = H.leaves[H.ent_leaf[e]];
+        const int r = H.row_map[H.ent_rows[e] + a];    // row within the leaf's row cluster
+        if (lf.kind == 0) {
+            const VT* D = vals + lf.val + (long long)r * lf.n;
+            const int* cols = H.idx + lf.col_begin;
+            for (int b = 0; b < lf.n; ++b) acc.add(T(D[b]), x[(size_t)cols[b] * ldx + coff + c]);
+        } else {
+            const VT* U = vals + lf.val + (long long)lf.rank * lf.n + (long long)r * lf.rank;
+            const T* tl = t + (size_t)lf.t_off * B + c;
+            for (int l = 0; l < lf.rank; ++l) acc.add(T(U[l]), tl[(size_t)l * B]);
+        }
+    }
+    y[(size_t)H.idx[H.owner_begin[o] + a] * ldx + coff + c] = T(acc.value());
+}
+
+template <typename T>
+static void hm_apply(const Launch& L, const HMView& H, const T* x, T* y, int ldx, int coff, int B, T* t) {
+    using VT = T;
+    const VT* vals;
+    if constexpr (sizeof(T) == 4) vals = reinterpret_cast<const VT*>(H.v32);
+    else vals = reinterpret_cast<const VT*>(H.v64);
+    if (H.n_t > 0) {
+        if (B == 1) {
+            const long long threads = (long long)H.n_t * 32;
+            k_hm_v<T, VT, true><<<(unsigned)((threads + 255) / 256), 256, 0, L.stream>>>(H, vals, x, ldx, coff, B, t);
+        } else {
+            const long long threads = (long long)H.n_t * B;
+            k_hm_v<T, VT, false><<<(unsigned)((threads + 255) / 256), 256, 0, L.stream>>>(H, vals, x, ldx, coff, B, t);
+        }
+        *L.launches += 1;
+    }
+    const long long threads = (long long)H.nb * B;
+    k_hm_own<T, VT><<<(unsigned)((threads + 255) / 256), 256, 0, L.stream>>>(H, vals, x, ldx, coff, B, t, y);
+    *L.launches += 1;
+}
+
+template <typename T>
+void hm_product(const Launch& L, const HMDevice& H, const T* x, T* y, int B) {
+    T* t0 = reinterpret_cast<T*>(H.t);
+    T* t1 = t0 + (size_t)H.fwd.n_t * B;
+    hm_apply<T>(L, H.fwd, x, y, 2 * B, 0, B, t0);   // u2_S = B u1_S
+    hm_apply<T>(L, H.adj, x, y, 2 * B, B, B, t1);   // c_S = B^T t_S
+}
+
 // FP32 vectors use the FP32 copy of B, FP64 vectors the FP64 matrix (the FP64
 // phase of a mixed run included: FP32 arithmetic in its products perturbed the
 // stray field enough to keep the true torque of the final state near 4e-5).
+// With a hierarchical form of B on the mesh, both products use it.
 template <typename T>
 void bem_product(const Launch& L, const MeshView& M, const BatchView<T>& V) {
+    if (M.hm) {
+        hm_product<T>(L, *M.hm, V.ub_in, V.ub_out, V.B);
+        return;
+    }
     if constexpr (sizeof(T) == 4) bem_launch<float, T>(L, M.B32, M, V);
     else bem_launch<double, T>(L, M.B64, M, V);
 }
@@ -1465,6 +1559,7 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
     template int pcg_solve<T>(const Launch&, const MeshView&, const BatchView<T>&, int, double, int, bool); \
     template void bem_product<T>(const Launch&, const MeshView&, const BatchView<T>&);                     \
     template void rhs_eval<T>(const Launch&, const MeshView&, const BatchView<T>&);                        \
+    template void hm_product<T>(const Launch&, const HMDevice&, const T*, T*, int);                         \
     template void field_eval<T>(const Launch&, const MeshView&, const BatchView<T>&, int);                 \
     template void trial_update<T>(const Launch&, const MeshView&, const BatchView<T>&);                    \
     template void decide<T>(const Launch&, const MeshView&, const BatchView<T>&, const StepOpts&, int);    \
