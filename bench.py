@@ -66,6 +66,10 @@ def parse():
                     help="batched: 64 same-mesh instances (default); served: Poisson request stream; "
                          "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix)")
     ap.add_argument("--n", type=int, default=80, help="cells per side of the large workload")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the single-instance 80^3-cell leg of the default line")
+    ap.add_argument("--large-hm-eps", type=float, default=1e-6,
+                    help="tolerance of the H-matrix variant of the large leg (0: dense only)")
     ap.add_argument("--max-iter", type=int, default=100000, help="iteration cap of the large workload")
     ap.add_argument("--pcg-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="potential-solve kernel (lbm_solve_opts.pcg_kernel): 0 choose, 1 grid-wide, 2 clusters")
@@ -363,6 +367,105 @@ def pcg_bytes_per_row(kind):
     return {"fp32": 48, "fp64": 96, "fp64_fp32iter": 48}[kind]
 
 
+# Algorithmic bytes of one unit of each kernel kind on a single instance (B = 1),
+# FP32 work vectors: every array a kernel must touch read or written once (the
+# mesh tables included -- with one instance they are not shared):
+#   trial update, per node: m and grad phi at the base point (2 x 24 B), the
+#     trial m (24 B) and, in the FP32 phase, its FP32 copy (12 B);
+#   field, per node: the CSR row (column, {K, G}, G^T words: 12 B per entry),
+#     the node word (4 B), the trial point (24 B FP64 + 12 B FP32 copy in the
+#     FP32 phase, or 24 B), the base point and its gradient (48 B), three
+#     potential columns (12 or 24 B), the new gradient (24 B);
+#   potential solves, per row and sweep of the two systems (forward, adjoint):
+#     12 FP32 words per system (z, p, q; x or d, r, p, q, z) and the row's
+#     stiffness entries, pointer and node word (36 B);
+#   BEM products, per evaluation: the forward and the transposed product each
+#     read the matrix once (4 or 8 B per entry; with B_H its stored values).
+def large_leg(local, n, hm_eps, max_iter=100000, warmup=1):
+    """One instance on an n^3-cell cube (random start, -3 T, mixed precision):
+    time to solution and per-kernel achieved bandwidth against the measured HBM
+    peak, with the dense boundary matrix and (hm_eps > 0) with B_H."""
+    import torch
+    import paper_1309_5796_gb300 as lbm
+    from synth.inputs import large_case
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    stream = torch.cuda.current_stream()
+    ctx = lbm.Context(local, stream=stream.cuda_stream)
+    case = large_case(n)
+    t0 = time.perf_counter()
+    mesh = ctx.mesh_cube(2e-9, n)
+    setup_s = time.perf_counter() - t0
+    info = ctx.mesh_info(mesh)
+    N, nb, nnz = info["N"], info["nb"], info["nnz"]
+    m0 = torch.from_numpy(np.ascontiguousarray(case.m0)).to(f"cuda:{local}")
+    out = {"workload": f"one instance on a {n}^3-cell Kuhn cube ({N} nodes, {nb} surface nodes), random start "
+                       "on the sphere (seed 3), -3 T along z, mixed precision; BEM matrix "
+                       f"{4 * nb * nb / 1e9:.2f} GB in FP32 (> L2)",
+           "mesh_setup_s": round(setup_s, 2), "peak_GB_s": hbm_peak,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    variants = [("dense", 0.0)] + ([("hmatrix", hm_eps)] if hm_eps > 0 else [])
+    for name, eps in variants:
+        stored = nb * nb
+        if eps > 0:
+            t0 = time.perf_counter()
+            hinfo = ctx.mesh_hmatrix(mesh, eps)
+            stored = hinfo["stored"]
+            build_s = time.perf_counter() - t0
+        inst = ctx.instance_create(mesh, 1, lbm.LBM_MIXED)
+        inst.set_material(JS_T, A_JM, K1_JM3, case.axis)
+        inst.set_field(case.h_ext)
+        opts = lbm.default_opts(lbm.LBM_MIXED, max_iter=max_iter)
+        for _ in range(warmup):
+            inst.set_m_device(m0.data_ptr())
+            inst.minimise(opts)
+        ctx.profile_read(reset=True)
+        ctx.profile_enable(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst.set_m_device(m0.data_ptr())
+        r = inst.minimise(opts)[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = ctx.profile_read(reset=True)
+        ctx.profile_enable(False)
+        inst.destroy()
+        n32, n64 = prof["pcg1_fp32"]["launches"], prof["pcg1_fp64"]["launches"]
+        sweeps = sum(prof["cg_sweeps"])
+        kern = {
+            "trial_update": (prof["trial_update"], (n32 * 84 + n64 * 72) * N),
+            "field": (prof["field"], (n32 + n64) * (12 * nnz + 124 * N)),
+            "potential_solves": ({"ms": sum(prof[k]["ms"] for k in ("pcg1_fp32", "pcg2_fp32", "pcg1_fp64", "pcg2_fp64")),
+                                  "launches": sum(prof[k]["launches"] for k in ("pcg1_fp32", "pcg2_fp32", "pcg1_fp64",
+                                                                                "pcg2_fp64"))},
+                                 sweeps * N * (2 * 48 + 36)),
+            "bem_products": (prof["bem_product"], (n32 * 2 * 4 + n64 * 2 * 8) * stored),
+        }
+        per = {}
+        for k, (p, by) in kern.items():
+            gbs = by / (p["ms"] / 1e3) / 1e9 if p["ms"] > 0 else None
+            per[k] = {"ms": round(p["ms"], 3), "launches": p["launches"], "bytes": int(by),
+                      "GB_s": round(gbs, 1) if gbs else None,
+                      "frac": round(gbs / hbm_peak, 4) if gbs else None}
+        v = {"ms_to_solution": round(ms, 1), "status": r["status"], "iterations": r["iterations"],
+             "evaluations": r["evaluations"], "torque": r["torque"], "energy_J": r["energy"][4],
+             "cg_sweeps": prof["cg_sweeps"], "kernels": per}
+        if eps > 0:
+            v.update({"eps": eps, "stored_values": stored, "stored_fraction": round(stored / (nb * nb), 4),
+                      "build_s": round(build_s, 2)})
+        out[name] = v
+    ctx.mesh_destroy(mesh)
+    ctx.close()
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1309_5796_gb300 as lbm
@@ -511,6 +614,13 @@ def run_ours(args, ws, rank, local):
                     "max_rel_energy_err_batched_mixed_vs_fp64": max(e_err)}
         single.destroy()
 
+    large = None
+    if not args.no_large:
+        try:
+            large = large_leg(local, 80, args.large_hm_eps, warmup=1)
+        except Exception as exc:   # the headline stands on its own
+            large = {"error": repr(exc)[:300]}
+
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
@@ -527,6 +637,7 @@ def run_ours(args, ws, rank, local):
         "kernel_ms": {k: round(v["ms"], 3) for k, v in kinds.items()},
         "cpu_baseline": cpu,
         "fp64_single_instance": fp64_arm,
+        "large_single_instance_n80": large,
         "e2e": {"value": e2e_value, "unit": "solves/s",
                 "h2d_bytes_per_step": int(m0_e2e.nbytes), "d2h_bytes_per_step": int(m_out.nbytes),
                 "host_memory": host_mem},

@@ -1115,6 +1115,7 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
     if (lane && phase != PH_DONE) {
         const int cur = V.st[b].cur;
         const InstConst ic = V.ic[b];
+        const double lam6 = ic.lam / 6.0, q24 = ic.Q / 24.0;
         const double* mt = V.m + (size_t)(1 - cur) * N * 3 * B;
         const double* mb = V.m + (size_t)cur * N * 3 * B;
         double* Gt = V.H + (size_t)(1 - cur) * N * 3 * B;        // grad phi at the trial point
@@ -1158,13 +1159,19 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
             const double m[3] = {mx, my, mz};
             const double kx[3] = {(double)ex0, (double)ex1, (double)ex2};
             const double ma = m[0] * ic.a[0] + m[1] * ic.a[1] + m[2] * ic.a[2];
-            const double hd[3] = {-(double)hd0 / vi, -(double)hd1 / vi, -(double)hd2 / vi};
+            // GB300 issues FP64 at a small fraction of its FP32 rate: one division
+            // per node (1/V_i), constant factors as products, squared maxima
+            // (the square roots are taken once, on the totals, by k_decide)
+            const double ivi = 1.0 / vi;
+            const double cex = -4.0 * ic.lam * ivi;
+            const double hd[3] = {-(double)hd0 * ivi, -(double)hd1 * ivi, -(double)hd2 * ivi};
             double h[3];
-            for (int c = 0; c < 3; ++c) h[c] = -4.0 * ic.lam * kx[c] / vi + ic.Q * ma * ic.a[c] + ic.hz[c] + hd[c];
+            for (int c = 0; c < 3; ++c) h[c] = cex * kx[c] + ic.Q * ma * ic.a[c] + ic.hz[c] + hd[c];
             // grad phi = -(V/12) h ;  H = -m x grad phi = (V/12) m x h ;  g = m x H
-            const double gr[3] = {-vi / 12.0 * h[0], -vi / 12.0 * h[1], -vi / 12.0 * h[2]};
+            const double v12 = vi * (1.0 / 12.0), v24 = vi * (1.0 / 24.0);
+            const double gr[3] = {-v12 * h[0], -v12 * h[1], -v12 * h[2]};
             const double mh[3] = {m[1] * h[2] - m[2] * h[1], m[2] * h[0] - m[0] * h[2], m[0] * h[1] - m[1] * h[0]};
-            const double Hv[3] = {vi / 12.0 * mh[0], vi / 12.0 * mh[1], vi / 12.0 * mh[2]};
+            const double Hv[3] = {v12 * mh[0], v12 * mh[1], v12 * mh[2]};
             Gt[i3] = gr[0];
             Gt[i3 + B] = gr[1];
             Gt[i3 + 2 * B] = gr[2];
@@ -1185,12 +1192,12 @@ __global__ void __launch_bounds__(FIELD_THREADS) k_field(MeshView M, BatchView<T
                                 (gr[2] + bg[2]) * (m[2] - bm[2]));
             const double mxa[3] = {m[1] * ic.a[2] - m[2] * ic.a[1], m[2] * ic.a[0] - m[0] * ic.a[2],
                                    m[0] * ic.a[1] - m[1] * ic.a[0]};
-            acc[Q_EEX] += ic.lam / 6.0 * (m[0] * kx[0] + m[1] * kx[1] + m[2] * kx[2]);
-            acc[Q_EAN] += ic.Q / 24.0 * vi * (mxa[0] * mxa[0] + mxa[1] * mxa[1] + mxa[2] * mxa[2]);
-            acc[Q_EZ] -= vi / 12.0 * (m[0] * ic.hz[0] + m[1] * ic.hz[1] + m[2] * ic.hz[2]);
-            acc[Q_ED] -= vi / 24.0 * (m[0] * hd[0] + m[1] * hd[1] + m[2] * hd[2]);
-            acc[Q_TORQUE] = fmax(acc[Q_TORQUE], sqrt(mh[0] * mh[0] + mh[1] * mh[1] + mh[2] * mh[2]));
-            acc[Q_HMAX] = fmax(acc[Q_HMAX], sqrt(Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2]));
+            acc[Q_EEX] += lam6 * (m[0] * kx[0] + m[1] * kx[1] + m[2] * kx[2]);
+            acc[Q_EAN] += q24 * vi * (mxa[0] * mxa[0] + mxa[1] * mxa[1] + mxa[2] * mxa[2]);
+            acc[Q_EZ] -= v12 * (m[0] * ic.hz[0] + m[1] * ic.hz[1] + m[2] * ic.hz[2]);
+            acc[Q_ED] -= v24 * (m[0] * hd[0] + m[1] * hd[1] + m[2] * hd[2]);
+            acc[Q_TORQUE] = fmax(acc[Q_TORQUE], mh[0] * mh[0] + mh[1] * mh[1] + mh[2] * mh[2]);
+            acc[Q_HMAX] = fmax(acc[Q_HMAX], Hv[0] * Hv[0] + Hv[1] * Hv[1] + Hv[2] * Hv[2]);
             double ss = 0.0, sy = 0.0, yy = 0.0, gg = 0.0;
             for (int c = 0; c < 3; ++c) {
                 const double sc = m[c] - bm[c], yc = g[c] - gb[c];
@@ -1266,6 +1273,8 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
         s.phase = PH_DONE;
         return;
     }
+    v[Q_TORQUE] = sqrt(v[Q_TORQUE]);   // the field kernel keeps squared maxima
+    v[Q_HMAX] = sqrt(v[Q_HMAX]);
     const double gg = v[Q_GG], torque = v[Q_TORQUE];
     const bool conv = so.grad_tol > 0.0 ? (gg < so.grad_tol) : (torque < so.tol);
     bool accept;
@@ -1460,9 +1469,9 @@ __global__ void k_trial(int N, BatchView<T> V) {
         const double ww = w0 * w0 + w1 * w1 + w2 * w2;
         const double mw = m0 * w0 + m1 * w1 + m2 * w2;
         const double c0 = m1 * w2 - m2 * w1, c1 = m2 * w0 - m0 * w2, c2 = m0 * w1 - m1 * w0;
-        const double den = 1.0 + ww;
-        put(((1.0 - ww) * m0 - 2.0 * c0 + 2.0 * mw * w0) / den, ((1.0 - ww) * m1 - 2.0 * c1 + 2.0 * mw * w1) / den,
-            ((1.0 - ww) * m2 - 2.0 * c2 + 2.0 * mw * w2) / den);
+        const double iden = 1.0 / (1.0 + ww);   // one FP64 division per node
+        put(((1.0 - ww) * m0 - 2.0 * c0 + 2.0 * mw * w0) * iden, ((1.0 - ww) * m1 - 2.0 * c1 + 2.0 * mw * w1) * iden,
+            ((1.0 - ww) * m2 - 2.0 * c2 + 2.0 * mw * w2) * iden);
     }
 }
 
