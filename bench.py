@@ -339,7 +339,7 @@ def run_reference(args, ws, rank):
 # kernels, from one ncu capture each of the batched workload (profiles/), used to
 # report the roofline's measured traffic per launch: (bytes/ms) x average launch ms.
 PROFILED_DRAM_BYTES_PER_MS = {
-    "fp32": (5.415e9 / 6.009, "profiles/k_pcg_fp32_batched64_n30.md"),
+    "fp32": (1387.8e6 / 9.128, "profiles/k_pcg_cluster_fp32_batched64_n30.md"),
 }
 
 
@@ -574,7 +574,7 @@ def run_ours(args, ws, rank, local):
     if d["kind"] in PROFILED_DRAM_BYTES_PER_MS and args.workload == "batched":
         rate, traffic_src = PROFILED_DRAM_BYTES_PER_MS[d["kind"]]
         traffic = rate * avg_ms
-    roofline = {"bound": "hbm", "kernel": f"k_pcg ({d['kind']} potential solves, forward + adjoint)",
+    roofline = {"bound": "hbm", "kernel": f"k_pcg_cluster ({d['kind']} potential solves, forward + adjoint)",
                 "bytes_per_row_system_iteration": pcg_bytes_per_row(d["kind"]),
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
