@@ -120,6 +120,11 @@ typedef struct {
                                and z of a cluster's systems fits its shared memory;
                                otherwise as 1).  0 takes 2 where it qualifies.
                                Results agree to rounding, not bit for bit */
+    int32_t use_graphs;     /* 1 (default): each chunk of check_every iterations is
+                               captured once as a CUDA graph (per batch, options and
+                               mesh operators) and replayed; the first chunk of a solve
+                               runs uncaptured.  0: kernels launched one by one.  The
+                               same kernels run in the same order: the same bits */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -354,6 +359,11 @@ int lbm_mesh_hmatrix(lbm_ctx* ctx, lbm_mesh mesh, double eps, double eta, int32_
 int lbm_bem_apply(lbm_ctx* ctx, lbm_mesh mesh, int32_t precision, int32_t batch, const double* x, double* y,
                   double* yt);
 
+/* CUDA-graph use of the context's solves: out[0] replays of captured chunks,
+ * out[1] chunks captured, out[2] captures the driver refused (those chunks run
+ * their kernels one by one).  The paper has no counterpart. */
+int lbm_graph_stats(lbm_ctx* ctx, int64_t out[3]);
+
 /* ---- device waits ------------------------------------------------------------
  * Every device-side wait of this context's kernels (the grid barrier of the
  * cooperative potential solves) gives up after a time limit, sets the
@@ -399,6 +409,12 @@ typedef struct {
 
 void lbm_default_serve_opts(lbm_serve_opts* o);
 int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt /* NULL: defaults */);
+/* Device-time trace of the serving loop (the paper has no counterpart): per
+ * chunk of iterations of a size group, its cube size and the chunk's start and
+ * end in milliseconds since lbm_serve_start, from CUDA events on the group's
+ * stream (so intervals of different groups that intersect ran concurrently on
+ * the device).  out: [max][3] host; *n: entries written (the latest ones). */
+int lbm_serve_trace(lbm_ctx* ctx, double* out, int64_t max, int64_t* n);
 /* Queue a request; returns immediately with its ticket. */
 int lbm_submit(lbm_ctx* ctx, const lbm_request* req, lbm_ticket* out);
 /* LBM_OK and the result (res->wall_ms = submit-to-completion latency) when the

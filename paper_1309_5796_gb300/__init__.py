@@ -37,7 +37,7 @@ class SolveOpts(C.Structure):
                 ("demag", C.c_int32), ("check_every", C.c_int32), ("switch_tol", C.c_double),
                 ("cg_tol_polish", C.c_double), ("cg_mixed_iter", C.c_int32), ("bb_rule", C.c_int32),
                 ("method", C.c_int32), ("omega", C.c_double), ("stall_iters", C.c_int32),
-                ("pcg_kernel", C.c_int32)]
+                ("pcg_kernel", C.c_int32), ("use_graphs", C.c_int32)]
 
 
 class ProfileStats(C.Structure):
@@ -110,6 +110,8 @@ SIGNATURES = [
     ("lbm_evaluate_noalloc", C.c_int, [_P, _I64, C.POINTER(Material), _DP, C.POINTER(SolveOpts),
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lbm_set_wait_limit", C.c_int, [_P, C.c_double, C.c_int32]),
+    ("lbm_graph_stats", C.c_int, [_P, C.POINTER(_I64)]),
+    ("lbm_serve_trace", C.c_int, [_P, _DP, _I64, C.POINTER(_I64)]),
     ("lbm_mesh_hmatrix", C.c_int, [_P, _I64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(_I64)]),
     ("lbm_bem_apply", C.c_int, [_P, _I64, C.c_int32, C.c_int32, _DP, _DP, _DP]),
     ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
@@ -300,6 +302,20 @@ class Context:
         y, yt = np.empty_like(xa), np.empty_like(xa)
         _check(lib().lbm_bem_apply(self._h, mesh, precision, batch, _dptr(xa), _dptr(y), _dptr(yt)))
         return (y[:, 0], yt[:, 0]) if one else (y, yt)
+
+    def graph_stats(self) -> dict:
+        """lbm_graph_stats: CUDA-graph replays, captures and refused captures."""
+        out = (C.c_int64 * 3)()
+        _check(lib().lbm_graph_stats(self._h, out))
+        return dict(replays=out[0], captures=out[1], refused=out[2])
+
+    def serve_trace(self, max_entries: int = 100000) -> np.ndarray:
+        """lbm_serve_trace: [k, 3] rows (cube size, start ms, end ms) of the serving
+        loop's chunks on the device."""
+        out = np.empty((max_entries, 3))
+        n = C.c_int64()
+        _check(lib().lbm_serve_trace(self._h, _dptr(out), max_entries, C.byref(n)))
+        return out[:n.value].copy()
 
     def set_wait_limit(self, seconds: float, unreachable: bool = False):
         """lbm_set_wait_limit: the device-wait limit of this context's kernels

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <array>
 #include <deque>
 #include <map>
 #include <memory>
@@ -20,6 +21,7 @@
 #include <stdexcept>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -109,6 +111,29 @@ struct Mesh {
     }
 };
 
+// One captured chunk of iterations of a batch (check_every calls of the trial
+// update, field evaluation and step decision), replayed as a CUDA graph.  Valid
+// for the batch, options and mesh operators it was captured with (`key`).
+struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> key;
+    int64_t launches = 0;                                  // kernel launches per replay
+    bool failed = false;                                   // capture not possible for `key`
+    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> prof;   // profiling event nodes
+    void clear() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        for (auto& e : prof) {
+            cudaEventDestroy(std::get<1>(e));
+            cudaEventDestroy(std::get<2>(e));
+        }
+        prof.clear();
+        key.clear();
+        launches = 0;
+        failed = false;
+    }
+};
+
 struct Inst {
     int64_t mesh = 0;
     int B = 0, precision = 0, tsize = 8;
@@ -125,6 +150,7 @@ struct Inst {
     std::vector<lbm_material> mats;
     std::vector<double> h;         // B*3 tesla
     size_t bytes = 0;
+    ChunkGraph graph;              // the batch's captured chunk of iterations
 };
 
 }  // namespace
@@ -156,6 +182,9 @@ struct lbm_ctx {
     std::map<int64_t, Inst*> insts;
     unsigned long long* sweeps = nullptr;   // device [4]
     double* fin = nullptr;                  // device [4096] grid-reduction results
+    cudaStream_t cap_stream = nullptr;      // where chunks are captured (lazy)
+    ChunkGraph* capturing = nullptr;        // the chunk being captured (profiling events become nodes)
+    int64_t graph_stats[3] = {0, 0, 0};     // replays, captures, captures refused
     Launch launch() { return Launch{stream, num_sms, bar, err, &launches, sweeps, fin, 0}; }
 };
 
@@ -180,19 +209,40 @@ struct ProfScope {
     cudaStream_t st;
     cudaEvent_t a = nullptr;
     ProfScope(lbm_ctx* c, int k, cudaStream_t s) : ctx(c), kind(k), st(s) {
-        if (ctx->prof && st == ctx->stream) {
+        if (ctx->prof && ctx->capturing && st == ctx->cap_stream) {
+            // captured: an event-record node of the graph, timed after each replay
+            cudaEventCreate(&a);
+            cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
+        } else if (ctx->prof && st == ctx->stream) {
             a = pool_get(ctx);
             cudaEventRecord(a, st);
         }
     }
     ~ProfScope() {
-        if (a) {
+        if (!a) return;
+        if (ctx->prof && ctx->capturing && st == ctx->cap_stream) {
+            cudaEvent_t b;
+            cudaEventCreate(&b);
+            cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+            ctx->capturing->prof.emplace_back(kind, a, b);
+        } else {
             cudaEvent_t b = pool_get(ctx);
             cudaEventRecord(b, st);
             ctx->ev_live.push_back(ProfEvent{kind, a, b});
         }
     }
 };
+
+// After a replay of a captured chunk and a synchronisation: its event nodes' times.
+void prof_harvest_graph(lbm_ctx* ctx, const ChunkGraph& g) {
+    for (const auto& e : g.prof) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, std::get<1>(e), std::get<2>(e)) == cudaSuccess) {
+            ctx->prof_ms[std::get<0>(e)] += ms;
+            ctx->prof_launches[std::get<0>(e)] += 1;
+        }
+    }
+}
 
 // After a stream synchronisation: fold the recorded event pairs into the totals.
 void prof_harvest(lbm_ctx* ctx) {
@@ -329,6 +379,7 @@ void free_mesh(Mesh* m) {
 }
 
 void free_inst(Inst* I) {
+    I->graph.clear();
     if (I->polish) free_inst(I->polish);
     if (I->tc_scratch && I->owns_tc_scratch) cudaFree(I->tc_scratch);
     void* ptrs[] = {I->vec, I->part, I->st, I->ic, I->staged, I->staged_u};
@@ -385,7 +436,7 @@ int check_opts(const lbm_solve_opts& o) {
         o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
         !(o.cg_tol_polish > 0) || o.bb_rule < 0 || o.bb_rule > 3 || o.method < 0 || o.method > 1 ||
         (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)) || o.stall_iters < 0 || o.pcg_kernel < 0 ||
-        o.pcg_kernel > 2)
+        o.pcg_kernel > 2 || o.use_graphs < 0 || o.use_graphs > 1)
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -443,6 +494,78 @@ int iterate_once(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, co
     return LBM_OK;
 }
 
+// `chunk` iterations of a batch: captured once as a CUDA graph (on the
+// context's capture stream, or on `cap` when given) and replayed, or launched
+// one by one (use_graphs == 0, the first chunk of a run -- it performs any
+// one-time set-up: kernel attributes, occupancy queries, autotuning -- or a
+// capture that the driver refused).  The graph is valid for the batch, options
+// and the mesh's operators it was captured with; *replayed tells the caller
+// to read the graph's profiling nodes after its synchronisation.
+template <typename T>
+int run_chunk(lbm_ctx* ctx, const Launch& L, const Mesh& M, Inst* I, const BatchView<T>& V, const lbm_solve_opts& o,
+              const StepOpts& so, int nblk_field, int chunk, bool first, cudaStream_t cap, bool* replayed) {
+    *replayed = false;
+    ChunkGraph& g = I->graph;
+    std::vector<char> key(sizeof(lbm_solve_opts) + 8 * sizeof(int64_t));
+    {
+        const int64_t k[8] = {chunk, (int64_t)sizeof(T), I->B, (int64_t)(intptr_t)M.hm, (int64_t)(intptr_t)M.B32lo,
+                              (int64_t)(intptr_t)M.tcA, ctx->prof ? 1 : 0, (int64_t)(intptr_t)V.m};
+        memcpy(key.data(), &o, sizeof(lbm_solve_opts));
+        memcpy(key.data() + sizeof(lbm_solve_opts), k, sizeof k);
+    }
+    const bool use = o.use_graphs != 0 && !first && chunk > 1 && !(g.failed && g.key == key);
+    if (use && !(g.exec && g.key == key)) {
+        g.clear();
+        if (!cap) {
+            if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cap = ctx->cap_stream;
+        }
+        Launch Lc = L;
+        Lc.stream = cap;
+        const int64_t l0 = ctx->launches;
+        ctx->capturing = &g;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int rc = LBM_OK;
+        if (e == cudaSuccess)
+            for (int k = 0; k < chunk && rc == LBM_OK; ++k) rc = iterate_once<T>(ctx, Lc, M, *I, V, o, so, nblk_field);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap, &graph) : e;
+        ctx->capturing = nullptr;
+        const int64_t per = ctx->launches - l0;
+        ctx->launches = l0;
+        if (e2 == cudaSuccess && rc == LBM_OK && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        else e = e2 != cudaSuccess ? e2 : cudaErrorStreamCaptureInvalidated;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();   // a refused capture leaves its error here
+        g.key = key;
+        ctx->graph_stats[1] += 1;
+        if (e != cudaSuccess || !g.exec) {
+            ctx->graph_stats[2] += 1;
+            for (auto& pe : g.prof) {
+                cudaEventDestroy(std::get<1>(pe));
+                cudaEventDestroy(std::get<2>(pe));
+            }
+            g.prof.clear();
+            g.exec = nullptr;
+            g.failed = true;   // plain launches for these settings from now on
+        } else {
+            g.launches = per;
+        }
+    }
+    if (use && g.exec && g.key == key) {
+        CK(cudaGraphLaunch(g.exec, L.stream));
+        ctx->launches += g.launches;
+        ctx->graph_stats[0] += 1;
+        *replayed = true;
+        return LBM_OK;
+    }
+    for (int k = 0; k < chunk; ++k) {
+        const int e = iterate_once<T>(ctx, L, M, *I, V, o, so, nblk_field);
+        if (e) return e;
+    }
+    return LBM_OK;
+}
+
 void fill_result(const InstState& s, const InstConst& c, lbm_result& r, double wall_ms) {
     r.status = s.status;
     r.iterations = s.iters;
@@ -476,12 +599,13 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
     const int64_t max_loops = (int64_t)(oo.max_iter + 1) * (oo.max_backtracks + 2) + 2;
     int64_t loops = 0;
     int rc = LBM_OK;
+    bool first = true;
     while (true) {
         const int chunk = evaluate_only ? 1 : oo.check_every;
-        for (int k = 0; k < chunk; ++k) {
-            int e = iterate_once<T>(ctx, L, M, *I, V, oo, so, nblk_field);
-            if (e) return e;
-        }
+        bool replayed = false;
+        int e = run_chunk<T>(ctx, L, M, I, V, oo, so, nblk_field, chunk, first, nullptr, &replayed);
+        if (e) return e;
+        first = false;
         loops += chunk;
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(hs.data(), I->st, sizeof(InstState) * I->B, cudaMemcpyDeviceToHost, ctx->stream));
@@ -489,6 +613,7 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
         CK(cudaMemcpyAsync(&errw, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         prof_harvest(ctx);
+        if (replayed && ctx->prof) prof_harvest_graph(ctx, I->graph);
         if (errw) {
             cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream);
             return fail(LBM_E_TIMEOUT, "a device-side wait ran out of time (error word %d)", errw);
@@ -645,6 +770,8 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->method = 0;
     o->omega = 1.0;
     o->stall_iters = precision == LBM_FP64 ? 0 : 200;
+    o->pcg_kernel = 0;
+    o->use_graphs = 1;
     if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
@@ -705,6 +832,7 @@ int lbm_destroy(lbm_ctx* ctx) {
     cudaFree(ctx->sweeps);
     cudaFree(ctx->fin);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return LBM_OK;
     LBM_CATCH
@@ -714,6 +842,14 @@ int lbm_launch_count(lbm_ctx* ctx, int64_t* count) {
     LBM_TRY
     if (!ctx || !count) return fail(LBM_E_INVALID, "null argument");
     *count = ctx->launches;
+    return LBM_OK;
+    LBM_CATCH
+}
+
+int lbm_graph_stats(lbm_ctx* ctx, int64_t out[3]) {
+    LBM_TRY
+    if (!ctx || !out) return fail(LBM_E_INVALID, "null argument");
+    for (int k = 0; k < 3; ++k) out[k] = ctx->graph_stats[k];
     return LBM_OK;
     LBM_CATCH
 }
@@ -1852,6 +1988,8 @@ struct Ticket {
 struct Group {
     int n = 0;
     double cell = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // the current chunk's start and end on the group's stream
+    InstState* pin = nullptr;          // page-locked staging of both batches' states (asynchronous copies)
     int64_t mesh_id = 0, i32_id = 0, i64_id = 0;
     Inst *I32 = nullptr, *I64 = nullptr;
     cudaStream_t stream = nullptr;
@@ -1863,6 +2001,7 @@ struct Group {
     std::vector<int64_t> t32, t64;     // ticket of each slot (-1: free)
     std::vector<InstState> h32, h64;   // states read back each poll
     std::vector<char> fresh32, fresh64;
+    bool ran32 = false, ran64 = false;  // a chunk of the batch ran (its set-up is done)
     double last_used = 0;
     size_t bytes = 0;
     int occupied() const {
@@ -1888,6 +2027,8 @@ struct Server {
     std::map<int, Group*> groups;
     int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_stalls = 0, n_evicted = 0;
     std::vector<double> pinned_m;      // host staging
+    cudaEvent_t t_ref = nullptr;       // device-time origin of the trace
+    std::deque<std::array<double, 3>> trace;   // per chunk: cube size, start, end (ms)
 };
 
 Launch group_launch(lbm_ctx* ctx, Group& G, int max_blocks) {
@@ -1902,6 +2043,9 @@ void group_free(lbm_ctx* ctx, Group* G) {
     void* ptrs[] = {G->bar, G->err, G->fin, G->sweeps, G->staged};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (G->ev0) cudaEventDestroy(G->ev0);
+    if (G->ev1) cudaEventDestroy(G->ev1);
+    if (G->pin) cudaFreeHost(G->pin);
     if (G->stream) cudaStreamDestroy(G->stream);
     delete G;
 }
@@ -1943,6 +2087,8 @@ Group* group_get(Server& S, int n, double cell) {
         return (Group*)nullptr;
     };
     if (cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking) != cudaSuccess) return bad(0);
+    if (cudaEventCreate(&G->ev0) != cudaSuccess || cudaEventCreate(&G->ev1) != cudaSuccess) return bad(0);
+    if (cudaMallocHost(&G->pin, sizeof(InstState) * 2 * (size_t)B) != cudaSuccess) return bad(0);
     if (cudaMalloc(&G->bar, 64) != cudaSuccess || cudaMalloc(&G->err, 64) != cudaSuccess ||
         cudaMalloc(&G->fin, sizeof(double) * 4096) != cudaSuccess || cudaMalloc(&G->sweeps, 64) != cudaSuccess)
         return bad(0);
@@ -2110,25 +2256,45 @@ void serve_loop(Server* Sp) {
             bool any32 = false, any64 = false;
             for (int b = 0; b < (int)G->t32.size(); ++b) any32 |= G->t32[b] >= 0 && (G->fresh32[b] || G->h32[b].phase != PH_DONE);
             for (int b = 0; b < (int)G->t64.size(); ++b) any64 |= G->t64[b] >= 0 && (G->fresh64[b] || G->h64[b].phase != PH_DONE);
-            for (int k = 0; k < S.opt.chunk; ++k) {
-                if (any32) {
-                    BatchView<float> V = batch_view<float>(ctx, M, *G->I32, false);
-                    iterate_once<float>(ctx, L, M, *G->I32, V, o1, so1, field_blocks(L, M.view(), G->I32->B));
-                }
-                if (any64) {
-                    BatchView<double> V = batch_view<double>(ctx, M, *G->I64, false);
-                    // FP64 batch: mixed requests finish with the polish options,
-                    // plain FP64 requests share them except for the BEM matrix
-                    iterate_once<double>(ctx, L, M, *G->I64, V, o2, so2, field_blocks(L, M.view(), G->I64->B));
-                }
+            // each batch's chunk is captured once as a graph (on the group's own
+            // stream) and replayed; the first chunk of a batch runs uncaptured
+            bool rep = false;
+            cudaEventRecord(G->ev0, G->stream);
+            if (any32) {
+                BatchView<float> V = batch_view<float>(ctx, M, *G->I32, false);
+                run_chunk<float>(ctx, L, M, G->I32, V, o1, so1, field_blocks(L, M.view(), G->I32->B), S.opt.chunk,
+                                 !G->ran32, G->stream, &rep);
+                G->ran32 = true;
             }
-            cudaMemcpyAsync(G->h32.data(), G->I32->st, sizeof(InstState) * G->t32.size(), cudaMemcpyDeviceToHost, G->stream);
-            cudaMemcpyAsync(G->h64.data(), G->I64->st, sizeof(InstState) * G->t64.size(), cudaMemcpyDeviceToHost, G->stream);
+            if (any64) {
+                BatchView<double> V = batch_view<double>(ctx, M, *G->I64, false);
+                // FP64 batch: mixed requests finish with the polish options,
+                // plain FP64 requests share them except for the BEM matrix
+                run_chunk<double>(ctx, L, M, G->I64, V, o2, so2, field_blocks(L, M.view(), G->I64->B), S.opt.chunk,
+                                  !G->ran64, G->stream, &rep);
+                G->ran64 = true;
+            }
+            cudaEventRecord(G->ev1, G->stream);
+            // page-locked staging: the copies stay asynchronous, so the next
+            // group's chunk is queued while this one runs
+            cudaMemcpyAsync(G->pin, G->I32->st, sizeof(InstState) * G->t32.size(), cudaMemcpyDeviceToHost, G->stream);
+            cudaMemcpyAsync(G->pin + G->t32.size(), G->I64->st, sizeof(InstState) * G->t64.size(),
+                            cudaMemcpyDeviceToHost, G->stream);
         }
         // ---- retire and move -----------------------------------------------
         std::lock_guard<std::mutex> lk(S.mu);
         for (Group* G : active) {
             cudaError_t e = cudaStreamSynchronize(G->stream);
+            std::copy(G->pin, G->pin + G->t32.size(), G->h32.begin());
+            std::copy(G->pin + G->t32.size(), G->pin + G->t32.size() + G->t64.size(), G->h64.begin());
+            {   // the chunk's device-time interval, relative to the server's start
+                float a = 0.f, b = 0.f;
+                if (S.t_ref && cudaEventElapsedTime(&a, S.t_ref, G->ev0) == cudaSuccess &&
+                    cudaEventElapsedTime(&b, S.t_ref, G->ev1) == cudaSuccess) {
+                    S.trace.push_back({(double)G->n, (double)a, (double)b});
+                    if (S.trace.size() > 100000) S.trace.pop_front();
+                }
+            }
             int errw = 0;
             cudaMemcpy(&errw, G->err, sizeof errw, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess || errw) {
@@ -2211,6 +2377,12 @@ int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt) {
     if (S->opt.max_pcg_blocks <= 0) S->opt.max_pcg_blocks = ctx->num_sms / 4 > 0 ? ctx->num_sms / 4 : 1;
     int rc = check_opts(S->opt.opt);
     if (rc) { delete S; return rc; }
+    CK(cudaSetDevice(ctx->device));
+    if (cudaEventCreate(&S->t_ref) != cudaSuccess || cudaEventRecord(S->t_ref, ctx->stream) != cudaSuccess) {
+        if (S->t_ref) cudaEventDestroy(S->t_ref);
+        delete S;
+        return fail(LBM_E_CUDA, "serving trace event");
+    }
     ctx->server = S;
     S->worker = std::thread(serve_loop, S);
     return LBM_OK;
@@ -2304,8 +2476,23 @@ int lbm_serve_stop(lbm_ctx* ctx) {
     if (S->worker.joinable()) S->worker.join();
     for (auto& kv : S->groups) group_free(ctx, kv.second);
     S->groups.clear();
+    if (S->t_ref) cudaEventDestroy(S->t_ref);
     ctx->server = nullptr;
     delete S;
+    return LBM_OK;
+    LBM_CATCH
+}
+
+int lbm_serve_trace(lbm_ctx* ctx, double* out, int64_t max, int64_t* n) {
+    LBM_TRY
+    if (!ctx || !ctx->server || !n || max < 0 || (max > 0 && !out)) return fail(LBM_E_INVALID, "bad argument or not serving");
+    Server* S = ctx->server;
+    std::lock_guard<std::mutex> lk(S->mu);
+    const int64_t have = (int64_t)S->trace.size();
+    const int64_t k = have < max ? have : max;
+    for (int64_t i = 0; i < k; ++i)
+        for (int c = 0; c < 3; ++c) out[3 * i + c] = S->trace[(size_t)(have - k + i)][c];
+    *n = k;
     return LBM_OK;
     LBM_CATCH
 }

@@ -25,6 +25,10 @@
 // iterated in FP32 with the FP64 residual recomputed at every restart.
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "solver_common.cuh"
 
 namespace lbm {
@@ -650,12 +654,28 @@ cudaError_t launch_cluster(const Launch& L, PcgArgs<T>& a, bool* ok) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // clusters resident at once, queried once per (kernel, device, shared memory)
+    // and cached: no query runs while a chunk of iterations is being captured
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
     int ncl = 0;
-    e = cudaOccupancyMaxActiveClusters(&ncl, (const void*)fn, &cfg);
-    if (e != cudaSuccess || ncl < nclusters) {
-        cudaGetLastError();
-        return cudaSuccess;   // the next shape, or the grid-wide kernel
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto key = std::make_tuple((const void*)fn, dev, smem);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            e = cudaOccupancyMaxActiveClusters(&ncl, (const void*)fn, &cfg);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ncl = 0;
+            }
+            it = cache.emplace(key, ncl).first;
+        }
+        ncl = it->second;
     }
+    if (ncl < nclusters) return cudaSuccess;   // the next shape, or the grid-wide kernel
     *ok = true;
     return cudaLaunchKernelEx(&cfg, fn, a, rpc);
 }

@@ -78,3 +78,30 @@ def test_fp64_requests_and_latency(ctx):
     assert all(r["status"] == lbm.LBM_OK and r["torque"] < 1e-6 for r in res)
     assert all(r["wall_ms"] > 0 for r in res)
     assert pending is None or pending[0]["status"] == lbm.LBM_OK
+
+
+def test_size_groups_overlap_on_the_device(ctx):
+    """Requests of three cube sizes served together: the serving loop's device
+    trace (CUDA events on each size group's stream) has chunks of different
+    groups whose intervals intersect, i.e. their kernels ran concurrently."""
+    from synth.inputs import m_perturbed, tilted_axis
+    ctx.serve_start(slots=16, chunk=8)
+    try:
+        tickets = []
+        for k, n in enumerate((10, 14, 18) * 3):
+            N = (n + 1) ** 3
+            tickets.append(ctx.submit(n, 2e-9, JS_T, A_JM, K1_JM3, tilted_axis(2.0 + k, 0.3 * k),
+                                      np.array([0.0, 0.0, -1.0 - 0.4 * k]), m_perturbed(N, 4000 + k)))
+        res = [ctx.wait(t, None, timeout_s=600)[0] for t in tickets]
+        tr = ctx.serve_trace()
+    finally:
+        ctx.serve_stop()
+    assert all(r["status"] == lbm.LBM_OK for r in res)
+    sizes = sorted(set(tr[:, 0].astype(int)))
+    assert len(sizes) == 3
+    overlaps = 0
+    for i in range(len(tr)):
+        for j in range(i + 1, len(tr)):
+            if tr[i, 0] != tr[j, 0] and max(tr[i, 1], tr[j, 1]) < min(tr[i, 2], tr[j, 2]):
+                overlaps += 1
+    assert overlaps > 0
