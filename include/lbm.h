@@ -348,6 +348,33 @@ int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_material* mat, c
 int lbm_mesh_hmatrix(lbm_ctx* ctx, lbm_mesh mesh, double eps, double eta, int32_t n_min, int32_t threads,
                      int64_t info[4]);
 
+/* Open boundary by space transformation (Sec. 3.1: the paper's own
+ * steepest-descent solver maps a shell onto the exterior instead of coupling
+ * FEM with BEM).  Attaches to a Kuhn-cube mesh (lbm_mesh_create) one Kuhn grid
+ * of spacing h over the magnet [0, n]^3, an air layer a cells deep and a shell
+ * s cells deep (max-norm radii R1 = n/2 + a, R2 = R1 + s about the magnet's
+ * centre); the shell is mapped onto everything outside R1 by
+ * x' - c = g(rho)/rho (x - c), g = R1 (R2 - R1)/(R2 - rho), its tetrahedra carry
+ * the tensor M = |det J| J^-1 J^-T of the map at their centroids, and the
+ * potential vanishes on the outer face (the image of infinity).  From then on
+ * every stray-field evaluation of the mesh's instances (minimise, evaluate,
+ * serving; every precision) solves the one symmetric system K_grid u = b on
+ * the grid (FP64 Jacobi-PCG on the device, cg_tol / cg_max_iter of the solve
+ * options, warm-started from the instance's previous grid potential) instead
+ * of the two Poisson solves and the boundary product; its iterations count as
+ * cg_iters1 and its time as the first potential solve.  The field at the
+ * magnet's nodes is the exact gradient field of the discrete stray-field
+ * energy (b^T K_grid^-1 b)/2 of this truncated, transformed problem.
+ * a = s = 0 detaches it (back to FEM/BEM).  Must be called while the mesh has
+ * no instances (their vectors are sized by it).  lbm_evaluate_noalloc refuses
+ * such a mesh.
+ * info (nullable, int64[3]): grid nodes, stiffness entries, shell tetrahedra.
+ * Builds the grid and its stiffness on the host (seconds for n + 2(a + s)
+ * near 100), uploads it and waits.  Returns LBM_E_INVALID for a general mesh,
+ * a mesh with instances, a or s < 1 (unless both 0), or n + 2(a + s) > 200;
+ * LBM_E_OOM when device memory runs out. */
+int lbm_mesh_shell(lbm_ctx* ctx, lbm_mesh mesh, int32_t a, int32_t s, int64_t info[3]);
+
 /* The boundary operator of the mesh (dense, or the hierarchical form when
  * built) applied to `batch` host vectors, as the solver applies it (Sec. 3.1,
  * the a3 step): y = B x and yt = B^T x.  precision: LBM_FP64 (FP64 vectors and

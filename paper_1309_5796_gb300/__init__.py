@@ -113,6 +113,7 @@ SIGNATURES = [
     ("lbm_graph_stats", C.c_int, [_P, C.POINTER(_I64)]),
     ("lbm_serve_trace", C.c_int, [_P, _DP, _I64, C.POINTER(_I64)]),
     ("lbm_mesh_hmatrix", C.c_int, [_P, _I64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(_I64)]),
+    ("lbm_mesh_shell", C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(_I64)]),
     ("lbm_bem_apply", C.c_int, [_P, _I64, C.c_int32, C.c_int32, _DP, _DP, _DP]),
     ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
     ("lbm_serve_start", C.c_int, [_P, C.POINTER(ServeOpts)]),
@@ -291,6 +292,13 @@ class Context:
         _check(lib().lbm_mesh_hmatrix(self._h, mesh, float(eps), float(eta), int(n_min), int(th), out))
         return dict(stored=out[0], dense=out[1], leaves=out[2], low_rank=out[3],
                     fraction=(out[0] / out[1]) if out[1] else 0.0)
+
+    def mesh_shell(self, mesh: int, a: int, s: int) -> dict:
+        """lbm_mesh_shell: attach the space-transformation open boundary (air a
+        cells deep, shell s cells deep; a = s = 0 detaches it)."""
+        out = (C.c_int64 * 3)()
+        _check(lib().lbm_mesh_shell(self._h, mesh, int(a), int(s), out))
+        return dict(grid_nodes=out[0], nnz=out[1], shell_tets=out[2])
 
     def bem_apply(self, mesh: int, x, precision=LBM_FP64):
         """lbm_bem_apply: (B x, B^T x) for x of shape [nb] or [nb, batch]."""

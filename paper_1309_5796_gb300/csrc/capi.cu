@@ -84,6 +84,8 @@ struct Mesh {
     float* B32lo = nullptr;                   // fp32(B64 - B32) for FP64 batches of >1 instance (lazy)
     HMDevice* hm = nullptr;                   // hierarchical form of B (lbm_mesh_hmatrix), or null
     std::vector<void*> hm_mem;                // its device allocations
+    ShellDev* shell = nullptr;                // space-transformation boundary (lbm_mesh_shell), or null
+    std::vector<void*> shell_mem;             // its device allocations
     float *tcA = nullptr, *tcAT = nullptr;   // padded FP32 B and B^T for the tensor-core path (lazy)
     // general meshes (lbm_mesh_upload; n == 0)
     bool gen = false;
@@ -102,6 +104,7 @@ struct Mesh {
         v.kptr = kptr; v.kent = kent;
         v.B64 = B64; v.B32 = B32; v.B32lo = B32lo;
         v.hm = hm;
+        v.shell = shell;
         v.vsum = gen ? vsum : 24.0 * (double)n * n * n;
         v.cell = cell;
         v.gen = gen ? 1 : 0;
@@ -261,7 +264,7 @@ void prof_harvest(lbm_ctx* ctx) {
 // Byte offsets of the per-instance arrays inside one allocation; every array
 // starts on a 256-byte boundary (the PCG reads 8- and 16-byte vectors).
 struct VecLayout {
-    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, m32, bvec, total;
+    size_t m, g, hout, U1, U2, r, z, p, q, ub_in, ub_out, bem_part, m32, bvec, shx, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -288,6 +291,8 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.bem_part = take(8 * (32 * nb > df ? 32 * nb : df));
     L.m32 = tsize == 4 ? take(4 * N * 3 * B) : 0;
     L.bvec = take(8 * N * B);
+    // space-transformation boundary: grid potential and CG vectors, FP64 in every mode
+    L.shx = M.shell ? take(8 * 5 * (size_t)M.shell->Ng * B) : 0;
     L.total = o;
     return L;
 }
@@ -313,6 +318,7 @@ BatchView<T> batch_view(const lbm_ctx* ctx, const Mesh& M, const Inst& I, bool w
     v.bem_part = (T*)(base + L.bem_part);
     v.m32 = sizeof(T) == 4 ? (float*)(base + L.m32) : nullptr;
     v.bvec = (double*)(base + L.bvec);
+    v.shx = M.shell ? (double*)(base + L.shx) : nullptr;
     v.part = I.part;
     v.st = I.st;
     v.ic = I.ic;
@@ -328,6 +334,7 @@ int zero_potentials(lbm_ctx* ctx, const Mesh& M, const Inst& I) {
     const size_t bytes = (size_t)I.tsize * M.N * 2 * I.B;
     CK(cudaMemsetAsync((char*)I.vec + L.U1, 0, bytes, ctx->stream));
     CK(cudaMemsetAsync((char*)I.vec + L.U2, 0, bytes, ctx->stream));
+    if (M.shell) CK(cudaMemsetAsync((char*)I.vec + L.shx, 0, sizeof(double) * M.shell->Ng * I.B, ctx->stream));
     return LBM_OK;
 }
 
@@ -368,8 +375,16 @@ int hm_reserve(lbm_ctx* ctx, Mesh* M, int B) {
     return LBM_OK;
 }
 
+void free_shell(Mesh* m) {
+    for (void* p : m->shell_mem) cudaFree(p);
+    m->shell_mem.clear();
+    delete m->shell;
+    m->shell = nullptr;
+}
+
 void free_mesh(Mesh* m) {
     free_hm(m);
+    free_shell(m);
     void* ptrs[] = {m->rowptr, m->col, m->pkA, m->pkB, m->node, m->bidx, m->tris, m->inc_ptr, m->inc_slot,
                     m->kptr, m->kent, m->B64, m->B32, m->B32lo, m->tcA, m->tcAT, m->tets, m->xyz, m->gA64, m->gB64,
                     m->gA32, m->gB32, m->gk64, m->gV, m->gd64, m->gk32, m->gd32};
@@ -446,7 +461,13 @@ template <typename T>
 int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, const BatchView<T>& V,
                const lbm_solve_opts& o) {
     MeshView mv = M.view();
-    if (o.demag) {
+    if (o.demag && M.shell) {
+        // open boundary by space transformation: one symmetric solve on the grid
+        ProfScope ps(ctx, 1 + (sizeof(T) == 8 ? 5 : 0), L.stream);
+        rhs_eval<T>(L, mv, V);
+        const int e = shell_solve<T>(L, mv, V, o.cg_tol, o.cg_max_iter);
+        if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    } else if (o.demag) {
         int e;
         const int k64 = sizeof(T) == 8 ? 5 : 0;
         {
@@ -506,10 +527,11 @@ int run_chunk(lbm_ctx* ctx, const Launch& L, const Mesh& M, Inst* I, const Batch
               const StepOpts& so, int nblk_field, int chunk, bool first, cudaStream_t cap, bool* replayed) {
     *replayed = false;
     ChunkGraph& g = I->graph;
-    std::vector<char> key(sizeof(lbm_solve_opts) + 8 * sizeof(int64_t));
+    std::vector<char> key(sizeof(lbm_solve_opts) + 9 * sizeof(int64_t));
     {
-        const int64_t k[8] = {chunk, (int64_t)sizeof(T), I->B, (int64_t)(intptr_t)M.hm, (int64_t)(intptr_t)M.B32lo,
-                              (int64_t)(intptr_t)M.tcA, ctx->prof ? 1 : 0, (int64_t)(intptr_t)V.m};
+        const int64_t k[9] = {chunk, (int64_t)sizeof(T), I->B, (int64_t)(intptr_t)M.hm, (int64_t)(intptr_t)M.B32lo,
+                              (int64_t)(intptr_t)M.tcA, ctx->prof ? 1 : 0, (int64_t)(intptr_t)V.m,
+                              (int64_t)(intptr_t)M.shell};
         memcpy(key.data(), &o, sizeof(lbm_solve_opts));
         memcpy(key.data() + sizeof(lbm_solve_opts), k, sizeof k);
     }
@@ -709,6 +731,9 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
         k_widen<<<4 * ctx->num_sms, 256, 0, ctx->stream>>>((const float*)((const char*)I->vec + L32.U2),
                                                            (double*)((char*)P->vec + L64.U2), npot);
         ctx->launches += 2;
+        if (M.shell)   // the grid potential (FP64 in both phases) warm-starts the FP64 phase's solves
+            CK(cudaMemcpyAsync((char*)P->vec + L64.shx, (const char*)I->vec + L32.shx,
+                               sizeof(double) * M.shell->Ng * B, cudaMemcpyDeviceToDevice, ctx->stream));
         lbm_solve_opts o2 = o;
         o2.cg_tol = o.cg_tol_polish;
         o2.stall_iters = 0;   // the FP64 phase runs to tol or max_iter
@@ -1364,6 +1389,74 @@ int lbm_mesh_hmatrix(lbm_ctx* ctx, lbm_mesh mesh, double eps, double eta, int32_
     LBM_CATCH
 }
 
+int lbm_mesh_shell(lbm_ctx* ctx, lbm_mesh mesh, int32_t a, int32_t s, int64_t info[3]) {
+    LBM_TRY
+    Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
+    if (!M) return fail(LBM_E_INVALID, "lbm_mesh_shell: unknown mesh");
+    if (M->gen) return fail(LBM_E_INVALID, "lbm_mesh_shell: only Kuhn-cube meshes (lbm_mesh_create)");
+    for (auto& kv : ctx->insts)
+        if (kv.second->mesh == mesh)
+            return fail(LBM_E_INVALID, "lbm_mesh_shell: the mesh has instances (attach or detach before creating them)");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (a == 0 && s == 0) {   // back to the FEM/BEM coupling
+        free_shell(M);
+        if (info) info[0] = info[1] = info[2] = 0;
+        return LBM_OK;
+    }
+    if (a < 1 || s < 1) return fail(LBM_E_INVALID, "lbm_mesh_shell: a and s must be at least 1 (or both 0)");
+    if ((int64_t)M->n + 2 * ((int64_t)a + s) > 200)
+        return fail(LBM_E_INVALID, "lbm_mesh_shell: grid too large (n + 2(a + s) > 200)");
+    ShellGrid G;
+    const std::string why = host_shell_setup(M->n, a, s, 1.0, G);   // K in units of h
+    if (!why.empty()) return fail(LBM_E_INVALID, "lbm_mesh_shell: %s", why.c_str());
+    const int Ng = (int)(G.rowptr.size() - 1), nnz = (int)G.col.size();
+    std::vector<double> val(nnz), dinv(Ng, 0.0);
+    std::vector<int> gnode(Ng, -1);
+    for (int k = 0; k < nnz; ++k) val[k] = 6.0 * G.K[k];
+    for (int v : G.outer) gnode[v] = -2;
+    for (size_t i = 0; i < G.magnet.size(); ++i) gnode[G.magnet[i]] = (int)i;
+    for (int r = 0; r < Ng; ++r) {
+        if (gnode[r] == -2) continue;
+        const int* b = G.col.data() + G.rowptr[r];
+        const int* e = G.col.data() + G.rowptr[r + 1];
+        const int* d = std::lower_bound(b, e, r);
+        if (d == e || *d != r || !(val[d - G.col.data()] > 0.0))
+            return fail(LBM_E_INVALID, "lbm_mesh_shell: stiffness without a positive diagonal");
+        dinv[r] = 1.0 / val[d - G.col.data()];
+    }
+    free_shell(M);
+    ShellDev* S = new ShellDev();
+    M->shell = S;
+    auto up = [&](const void* src, size_t bytes) -> void* {
+        void* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+        M->shell_mem.push_back(d);
+        if (cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return nullptr;
+        return d;
+    };
+    S->Ng = Ng;
+    S->nnz = nnz;
+    S->rowptr = (const int*)up(G.rowptr.data(), sizeof(int) * G.rowptr.size());
+    S->col = (const int*)up(G.col.data(), sizeof(int) * G.col.size());
+    S->val = (const double*)up(val.data(), sizeof(double) * val.size());
+    S->dinv = (const double*)up(dinv.data(), sizeof(double) * dinv.size());
+    S->gnode = (const int*)up(gnode.data(), sizeof(int) * gnode.size());
+    S->magnet = (const int*)up(G.magnet.data(), sizeof(int) * G.magnet.size());
+    if (!S->rowptr || !S->col || !S->val || !S->dinv || !S->gnode || !S->magnet) {
+        free_shell(M);
+        return fail(LBM_E_OOM, "lbm_mesh_shell: device allocation failed");
+    }
+    CK(cudaStreamSynchronize(ctx->stream));   // the host vectors go out of scope
+    if (info) {
+        info[0] = Ng;
+        info[1] = nnz;
+        info[2] = (int64_t)G.shell_tets;
+    }
+    return LBM_OK;
+    LBM_CATCH
+}
+
 int lbm_bem_apply(lbm_ctx* ctx, lbm_mesh mesh, int32_t precision, int32_t batch, const double* x, double* y,
                   double* yt) {
     LBM_TRY
@@ -1761,6 +1854,9 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     LBM_TRY
     Mesh* M = ctx ? get_mesh(ctx, mesh) : nullptr;
     if (!M || !mat || !h_ext || !d_m) return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: bad argument");
+    if (M->shell)
+        return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: the mesh has a space-transformation boundary (its grid "
+                    "vectors are not part of the static scratch)");
     if ((size_t)M->N > NOALLOC_MAX_NODES || (size_t)M->nb > NOALLOC_MAX_SURFACE)
         return fail(LBM_E_INVALID, "lbm_evaluate_noalloc: mesh of %d nodes / %d surface nodes exceeds the "
                     "static scratch (%zu nodes / %zu surface nodes)", M->N, M->nb, NOALLOC_MAX_NODES,
@@ -1952,6 +2048,15 @@ __global__ void k_slot_zero_pot(T* U1, T* U2, int N, int B, int b) {
         U2[(size_t)i * C + b] = T(0);
         U2[(size_t)i * C + B + b] = T(0);
     }
+}
+
+// column bd of a batch's space-transformation grid potential [Ng][Bd]: column
+// bs of src ([Ng][Bs], the FP32 phase's potential: the FP64 phase's warm start),
+// or zero (src null: a new magnetisation starts from zero)
+__global__ void k_slot_shell(const double* __restrict__ src, int Bs, int bs, double* __restrict__ dst, int Bd, int bd,
+                             int Ng) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Ng; i += gridDim.x * blockDim.x)
+        dst[(size_t)i * Bd + bd] = src ? src[(size_t)i * Bs + bs] : 0.0;
 }
 
 // move slot bs of an FP32 batch to slot bd of an FP64 batch: m (base point)
@@ -2161,6 +2266,11 @@ bool admit(Server& S, Group& G, int64_t t, Ticket& T) {
                                                          (float*)((char*)I->vec + L.U2), N, B, b);
     }
     ctx->launches += 3;
+    if (M.shell) {
+        const VecLayout L = vec_layout(M, B, fp64 ? 8 : 4);
+        k_slot_shell<<<64, 256, 0, G.stream>>>(nullptr, 0, 0, (double*)((char*)I->vec + L.shx), B, b, M.shell->Ng);
+        ctx->launches += 1;
+    }
     set_slot_consts(I, b, T.req.mat, T.req.h, G.cell, G.stream);
     slots[b] = t;
     (fp64 ? G.fresh64 : G.fresh32)[b] = 1;
@@ -2333,6 +2443,12 @@ void serve_loop(Server* Sp) {
                     (double*)((char*)G->I64->vec + L64.U2), M.N);
                 k_slot_warm<<<1, 1, 0, G->stream>>>(G->I64->st, d, G->I32->st, b);
                 ctx->launches += 3;
+                if (M.shell) {
+                    k_slot_shell<<<64, 256, 0, G->stream>>>((const double*)((const char*)G->I32->vec + L32.shx),
+                                                            G->I32->B, b, (double*)((char*)G->I64->vec + L64.shx),
+                                                            G->I64->B, d, M.shell->Ng);
+                    ctx->launches += 1;
+                }
                 set_slot_consts(G->I64, d, G->I32->mats[b], &G->I32->h[3 * b], G->cell, G->stream);
                 T.s32 = G->h32[b];
                 T.has32 = true;

@@ -156,6 +156,19 @@ struct ShellGrid {
 };
 std::string host_shell_setup(int n, int a, int s, double cell, ShellGrid& G);
 
+// The grid's operator on the device (uploaded by lbm_mesh_shell), in the
+// magnet's reduced units: val = 6 K / h (the magnet's integer stiffness where
+// M = I), so that K_grid u = (1/4) Gint m gives u in units of h.
+struct ShellDev {
+    int Ng = 0, nnz = 0;
+    const int* rowptr = nullptr;       // Ng + 1
+    const int* col = nullptr;          // nnz, ascending per row
+    const double* val = nullptr;       // nnz
+    const double* dinv = nullptr;      // Ng: 1 / K_ii (0 on the outer face)
+    const int* gnode = nullptr;        // Ng: -2 outer face, -1 air or shell, >= 0 the magnet's node
+    const int* magnet = nullptr;       // N: grid node of every magnet node
+};
+
 // ---- device view of one mesh --------------------------------------------------------
 struct MeshView {
     int n, N, nb, nnz, F;
@@ -171,6 +184,7 @@ struct MeshView {
     const float* B32;    // nb x nb row-major
     const float* B32lo;  // nb x nb: fp32(B64 - B32), for the FP64-accurate batched product (null: not built)
     const HMDevice* hm = nullptr;   // host pointer: the hierarchical form, when built (lbm_mesh_hmatrix)
+    const ShellDev* shell = nullptr;   // host pointer: the space-transformation boundary, when attached
     double vsum;         // sum_i Vint_i = 24 n^3 (general meshes: sum of gV)
     double cell;         // cell edge h (m); general meshes: the length unit L
     // General meshes (gen != 0): the same tables as FP64/FP32 values in the same
@@ -205,6 +219,7 @@ struct BatchView {
     double* hout;              // optional [N][3][B] effective field (nullable)
     float* m32 = nullptr;      // FP32 batches: [N][3][B] FP32 copy of the trial point (else null)
     double* bvec = nullptr;    // [N][B] divergence right-hand side b = G m at the trial point (rhs_eval)
+    double* shx = nullptr;     // [5][Ng][B] grid potential and CG work vectors (space-transformation boundary)
 };
 
 struct Launch {
@@ -224,6 +239,11 @@ struct Launch {
 // columns [0, B), adjoint columns [B, 2B)) with the hierarchical form of B
 template <typename T>
 void hm_product(const Launch& L, const HMDevice& H, const T* x, T* y, int B);
+// The potential by the space-transformation boundary (shell_solve.cu): K_grid u
+// = b on the grid for every active instance (FP64 Jacobi-PCG, warm-started from
+// V.shx), then U1 = u, U2 = (0 | u) at the magnet's nodes; 0 or a CUDA error.
+template <typename T>
+int shell_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, double tol, int max_iter);
 // Thread-block-cluster variant of the potential solves (pcg_cluster.cu): 1 when
 // launched (*err its status), 0 when the batch does not qualify.
 template <typename T>

@@ -69,30 +69,6 @@ __device__ __forceinline__ bool pcg_sync(unsigned* bar, unsigned& epoch, int* er
     }
 }
 
-// Grid-wide totals of per-block partials part[blk][C][4] (quantities
-// q0..q0+NQV-1) into out[q*C + c] of every block: after a barrier one warp of
-// the grid sums each (column, quantity) over the blocks (lanes stride the
-// blocks, then a fixed xor tree) into fin; after a second barrier every block
-// copies fin.  Fixed order, so all blocks and all runs get the same bits.
-template <int NQV>
-__device__ __forceinline__ bool grid_reduce(const double* part, int q0, int C, double* fin, double* out,
-                                            unsigned* bar, unsigned& epoch, int* err) {
-    if (!grid_sync(bar, gridDim.x, epoch, err)) return false;
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int gw = blockIdx.x * nw + (threadIdx.x >> 5), tw = gridDim.x * nw;
-    const int P = C * NQV;
-    for (int pidx = gw; pidx < P; pidx += tw) {
-        const int c = pidx / NQV, q = pidx % NQV;
-        double acc = 0.0;
-        for (int blk = lane; blk < (int)gridDim.x; blk += 32) acc += __ldcg(&part[((size_t)blk * C + c) * 4 + q0 + q]);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) fin[pidx] = acc;
-    }
-    if (!grid_sync(bar, gridDim.x, epoch, err)) return false;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) out[(t % NQV) * C + t / NQV] = __ldcg(&fin[t]);
-    __syncthreads();
-    return true;
-}
 
 // Jacobi-PCG on Kint for the 2B systems of one stage of the forward and adjoint
 // FEM/BEM chains (column c: instance c % B, adjoint if c >= B):
