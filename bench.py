@@ -66,6 +66,8 @@ def parse():
                     help="batched: 64 same-mesh instances (default); served: Poisson request stream; "
                          "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix)")
     ap.add_argument("--n", type=int, default=80, help="cells per side of the large workload")
+    ap.add_argument("--no-shell", action="store_true",
+                    help="skip the space-transformation leg (the bench batch with the shell boundary)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the single-instance 80^3-cell leg of the default line")
     ap.add_argument("--large-hm-eps", type=float, default=1e-6,
@@ -466,6 +468,79 @@ def large_leg(local, n, hm_eps, max_iter=100000, warmup=1):
     return out
 
 
+def shell_leg(ctx, local, insts, a=4, s=8, precision="mixed"):
+    """The bench's batch (64 instances on the 30^3-cell cube, same materials,
+    fields and starts) with the open boundary by space transformation (Sec. 3.1:
+    the paper's own solver) instead of FEM/BEM: air a cells, shell s cells, one
+    grid of (30 + 2(a + s))^3 cells.  Time to solution of the batch and the
+    shell solve kernel's achieved bandwidth against the measured HBM peak.
+    Algorithmic bytes of one CG iteration per grid row off the outer face: 12
+    work-vector words per instance (z, p, q read and p, q written in the stencil
+    pass; d, p, r, q read and d, r, z written in the update pass: FP32 words in
+    the FP32 phase and in the mixed-iteration FP64 phase) and the row's stencil
+    record read twice (64 B + 4 B FP32), shared by the instances."""
+    import torch
+    import paper_1309_5796_gb300 as lbm
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    stream = torch.cuda.current_stream()
+    prec = {"mixed": lbm.LBM_MIXED, "fp64": lbm.LBM_FP64}[precision]
+    B = len(insts)
+    mesh = ctx.mesh_cube(2e-9, N_CELLS)
+    t0 = time.perf_counter()
+    info = ctx.mesh_shell(mesh, a, s)
+    setup_s = time.perf_counter() - t0
+    nt = N_CELLS + 2 * (a + s)
+    rows = info["grid_nodes"] - (6 * nt * nt + 2)          # grid rows off the outer face
+    inst = ctx.instance_create(mesh, B, prec)
+    inst.set_material(JS_T, A_JM, K1_JM3, np.stack([i.axis for i in insts]))
+    inst.set_field(np.stack([i.h_ext for i in insts]))
+    m0 = torch.from_numpy(np.stack([i.m0 for i in insts])).to(f"cuda:{local}")
+    opts = lbm.default_opts(prec)
+    inst.set_m_device(m0.data_ptr())
+    inst.evaluate(opts, want_h=False, want_u=False)          # one-time set-up (attributes, occupancy)
+    ctx.profile_read(reset=True)
+    ctx.profile_enable(True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    inst.set_m_device(m0.data_ptr())
+    res = inst.minimise(opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    inst.destroy()
+    ctx.mesh_destroy(mesh)
+    sw = prof["cg_sweeps"]
+    word = 4 if (precision == "mixed" or opts.cg_mixed_iter) else 8
+    rec = 68 if word == 4 else 136
+    solve_ms = prof["pcg1_fp32"]["ms"] + prof["pcg1_fp64"]["ms"]
+    by = (sw[0] + sw[2]) * rows * (12 * word * B + rec)
+    gbs = by / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
+    return {"workload": f"the bench batch ({B} instances, {N_CELLS}^3-cell cube) with the space-transformation "
+                        f"boundary: air {a}, shell {s} cells, grid {nt}^3 cells ({info['grid_nodes']} nodes, "
+                        f"{info['shell_tets']} shell tetrahedra), {precision} precision",
+            "setup_s": round(setup_s, 3), "ms_to_solution": round(ms, 1),
+            "solves_per_s": B / (ms / 1e3), "statuses_nonzero": [r["status"] for r in res if r["status"]],
+            "evaluations_per_solve": float(np.mean([r["evaluations"] for r in res])),
+            "cg_sweeps": sw,
+            "shell_solve": {"kernel": "k_shell_pcg", "ms": round(solve_ms, 2),
+                            "launches": prof["pcg1_fp32"]["launches"] + prof["pcg1_fp64"]["launches"],
+                            "us_per_sweep": round(1e3 * solve_ms / max(1, sw[0] + sw[2]), 1),
+                            "bytes": int(by), "GB_s": round(gbs, 1) if gbs else None,
+                            "frac": round(gbs / hbm_peak, 4) if gbs else None,
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items()
+                          if isinstance(v, dict) and v.get("launches")}}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1309_5796_gb300 as lbm
@@ -614,6 +689,13 @@ def run_ours(args, ws, rank, local):
                     "max_rel_energy_err_batched_mixed_vs_fp64": max(e_err)}
         single.destroy()
 
+    shell = None
+    if not args.no_shell:
+        try:
+            shell = shell_leg(ctx, local, insts)
+        except Exception as exc:   # the headline stands on its own
+            shell = {"error": repr(exc)[:300]}
+
     large = None
     if not args.no_large:
         try:
@@ -638,6 +720,7 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
         "fp64_single_instance": fp64_arm,
         "large_single_instance_n80": large,
+        "shell_boundary_batched64_n30": shell,
         "e2e": {"value": e2e_value, "unit": "solves/s",
                 "h2d_bytes_per_step": int(m0_e2e.nbytes), "d2h_bytes_per_step": int(m_out.nbytes),
                 "host_memory": host_mem},

@@ -292,7 +292,7 @@ VecLayout vec_layout(const Mesh& M, int B, int tsize) {
     L.m32 = tsize == 4 ? take(4 * N * 3 * B) : 0;
     L.bvec = take(8 * N * B);
     // space-transformation boundary: grid potential and CG vectors, FP64 in every mode
-    L.shx = M.shell ? take(8 * 5 * (size_t)M.shell->Ng * B) : 0;
+    L.shx = M.shell ? take(8 * 6 * (size_t)M.shell->Ng * B) : 0;
     L.total = o;
     return L;
 }
@@ -465,7 +465,7 @@ int eval_trial(lbm_ctx* ctx, const Launch& L, const Mesh& M, const Inst& I, cons
         // open boundary by space transformation: one symmetric solve on the grid
         ProfScope ps(ctx, 1 + (sizeof(T) == 8 ? 5 : 0), L.stream);
         rhs_eval<T>(L, mv, V);
-        const int e = shell_solve<T>(L, mv, V, o.cg_tol, o.cg_max_iter);
+        const int e = shell_solve<T>(L, mv, V, o.cg_tol, o.cg_max_iter, o.cg_mixed_iter != 0);
         if (e) return fail(LBM_E_CUDA, "cooperative launch failed: %s", cudaGetErrorString((cudaError_t)e));
     } else if (o.demag) {
         int e;
@@ -1410,21 +1410,37 @@ int lbm_mesh_shell(lbm_ctx* ctx, lbm_mesh mesh, int32_t a, int32_t s, int64_t in
     ShellGrid G;
     const std::string why = host_shell_setup(M->n, a, s, 1.0, G);   // K in units of h
     if (!why.empty()) return fail(LBM_E_INVALID, "lbm_mesh_shell: %s", why.c_str());
-    const int Ng = (int)(G.rowptr.size() - 1), nnz = (int)G.col.size();
-    std::vector<double> val(nnz), dinv(Ng, 0.0);
+    const int Ng = (int)(G.rowptr.size() - 1), nnz = (int)G.col.size(), n1 = G.nt + 1;
+    // the per-row stencil records: every coupling of a row off the outer face
+    // lies along one of the 14 Kuhn directions
+    const int dir[15][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+                            {1, 1, 0}, {-1, -1, 0}, {1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, -1, -1}, {1, 1, 1},
+                            {-1, -1, -1}};
+    std::vector<double> c64((size_t)Ng * 16, 0.0);
+    std::vector<float> c32((size_t)Ng * 16, 0.0f);
+    std::vector<unsigned char> kind(Ng, 1);
     std::vector<int> gnode(Ng, -1);
-    for (int k = 0; k < nnz; ++k) val[k] = 6.0 * G.K[k];
-    for (int v : G.outer) gnode[v] = -2;
+    for (int v : G.outer) kind[v] = 0;
     for (size_t i = 0; i < G.magnet.size(); ++i) gnode[G.magnet[i]] = (int)i;
     for (int r = 0; r < Ng; ++r) {
-        if (gnode[r] == -2) continue;
-        const int* b = G.col.data() + G.rowptr[r];
-        const int* e = G.col.data() + G.rowptr[r + 1];
-        const int* d = std::lower_bound(b, e, r);
-        if (d == e || *d != r || !(val[d - G.col.data()] > 0.0))
-            return fail(LBM_E_INVALID, "lbm_mesh_shell: stiffness without a positive diagonal");
-        dinv[r] = 1.0 / val[d - G.col.data()];
+        if (kind[r] == 0) continue;
+        double* c = c64.data() + (size_t)r * 16;
+        const int ri = r % n1, rj = (r / n1) % n1, rk = r / (n1 * n1);
+        for (int e = G.rowptr[r]; e < G.rowptr[r + 1]; ++e) {
+            const int cidx = G.col[e];
+            const int di = cidx % n1 - ri, dj = (cidx / n1) % n1 - rj, dk = cidx / (n1 * n1) - rk;
+            int k = 0;
+            while (k < 15 && !(dir[k][0] == di && dir[k][1] == dj && dir[k][2] == dk)) ++k;
+            if (k == 15 || ri == 0 || rj == 0 || rk == 0 || ri == n1 - 1 || rj == n1 - 1 || rk == n1 - 1)
+                return fail(LBM_E_INVALID, "lbm_mesh_shell: grid stiffness outside the Kuhn stencil");
+            c[k] = 6.0 * G.K[e];
+        }
+        if (!(c[0] > 0.0)) return fail(LBM_E_INVALID, "lbm_mesh_shell: stiffness without a positive diagonal");
+        c[15] = 1.0 / c[0];
+        for (int k = 7; k < 15; ++k)
+            if (c[k] != 0.0) kind[r] = 2;
     }
+    for (size_t k = 0; k < c64.size(); ++k) c32[k] = (float)c64[k];
     free_shell(M);
     ShellDev* S = new ShellDev();
     M->shell = S;
@@ -1436,14 +1452,13 @@ int lbm_mesh_shell(lbm_ctx* ctx, lbm_mesh mesh, int32_t a, int32_t s, int64_t in
         return d;
     };
     S->Ng = Ng;
-    S->nnz = nnz;
-    S->rowptr = (const int*)up(G.rowptr.data(), sizeof(int) * G.rowptr.size());
-    S->col = (const int*)up(G.col.data(), sizeof(int) * G.col.size());
-    S->val = (const double*)up(val.data(), sizeof(double) * val.size());
-    S->dinv = (const double*)up(dinv.data(), sizeof(double) * dinv.size());
+    S->n1 = n1;
+    S->coef64 = (const double*)up(c64.data(), sizeof(double) * c64.size());
+    S->coef32 = (const float*)up(c32.data(), sizeof(float) * c32.size());
+    S->kind = (const unsigned char*)up(kind.data(), kind.size());
     S->gnode = (const int*)up(gnode.data(), sizeof(int) * gnode.size());
     S->magnet = (const int*)up(G.magnet.data(), sizeof(int) * G.magnet.size());
-    if (!S->rowptr || !S->col || !S->val || !S->dinv || !S->gnode || !S->magnet) {
+    if (!S->coef64 || !S->coef32 || !S->kind || !S->gnode || !S->magnet) {
         free_shell(M);
         return fail(LBM_E_OOM, "lbm_mesh_shell: device allocation failed");
     }

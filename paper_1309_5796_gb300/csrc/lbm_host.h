@@ -157,15 +157,18 @@ struct ShellGrid {
 std::string host_shell_setup(int n, int a, int s, double cell, ShellGrid& G);
 
 // The grid's operator on the device (uploaded by lbm_mesh_shell), in the
-// magnet's reduced units: val = 6 K / h (the magnet's integer stiffness where
-// M = I), so that K_grid u = (1/4) Gint m gives u in units of h.
+// magnet's reduced units: 6 K / h (the magnet's integer stiffness where M = I),
+// so that K_grid u = (1/4) Gint m gives u in units of h.  Every row off the
+// outer face is an interior grid node, coupled only along the 14 Kuhn
+// directions: per row a 16-value record {K_ii, the couplings along +x, -x, +y,
+// -y, +z, -z, +(x+y), -(x+y), +(x+z), -(x+z), +(y+z), -(y+z), +(x+y+z),
+// -(x+y+z), 1/K_ii} (zeros on the outer face).
 struct ShellDev {
-    int Ng = 0, nnz = 0;
-    const int* rowptr = nullptr;       // Ng + 1
-    const int* col = nullptr;          // nnz, ascending per row
-    const double* val = nullptr;       // nnz
-    const double* dinv = nullptr;      // Ng: 1 / K_ii (0 on the outer face)
-    const int* gnode = nullptr;        // Ng: -2 outer face, -1 air or shell, >= 0 the magnet's node
+    int Ng = 0, n1 = 0;                // grid nodes, grid nodes a side
+    const float* coef32 = nullptr;     // [Ng][16], rounded to FP32
+    const double* coef64 = nullptr;    // [Ng][16]
+    const unsigned char* kind = nullptr;   // Ng: 0 outer face, 1 seven-point row (M = I), 2 fifteen-point row
+    const int* gnode = nullptr;        // Ng: -1, or the magnet's node at this grid node
     const int* magnet = nullptr;       // N: grid node of every magnet node
 };
 
@@ -219,7 +222,7 @@ struct BatchView {
     double* hout;              // optional [N][3][B] effective field (nullable)
     float* m32 = nullptr;      // FP32 batches: [N][3][B] FP32 copy of the trial point (else null)
     double* bvec = nullptr;    // [N][B] divergence right-hand side b = G m at the trial point (rhs_eval)
-    double* shx = nullptr;     // [5][Ng][B] grid potential and CG work vectors (space-transformation boundary)
+    double* shx = nullptr;     // [6][Ng][B] FP64 grid potential and five CG work vectors (space-transformation boundary)
 };
 
 struct Launch {
@@ -240,10 +243,13 @@ struct Launch {
 template <typename T>
 void hm_product(const Launch& L, const HMDevice& H, const T* x, T* y, int B);
 // The potential by the space-transformation boundary (shell_solve.cu): K_grid u
-// = b on the grid for every active instance (FP64 Jacobi-PCG, warm-started from
-// V.shx), then U1 = u, U2 = (0 | u) at the magnet's nodes; 0 or a CUDA error.
+// = b on the grid for every active instance (Jacobi-PCG on the FP64 grid
+// potential, warm-started from V.shx; CG iterations in FP32 for FP32 batches and
+// with mixed_iter, plain FP64 otherwise), then U1 = u, U2 = (0 | u) at the
+// magnet's nodes; 0 or a CUDA error.
 template <typename T>
-int shell_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, double tol, int max_iter);
+int shell_solve(const Launch& L, const MeshView& M, const BatchView<T>& V, double tol, int max_iter,
+                bool mixed_iter);
 // Thread-block-cluster variant of the potential solves (pcg_cluster.cu): 1 when
 // launched (*err its status), 0 when the batch does not qualify.
 template <typename T>
