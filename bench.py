@@ -62,10 +62,13 @@ def parse():
                     help="seconds of oracle work per step of the reference arm (0: 5-30 s by step count)")
     ap.add_argument("--ref-cores", type=int, default=0,
                     help="host processes of the reference arm (0: all cores, capped by memory)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "served", "large"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "served", "large", "shell"],
                     help="batched: 64 same-mesh instances (default); served: Poisson request stream; "
-                         "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix)")
+                         "large: one instance on an n^3 cube (n = 80: 531 441 nodes, 5.9 GB FP32 BEM matrix); "
+                         "shell: the batched workload with the space-transformation boundary")
     ap.add_argument("--n", type=int, default=80, help="cells per side of the large workload")
+    ap.add_argument("--shell-a", type=int, default=4, help="air cells of the shell workload")
+    ap.add_argument("--shell-s", type=int, default=8, help="shell cells of the shell workload")
     ap.add_argument("--no-shell", action="store_true",
                     help="skip the space-transformation leg (the bench batch with the shell boundary)")
     ap.add_argument("--no-large", action="store_true",
@@ -692,7 +695,7 @@ def run_ours(args, ws, rank, local):
     shell = None
     if not args.no_shell:
         try:
-            shell = shell_leg(ctx, local, insts)
+            shell = shell_leg(ctx, local, insts, a=args.shell_a, s=args.shell_s)
         except Exception as exc:   # the headline stands on its own
             shell = {"error": repr(exc)[:300]}
 
@@ -867,6 +870,45 @@ def run_large(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_shell(args, ws, rank, local):
+    """The bench's batch with the open boundary by space transformation (one
+    JSON line; the default line carries the same leg)."""
+    import torch
+    import paper_1309_5796_gb300 as lbm
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lbm.Context(local, stream=stream.cuda_stream)
+    insts = batched_case(N_CELLS, BATCH, seed=rank_seed(rank))
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launch_count()
+    leg = shell_leg(ctx, local, insts, a=args.shell_a, s=args.shell_s,
+                    precision="fp64" if args.precision == "fp64" else "mixed")
+    launches = ctx.launch_count() - launches0
+    clocks = sampler.stop()
+    ctx.close()
+    if rank != 0:
+        return
+    k = leg["shell_solve"]
+    line = {"metric": "solves/s, the bench batch with the space-transformation boundary",
+            "value": leg["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": 1, "warmup": 1,
+            "ms_per_step": leg["ms_to_solution"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": leg["workload"], "n": N_CELLS, "batch": BATCH, "a": args.shell_a,
+                       "s": args.shell_s, "l2": "work vectors 6 x grid x batch > L2"},
+            "gpu_launches": launches, "clocks": clocks,
+            "roofline": {"bound": "hbm", "kernel": k["kernel"], "achieved": k["GB_s"], "peak": None,
+                         "unit": "GB/s", "frac": k["frac"], "traffic": None, "peak_source": k["peak_source"]},
+            "shell": leg}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    line["roofline"]["peak"] = float(peaks.get("hbm_gbs", 6800.0))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
@@ -878,6 +920,9 @@ def main():
         return
     if args.workload == "large":
         run_large(args, ws, rank, local)
+        return
+    if args.workload == "shell":
+        run_shell(args, ws, rank, local)
         return
     run_ours(args, ws, rank, local)
 

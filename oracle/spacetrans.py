@@ -121,10 +121,17 @@ class ShellProblem(CubeProblem):
         rho_n = np.max(np.abs(self.grid_nodes - self.c), axis=1)
         self.outer = np.nonzero(rho_n == self.R2)[0]
         self.free = np.nonzero(rho_n < self.R2)[0]
-        self.lu_grid = spla.splu(Kg[self.free][:, self.free].tocsc())
+        self._lu = None                                                 # factorised on first use
         # magnet node (i, j, k) -> grid node (i + off, j + off, k + off)
         mn = self.mesh.nodes.astype(np.int64) + off
         self.magnet_in_grid = mn[:, 0] + (nt + 1) * (mn[:, 1] + (nt + 1) * mn[:, 2])
+
+    @property
+    def lu_grid(self):
+        """Sparse LU of K restricted to the nodes off the outer face."""
+        if self._lu is None:
+            self._lu = spla.splu(self.Kgrid[self.free][:, self.free].tocsc())
+        return self._lu
 
     def grid_potential(self, m: np.ndarray) -> np.ndarray:
         """u on the whole grid (0 on the outer face) for the magnetisation m."""

@@ -179,3 +179,76 @@ def test_shell_attach_rules(ctx):
     assert res[0]["cg_iters2"] > 0          # the two Poisson solves are back
     inst.destroy()
     ctx.mesh_destroy(mesh)
+
+
+class _ShellProblemCG(ShellProblem):
+    """The oracle's problem with the grid system solved by Jacobi-preconditioned
+    CG (scipy) to a 1e-14 relative residual instead of the sparse LU: the same
+    definition, usable at the bench's grid size (166 375 grid nodes)."""
+
+    def grid_potential(self, m):
+        import scipy.sparse.linalg as spla
+        rhs = np.zeros(self.Kgrid.shape[0])
+        rhs[self.magnet_in_grid] = self.rhs(m)
+        Kf = self.Kgrid[self.free][:, self.free].tocsr()
+        d = 1.0 / Kf.diagonal()
+        M = spla.LinearOperator(Kf.shape, matvec=lambda v: d * v)
+        kw = {"rtol": 1e-14} if "rtol" in spla.cg.__code__.co_varnames else {"tol": 1e-14}
+        uf, info = spla.cg(Kf, rhs[self.free], M=M, maxiter=20000, atol=0.0, **kw)
+        assert info == 0
+        u = np.zeros_like(rhs)
+        u[self.free] = uf
+        return u
+
+
+_BENCH = dict(n=30, a=4, s=8, B=64, sample=(0, 17, 42, 63))
+
+
+@pytest.fixture(scope="module")
+def bench_ref():
+    """Inputs of the bench-shape case and the oracle's evaluations of the
+    sampled instances (shared by both precisions)."""
+    n, a, s, B = (_BENCH[k] for k in ("n", "a", "s", "B"))
+    N = (n + 1) ** 3
+    rng = np.random.default_rng(77)
+    axis = tilted_axis(1.0, 0.4)
+    fields = rng.normal(size=(B, 3))
+    m0 = np.stack([m_random_sphere(N, 900 + b) for b in range(B)])
+    p = _ShellProblemCG(n, JS_T, A_JM, K1_JM3, axis, a, s)
+    evs = {b: p.evaluate(m0[b], fields[b]) for b in _BENCH["sample"]}
+    return p, axis, fields, m0, evs
+
+
+@pytest.mark.parametrize("prec", [lbm.LBM_FP64, lbm.LBM_MIXED])
+def test_shell_bench_shape_sampled(ctx, bench_ref, prec):
+    """The bench's shape: 64 instances on the 30^3-cell cube, air 4 and shell 8
+    cells (a 54^3-cell grid, every SM a block, four instances per thread in the
+    FP32 kernel).  Four sampled instances: fields at every magnet node and the
+    energy terms against the oracle's definition (grid system by CG to 1e-14).
+    FP64 solves to a 1e-14 relative residual: 1e-10 of the largest field value;
+    the mixed precision's FP32 phase (FP32 CG to 1e-7): 1e-6 (measured 1.1e-7)."""
+    p, axis, fields, m0, evs = bench_ref
+    n, a, s, B = (_BENCH[k] for k in ("n", "a", "s", "B"))
+    N = (n + 1) ** 3
+    mesh, info = _shell_mesh(ctx, n, a, s)
+    inst = ctx.instance_create(mesh, B, prec)
+    inst.set_material(JS_T, A_JM, K1_JM3, axis)
+    inst.set_field(fields)
+    inst.set_m(m0)
+    opts = lbm.default_opts(prec)
+    rtol = 1e-6
+    if prec == lbm.LBM_FP64:
+        opts.cg_tol = 1e-14
+        rtol = 1e-10
+    res, h, _ = inst.evaluate(opts, want_u=False)
+    inst.destroy()
+    ctx.mesh_destroy(mesh)
+    Eunit = p.Kd * p.cell ** 3 * N
+    errs = []
+    for b, ev in evs.items():
+        hs = np.abs(ev.h).max()
+        errs.append(np.abs(h[b] - ev.h).max() / hs)
+        assert errs[-1] <= rtol, (b, errs)
+        for k, key in enumerate(("ex", "an", "z", "d")):
+            assert abs(res[b]["energy"][k] - ev.terms[key]) <= rtol * Eunit, (b, key)
+    print("max relative field error", max(errs))
