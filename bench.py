@@ -471,6 +471,11 @@ def large_leg(local, n, hm_eps, max_iter=100000, warmup=1):
     return out
 
 
+# DRAM bytes per ms of k_shell_pcg kernel time from the ncu capture in
+# profiles/k_shell_pcg_fp32_batched64_n30_shell4x8.md (185.03 GB in 38.277 ms)
+PROFILED_SHELL_DRAM_BYTES_PER_MS = 185.03e9 / 38.277
+
+
 def shell_leg(ctx, local, insts, a=4, s=8, precision="mixed"):
     """The bench's batch (64 instances on the 30^3-cell cube, same materials,
     fields and starts) with the open boundary by space transformation (Sec. 3.1:
@@ -527,6 +532,8 @@ def shell_leg(ctx, local, insts, a=4, s=8, precision="mixed"):
     solve_ms = prof["pcg1_fp32"]["ms"] + prof["pcg1_fp64"]["ms"]
     by = (sw[0] + sw[2]) * rows * (12 * word * B + rec)
     gbs = by / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
+    nlaunch = prof["pcg1_fp32"]["launches"] + prof["pcg1_fp64"]["launches"]
+    avg_ms = solve_ms / max(1, nlaunch)
     return {"workload": f"the bench batch ({B} instances, {N_CELLS}^3-cell cube) with the space-transformation "
                         f"boundary: air {a}, shell {s} cells, grid {nt}^3 cells ({info['grid_nodes']} nodes, "
                         f"{info['shell_tets']} shell tetrahedra), {precision} precision",
@@ -539,7 +546,14 @@ def shell_leg(ctx, local, insts, a=4, s=8, precision="mixed"):
                             "us_per_sweep": round(1e3 * solve_ms / max(1, sw[0] + sw[2]), 1),
                             "bytes": int(by), "GB_s": round(gbs, 1) if gbs else None,
                             "frac": round(gbs / hbm_peak, 4) if gbs else None,
-                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+                            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                            "algorithmic_bytes_per_sweep": rows * (12 * word * B + rec),
+                            "avg_launch_ms": round(avg_ms, 3),
+                            "bytes_per_launch": by / max(1, nlaunch),
+                            "traffic": PROFILED_SHELL_DRAM_BYTES_PER_MS * avg_ms if word == 4 else None,
+                            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per ms of kernel "
+                                               "time (profiles/k_shell_pcg_fp32_batched64_n30_shell4x8.md) x "
+                                               "average launch duration") if word == 4 else None},
             "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items()
                           if isinstance(v, dict) and v.get("launches")}}
 
@@ -898,7 +912,9 @@ def run_shell(args, ws, rank, local):
                        "s": args.shell_s, "l2": "work vectors 6 x grid x batch > L2"},
             "gpu_launches": launches, "clocks": clocks,
             "roofline": {"bound": "hbm", "kernel": k["kernel"], "achieved": k["GB_s"], "peak": None,
-                         "unit": "GB/s", "frac": k["frac"], "traffic": None, "peak_source": k["peak_source"]},
+                         "unit": "GB/s", "frac": k["frac"], "traffic": k["traffic"],
+                         "traffic_source": k["traffic_source"], "bytes_per_launch": k["bytes_per_launch"],
+                         "avg_launch_ms": k["avg_launch_ms"], "peak_source": k["peak_source"]},
             "shell": leg}
     peaks = {}
     try:
