@@ -432,6 +432,9 @@ typedef struct {
     int32_t max_pcg_blocks;  /* cooperative grid cap per group (default 0: a quarter of the SMs) */
     double  mem_reserve;     /* fraction of device memory kept free (default 0.05) */
     lbm_solve_opts opt;      /* solve options of every request */
+    int32_t shell_a;         /* > 0: every group's cube gets the space-transformation */
+    int32_t shell_s;         /*   boundary with air shell_a and shell shell_s cells
+                                (lbm_mesh_shell); default 0, 0: FEM/BEM */
 } lbm_serve_opts;
 
 void lbm_default_serve_opts(lbm_serve_opts* o);

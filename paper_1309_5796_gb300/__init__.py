@@ -69,7 +69,8 @@ class Request(C.Structure):
 
 class ServeOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("chunk", C.c_int32), ("max_pcg_blocks", C.c_int32),
-                ("mem_reserve", C.c_double), ("opt", SolveOpts)]
+                ("mem_reserve", C.c_double), ("opt", SolveOpts), ("shell_a", C.c_int32),
+                ("shell_s", C.c_int32)]
 
 
 _P = C.c_void_p

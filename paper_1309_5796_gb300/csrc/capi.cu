@@ -2170,11 +2170,16 @@ void group_free(lbm_ctx* ctx, Group* G) {
     delete G;
 }
 
-size_t group_estimate(int n, int slots) {
+size_t group_estimate(int n, int slots, int shell_a, int shell_s) {
     const size_t N = (size_t)(n + 1) * (n + 1) * (n + 1);
     const size_t nb = N - (size_t)(n > 1 ? (n - 1) * (n - 1) * (n - 1) : 0);
-    const size_t mesh = 12 * nb * nb + 100 * N;
-    const size_t per_slot = 8 * (2 * N * 3 * 2 + 3 * N) * 2 + (4 + 8) * (12 * N + 4 * nb) + 40 * N;
+    size_t mesh = 12 * nb * nb + 100 * N;
+    size_t per_slot = 8 * (2 * N * 3 * 2 + 3 * N) * 2 + (4 + 8) * (12 * N + 4 * nb) + 40 * N;
+    if (shell_a > 0) {   // the grid's stencil records and, per slot, its six FP64 vectors in both batches
+        const size_t g1 = (size_t)n + 2 * ((size_t)shell_a + shell_s) + 1, Ng = g1 * g1 * g1;
+        mesh += (16 * 12 + 9) * Ng;
+        per_slot += 2 * 6 * 8 * Ng;
+    }
     return mesh + per_slot * slots + ((size_t)64 << 20);
 }
 
@@ -2184,7 +2189,7 @@ Group* group_get(Server& S, int n, double cell) {
     auto it = S.groups.find(n);
     if (it != S.groups.end()) return it->second;
     lbm_ctx* ctx = S.ctx;
-    const size_t need = group_estimate(n, S.opt.slots);
+    const size_t need = group_estimate(n, S.opt.slots, S.opt.shell_a, S.opt.shell_s);
     for (;;) {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
@@ -2216,6 +2221,8 @@ Group* group_get(Server& S, int n, double cell) {
     cudaMemset(G->err, 0, 64);
     cudaMemset(G->sweeps, 0, 64);
     if (lbm_mesh_cube(ctx, cell, n, &G->mesh_id) != LBM_OK) return bad(0);
+    if (S.opt.shell_a > 0 && lbm_mesh_shell(ctx, G->mesh_id, S.opt.shell_a, S.opt.shell_s, nullptr) != LBM_OK)
+        return bad(0);
     if (lbm_instance_create(ctx, G->mesh_id, B, LBM_MIXED, &G->i32_id) != LBM_OK) return bad(0);
     if (lbm_instance_create(ctx, G->mesh_id, B, LBM_FP64, &G->i64_id) != LBM_OK) return bad(0);
     G->I32 = ctx->insts[G->i32_id];
@@ -2501,7 +2508,8 @@ int lbm_serve_start(lbm_ctx* ctx, const lbm_serve_opts* opt) {
     Server* S = new Server();
     S->ctx = ctx;
     if (opt) S->opt = *opt; else lbm_default_serve_opts(&S->opt);
-    if (S->opt.slots < 1 || S->opt.slots > 256 || S->opt.chunk < 1) {
+    const bool shell_ok = (S->opt.shell_a == 0 && S->opt.shell_s == 0) || (S->opt.shell_a >= 1 && S->opt.shell_s >= 1);
+    if (S->opt.slots < 1 || S->opt.slots > 256 || S->opt.chunk < 1 || !shell_ok) {
         delete S;
         return fail(LBM_E_INVALID, "invalid serve options");
     }

@@ -226,7 +226,7 @@ def test_shell_bench_shape_sampled(ctx, bench_ref, prec):
     FP32 kernel).  Four sampled instances: fields at every magnet node and the
     energy terms against the oracle's definition (grid system by CG to 1e-14).
     FP64 solves to a 1e-14 relative residual: 1e-10 of the largest field value;
-    the mixed precision's FP32 phase (FP32 CG to 1e-7): 1e-6 (measured 1.1e-7)."""
+    the mixed precision's FP32 phase (FP32 CG to 1e-6): 1e-6 (measured 1.1e-7)."""
     p, axis, fields, m0, evs = bench_ref
     n, a, s, B = (_BENCH[k] for k in ("n", "a", "s", "B"))
     N = (n + 1) ** 3
@@ -252,3 +252,34 @@ def test_shell_bench_shape_sampled(ctx, bench_ref, prec):
         for k, key in enumerate(("ex", "an", "z", "d")):
             assert abs(res[b]["energy"][k] - ev.terms[key]) <= rtol * Eunit, (b, key)
     print("max relative field error", max(errs))
+
+
+def test_shell_serving(ctx):
+    """The server with the space-transformation boundary on every group's cube
+    (serve option shell_a/shell_s): requests of two cube sizes, mixed and FP64
+    precision, each reaching its own oracle minimum within 1e-6 relative; a
+    request gives the same bits alone and after other requests reused its slot
+    (the slot's grid potential starts from zero)."""
+    from synth.inputs import m_perturbed
+    a, s = 2, 3
+    reqs = []
+    for k, (n, hz, prec) in enumerate(((3, -5.0, lbm.LBM_MIXED), (4, -6.0, lbm.LBM_MIXED),
+                                       (3, -4.5, lbm.LBM_FP64), (4, -5.5, lbm.LBM_MIXED))):
+        N = (n + 1) ** 3
+        reqs.append(dict(n=n, cell_m=2e-9, Js=JS_T, A=A_JM, K1=K1_JM3, axis=tilted_axis(2.0 + k, 0.7 * k),
+                         h=np.array([0.0, 0.0, hz]), m0=m_perturbed(N, 60 + k), precision=prec))
+    ctx.serve_start(slots=2, chunk=4, shell_a=a, shell_s=s)
+    try:
+        first = ctx.wait(ctx.submit(**reqs[0]), (reqs[0]["n"] + 1) ** 3, timeout_s=300)
+        tickets = [ctx.submit(**r) for r in reqs]
+        out = [ctx.wait(t, (r["n"] + 1) ** 3, timeout_s=300) for t, r in zip(tickets, reqs)]
+    finally:
+        ctx.serve_stop()
+    assert out[0][0]["energy"][4] == first[0]["energy"][4]
+    assert np.array_equal(out[0][1], first[1])
+    for (res, _), r in zip(out, reqs):
+        p = ShellProblem(r["n"], JS_T, A_JM, K1_JM3, r["axis"], a, s)
+        ref = oracle_minimise(p, r["m0"], r["h"], tol=1e-6, max_iter=20000)
+        scale = max(abs(ref.E), p.Kd * (r["n"] * p.cell) ** 3)
+        assert res["status"] == lbm.LBM_OK, r
+        assert abs(res["energy"][4] - ref.E) / scale < 1e-6, (r["n"], res["energy"][4], ref.E)
