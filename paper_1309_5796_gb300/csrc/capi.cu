@@ -527,11 +527,14 @@ int run_chunk(lbm_ctx* ctx, const Launch& L, const Mesh& M, Inst* I, const Batch
               const StepOpts& so, int nblk_field, int chunk, bool first, cudaStream_t cap, bool* replayed) {
     *replayed = false;
     ChunkGraph& g = I->graph;
-    std::vector<char> key(sizeof(lbm_solve_opts) + 9 * sizeof(int64_t));
+    std::vector<char> key(sizeof(lbm_solve_opts) + 10 * sizeof(int64_t));
     {
-        const int64_t k[9] = {chunk, (int64_t)sizeof(T), I->B, (int64_t)(intptr_t)M.hm, (int64_t)(intptr_t)M.B32lo,
-                              (int64_t)(intptr_t)M.tcA, ctx->prof ? 1 : 0, (int64_t)(intptr_t)V.m,
-                              (int64_t)(intptr_t)M.shell};
+        // the launch shape of the cluster potential solves (it follows the active
+        // instances; querying it here also caches its occupancy before a capture)
+        const int64_t shape = pcg_cluster_shape(L, M.view(), I->B, sizeof(T) == 8, o.cg_mixed_iter != 0);
+        const int64_t k[10] = {chunk, (int64_t)sizeof(T), I->B, (int64_t)(intptr_t)M.hm, (int64_t)(intptr_t)M.B32lo,
+                               (int64_t)(intptr_t)M.tcA, ctx->prof ? 1 : 0, (int64_t)(intptr_t)V.m,
+                               (int64_t)(intptr_t)M.shell, shape};
         memcpy(key.data(), &o, sizeof(lbm_solve_opts));
         memcpy(key.data() + sizeof(lbm_solve_opts), k, sizeof k);
     }
@@ -618,6 +621,10 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
     reset_states(L, I->st, I->B, so, 0, warm ? 1 : 0);
     const int nblk_field = field_blocks(L, mv, I->B);
     std::vector<InstState> hs(I->B);
+    // instances iterating at the start of each chunk (all after the reset); the
+    // cluster potential solves launch only for the groups among them
+    std::vector<unsigned char> active(I->B, 1);
+    L.active = active.data();
     const int64_t max_loops = (int64_t)(oo.max_iter + 1) * (oo.max_backtracks + 2) + 2;
     int64_t loops = 0;
     int rc = LBM_OK;
@@ -638,10 +645,15 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
         if (replayed && ctx->prof) prof_harvest_graph(ctx, I->graph);
         if (errw) {
             cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream);
+            if (errw & DEV_ERR_SHAPE)
+                return fail(LBM_E_CUDA, "a potential solve launched fewer clusters than active systems");
             return fail(LBM_E_TIMEOUT, "a device-side wait ran out of time (error word %d)", errw);
         }
         bool all = true;
-        for (int b = 0; b < I->B; ++b) all &= hs[b].phase == PH_DONE;
+        for (int b = 0; b < I->B; ++b) {
+            all &= hs[b].phase == PH_DONE;
+            active[b] = hs[b].phase != PH_DONE;
+        }
         if (all) break;
         if (loops > max_loops) { rc = LBM_E_NOT_CONVERGED; break; }
     }

@@ -236,7 +236,13 @@ struct Launch {
     int max_blocks;              // cap on the cooperative PCG grid (0: one block per SM)
     bool tune = true;            // launch-shape autotuning allowed (it waits on events)
     int pcg_kernel = 0;          // 0 choose, 1 grid-wide kernel, 2 prefer clusters (lbm_solve_opts)
+    // host flags [B]: the instances iterating at the start of the chunk (null: all);
+    // the cluster potential solves size their launch to the groups still active
+    const unsigned char* active = nullptr;
 };
+// The shape the cluster potential solves take for this launch (CPC * 100 + CL;
+// 0: the grid-wide kernel), from the active flags of L.
+int pcg_cluster_shape(const Launch& L, const MeshView& M, int B, bool fp64, bool mixed_iter);
 
 // u2_S = B_H u1_S and c_S = B_H^T t_S on the [nb][2B] surface arrays (forward
 // columns [0, B), adjoint columns [B, 2B)) with the hierarchical form of B

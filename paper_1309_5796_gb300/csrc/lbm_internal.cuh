@@ -30,6 +30,7 @@ constexpr int MALPHA_MAX = 8;
 
 // Device status bits (context-wide error word).
 constexpr int DEV_ERR_TIMEOUT = 1;
+constexpr int DEV_ERR_SHAPE = 2;     // a cluster solve launched fewer clusters than active groups
 
 // Four doubles on a 32-byte boundary (general-mesh value tables).
 struct __align__(32) Dbl4 {

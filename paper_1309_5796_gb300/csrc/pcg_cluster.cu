@@ -3,14 +3,16 @@
 // group of CPC systems, for batches with many systems.
 //
 // The systems of a batch are independent, so nothing needs to be shared across
-// the whole grid: cluster k (CL = 8 or 4 CTAs) solves columns [k*CPC, (k+1)*CPC) of
-// the [N][2B] system layout over all N rows, CTA r of the cluster owning the
-// contiguous rows [r*rpc, (r+1)*rpc).  Every reduction of the iteration (p.q;
-// r.z, r.r, sum r; the Neumann mean and the gauge) is a block sum in a fixed
-// order, then a sum over the cluster's 8 CTAs in rank order read through
-// distributed shared memory after one hardware cluster barrier: every CTA gets
-// the same bits, so every CTA takes the same decisions, and no CTA ever waits
-// on a memory flag (no software grid barrier, no time limit needed).
+// the whole grid: cluster k (CL = 4, 8 or 16 CTAs) solves the k-th group of CPC
+// columns [g*CPC, (g+1)*CPC) of the [N][2B] system layout that still has an
+// active instance, over all N rows, CTA r of the cluster owning the contiguous
+// rows [r*rpc, (r+1)*rpc); when few groups remain active (the end of a batch)
+// the host picks a shape with more CTAs per cluster.  Every reduction of the
+// iteration (p.q; r.z, r.r, sum r; the Neumann mean and the gauge) is a block
+// sum in a fixed order, then a fixed-order sum over the cluster's CTAs read
+// through distributed shared memory after one hardware cluster barrier: every
+// CTA gets the same bits, so every CTA takes the same decisions, and no CTA
+// ever waits on a memory flag (no software grid barrier, no time limit needed).
 //
 // The preconditioned residual z of the cluster's systems lives in the CTAs'
 // shared memory (rows of a CTA in its own, neighbours in other CTAs of the
@@ -25,6 +27,7 @@
 // iterated in FP32 with the FP64 residual recomputed at every restart.
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -128,8 +131,38 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
     const int tid = threadIdx.x;
     const int g = tid % G, rl = tid / G;
     const unsigned rank = cluster_rank();
-    const int col0 = (int)cluster_index() * CPC;
     const int B = A.V.B, C = 2 * B, N = A.M.N;
+    // The cluster's group of CPC systems: the k-th group with an active
+    // instance (k = the cluster's index), so that a launch with fewer, larger
+    // clusters serves the groups still iterating; clusters beyond the active
+    // groups have nothing to do.  Every CTA reads the same phases (no kernel of
+    // this launch changes them), so all agree.
+    __shared__ unsigned s_bal[8];
+    __shared__ int s_grp;
+    int grp;
+    {
+        const int ng = 2 * B / CPC;   // <= 256: B <= 512
+        bool a = false;
+        if (tid < ng)
+            for (int i = 0; i < CPC; ++i) a |= A.V.st[(tid * CPC + i) % B].phase != PH_DONE;
+        const unsigned bal = __ballot_sync(0xffffffffu, a);
+        if ((tid & 31) == 0 && tid < 256) s_bal[tid >> 5] = bal;
+        if (tid == 0) s_grp = -1;
+        __syncthreads();
+        if (a) {
+            int k = __popc(bal & ((1u << (tid & 31)) - 1u));
+            for (int w = 0; w < (tid >> 5); ++w) k += __popc(s_bal[w]);
+            if (k == (int)cluster_index()) s_grp = tid;
+        }
+        if (tid == 0 && rank == 0 && cluster_index() == 0) {
+            int nact = 0;
+            for (int w = 0; w < (ng + 31) / 32; ++w) nact += __popc(s_bal[w]);
+            if (nact > (int)(gridDim.x / CL)) atomicOr(A.err, DEV_ERR_SHAPE);   // groups left unsolved
+        }
+        __syncthreads();
+        grp = s_grp;
+    }
+    const int col0 = (grp < 0 ? 0 : grp) * CPC;
     const int c0 = col0 + g * VEC;                 // first column of this thread
     const int cl0 = g * VEC;                       // the same within the cluster's columns
     const int mode = A.mode;
@@ -139,7 +172,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
 
     for (int i = tid; i < CPC; i += CL_THREADS) {
         const int b = (col0 + i) % B;
-        s_act[i] = A.V.st[b].phase != PH_DONE;
+        s_act[i] = grp >= 0 && A.V.st[b].phase != PH_DONE;
         s_cur[i] = A.V.st[b].cur;
         s_it[i] = 0;
         s_done[i] = 0;
@@ -183,7 +216,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
     // its own cache line).  d, the FP32 correction that alpha p accumulates into
     // (folded into x at the end of every cycle), lives in the upper half of r's
     // FP64 storage (MP) or in the global z array (z itself is in shared memory).
-    const size_t gbase = (size_t)cluster_index() * N * CPC;
+    const size_t gbase = (size_t)(grp < 0 ? 0 : grp) * N * CPC;
     W* __restrict__ r = reinterpret_cast<W*>(A.V.r) + gbase;
     W* __restrict__ xacc = (MP ? reinterpret_cast<W*>(A.V.r) + (size_t)N * C : reinterpret_cast<W*>(A.V.z)) + gbase;
     W* __restrict__ p = reinterpret_cast<W*>(A.V.p) + gbase;
@@ -193,9 +226,9 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
 
     // Cluster reductions of NQV quantities (per-thread values of VEC columns):
     // partial() sums the CTA's values (warp shuffles, then the warps in order)
-    // into this CTA's slot slots[par] and passes the cluster barrier; total()
-    // then adds the CL slots of the cluster in rank order (the same bits in
-    // every CTA); reduce() puts every total into out[q*CPC + c] for all threads.
+    // into this CTA's slot slots[par] and passes the cluster barrier; totals()
+    // then adds the CL slots of the cluster (the same bits in every CTA);
+    // reduce() does both and leaves every total in out[q*CPC + c] for all threads.
     // The slots alternate, so a slot is rewritten only after two more cluster
     // barriers, when every CTA has read it.
     auto partial = [&](auto& vals) -> double* {
@@ -226,24 +259,33 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
         cluster_sync();
         return mine;
     };
-    auto total = [&](const double* slot, int idx) -> double {
-        const uint32_t a = smem_u32(slot + idx);
-        double acc = 0.0;
+    // totals(slot, nq): every total of the first nq quantities into out[q*CPC + c],
+    // all at once: thread t loads rank t % CL's partial of value t / CL, and the
+    // CL consecutive lanes of a value add theirs in a fixed butterfly (the same
+    // bits in every lane and every CTA of the cluster)
+    auto totals = [&](const double* slot, int nq) {
+        const int nv = nq * CPC;
+        double v = 0.0;
+        if (tid < nv * CL) v = ld_peer_f64(peer_u32(smem_u32(slot + tid / CL), (unsigned)(tid % CL)));
 #pragma unroll
-        for (int rr = 0; rr < CL; ++rr) acc += ld_peer_f64(peer_u32(a, rr));
-        return acc;
+        for (int off = CL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (tid < nv * CL && tid % CL == 0) out[tid / CL] = v;
+        __syncthreads();
     };
     auto reduce = [&](auto& vals) {
         constexpr int NQV = sizeof(vals) / sizeof(vals[0]);
-        const double* slot = partial(vals);
-        if (tid < NQV * CPC) out[tid] = total(slot, tid);
-        __syncthreads();
+        totals(partial(vals), NQV);
     };
     // z of row j (this thread's VEC columns): own rows from this CTA's shared
     // memory, others from the owning CTA's through the cluster window
+    // On the Kuhn cube a row's couplings reach at most 1 + (n+1) + (n+1)^2 rows
+    // away; when a CTA's slab is at least that long, a row outside this CTA's
+    // slab lies in a neighbouring CTA's (no division for the owner).
+    const int s2k = A.M.n + 1, halo = 1 + s2k + s2k * s2k;
+    const bool adj_only = !GEN && rpc >= halo;
     auto zrow = [&](int j) -> float4 {
         if (j >= lo && j < lo + rpc) return *reinterpret_cast<const float4*>(zs + (j - lo) * CPC + cl0);
-        const unsigned o = (unsigned)(j / rpc);
+        const unsigned o = adj_only ? (j < lo ? rank - 1u : rank + 1u) : (unsigned)(j / rpc);
         return ld_peer4(peer_u32(zbase + (uint32_t)(((j - (int)o * rpc) * CPC + cl0) * 4), o));
     };
 
@@ -349,27 +391,28 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
             }
             for (int it = 0;; ++it) {
                 // the slot `last` holds the CTAs' r.z, r.r, (ref.ref: first pass
-                // only), sum r; the column's thread reads their totals itself
+                // only), sum r
+                totals(last, 4);
                 if (tid < CPC) {
                     if (it > 0) {   // bookkeeping of the iteration just finished
                         s_rhop[tid] = s_rho[tid];
                         if (!s_flag[tid]) s_it[tid] += 1;
                     }
-                    const double rho = total(last, tid);
+                    const double rho = out[tid];
                     // Neumann: the residual without its null-space (mean) component
-                    const double sr = total(last, 3 * CPC + tid);
-                    const double rr0 = total(last, CPC + tid);
+                    const double sr = out[3 * CPC + tid];
+                    const double rr0 = out[CPC + tid];
                     const double rr = neu ? fmax(rr0 - sr * sr / (double)N, 0.0) : rr0;
                     int conv;
                     if constexpr (MP) {
                         if (it == 0) {   // rr is the true (FP64) residual of this cycle
-                            s_tol[tid] = A.tol2 * total(last, 2 * CPC + tid);
+                            s_tol[tid] = A.tol2 * out[2 * CPC + tid];
                             s_done[tid] = !s_act[tid] || rr <= s_tol[tid] || s_it[tid] >= A.max_iter;
                             s_tin[tid] = fmax(s_tol[tid], MP_INNER * MP_INNER * rr);
                         }
                         conv = s_done[tid] || rr <= s_tin[tid] || s_it[tid] >= A.max_iter;
                     } else {
-                        if (it == 0) s_tol[tid] = A.tol2 * total(last, 2 * CPC + tid);
+                        if (it == 0) s_tol[tid] = A.tol2 * out[2 * CPC + tid];
                         conv = !s_act[tid] || rr <= s_tol[tid] || it >= A.max_iter;
                     }
                     s_ab[tid] = (it == 0 || conv) ? 0.0 : rho / s_rhop[tid];
@@ -481,8 +524,8 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                         }
                     }
                 {
-                    const double* slot = partial(tpq);
-                    if (tid < CPC) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / total(slot, tid);
+                    totals(partial(tpq), 1);
+                    if (tid < CPC) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
                     __syncthreads();
                 }
                 W alpha[VEC];
@@ -627,21 +670,54 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
     cluster_sync();   // no CTA leaves while another may still read its shared memory
 }
 
-// One cluster shape: CL CTAs per cluster, CPC systems per cluster.  Launched
-// only when every cluster of the grid can be resident at once (otherwise the
-// clusters would run in waves); *ok tells whether it was.
+// Clusters of one shape (CL CTAs, CPC systems) that can be resident at once,
+// queried once per (kernel, device, shared memory) and cached, so that no query
+// runs while a chunk of iterations is being captured.
 template <typename T, bool MP, bool GEN, int CPC, int CL>
-cudaError_t launch_cluster(const Launch& L, PcgArgs<T>& a, bool* ok) {
-    *ok = false;
-    const int B = a.V.B, N = a.M.N;
-    if (B % CPC != 0) return cudaSuccess;
+int resident_clusters(int N, size_t* smem_out) {
     const int rpc = (N + CL - 1) / CL;
     const size_t smem = cl_smem(rpc, CPC).total;
-    if (smem > CL_SMEM_MAX) return cudaSuccess;
+    *smem_out = smem;
+    if (smem > CL_SMEM_MAX) return 0;
     auto fn = k_pcg_cluster<T, MP, GEN, CPC, CL>;
-    cudaError_t e = kernel_smem_attr((const void*)fn, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int nclusters = 2 * B / CPC;
+    static std::mutex mu;
+    static std::map<std::tuple<int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int ncl = 0;
+    if (kernel_smem_attr((const void*)fn, (int)smem) == cudaSuccess &&
+        (CL <= 8 || cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                        cudaSuccess)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)CL);
+        cfg.blockDim = dim3(cl_threads<CPC>());
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&ncl, (const void*)fn, &cfg) != cudaSuccess) ncl = 0;
+    }
+    cudaGetLastError();
+    cache.emplace(key, ncl);
+    return ncl;
+}
+
+// Launch nclusters clusters of one shape (the caller has checked that they can
+// all be resident at once: otherwise they would run in waves).
+template <typename T, bool MP, bool GEN, int CPC, int CL>
+cudaError_t launch_cluster(const Launch& L, PcgArgs<T>& a, int nclusters) {
+    const int N = a.M.N;
+    const int rpc = (N + CL - 1) / CL;
+    size_t smem = 0;
+    resident_clusters<T, MP, GEN, CPC, CL>(N, &smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclusters * CL));
     cfg.blockDim = dim3(cl_threads<CPC>());
@@ -654,62 +730,87 @@ cudaError_t launch_cluster(const Launch& L, PcgArgs<T>& a, bool* ok) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // clusters resident at once, queried once per (kernel, device, shared memory)
-    // and cached: no query runs while a chunk of iterations is being captured
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, size_t>, int> cache;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int ncl = 0;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        const auto key = std::make_tuple((const void*)fn, dev, smem);
-        auto it = cache.find(key);
-        if (it == cache.end()) {
-            e = cudaOccupancyMaxActiveClusters(&ncl, (const void*)fn, &cfg);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                ncl = 0;
-            }
-            it = cache.emplace(key, ncl).first;
+    return cudaLaunchKernelEx(&cfg, k_pcg_cluster<T, MP, GEN, CPC, CL>, a, rpc);
+}
+
+// The shape for a batch of B instances of which active[b] (host flags at the
+// start of the chunk; null: all) are iterating: the groups of CPC systems with
+// an active instance must all fit in the resident clusters.  Preference: 4
+// systems on 16 CTAs, on 8 CTAs (fewer rows per CTA: shorter iterations for the
+// few instances still running at the end of a batch), 8 systems on 8 CTAs,
+// 4 systems on 4 CTAs.  Returns the shape's code (CPC * 100 + CL; 0: none) and
+// its cluster count (the groups a full batch has, or all resident clusters of
+// the shape, whichever is fewer).
+template <typename T, bool MP, bool GEN>
+int choose_shape(const Launch& L, int N, int B, int* nclusters) {
+    auto groups = [&](int cpc) {
+        int n = 0;
+        for (int gidx = 0; gidx < 2 * B / cpc; ++gidx) {
+            bool a = L.active == nullptr;
+            for (int i = 0; i < cpc && !a; ++i) a = L.active[(gidx * cpc + i) % B] != 0;
+            n += a;
         }
-        ncl = it->second;
-    }
-    if (ncl < nclusters) return cudaSuccess;   // the next shape, or the grid-wide kernel
-    *ok = true;
-    return cudaLaunchKernelEx(&cfg, fn, a, rpc);
+        return n;
+    };
+    size_t smem = 0;
+    // a shape serves n active groups if its resident clusters (and the caller's
+    // cap on CTAs, L.max_blocks) hold them all
+    auto fits = [&](int cpc, int cl, int r, int n) {
+        int cap = r;
+        if (L.max_blocks > 0) cap = std::min(cap, L.max_blocks / cl);
+        if (n > cap) return false;
+        *nclusters = std::min(cap, 2 * B / cpc);
+        return true;
+    };
+    const int n4 = groups(4);
+    if (fits(4, 16, resident_clusters<T, MP, GEN, 4, 16>(N, &smem), n4)) return 416;
+    if (fits(4, 8, resident_clusters<T, MP, GEN, 4, 8>(N, &smem), n4)) return 408;
+    if (B >= 32 && B % 8 == 0 && fits(8, 8, resident_clusters<T, MP, GEN, 8, 8>(N, &smem), groups(8))) return 808;
+    if (fits(4, 4, resident_clusters<T, MP, GEN, 4, 4>(N, &smem), n4)) return 404;
+    return 0;
 }
 
 template <typename T, bool MP, bool GEN>
 cudaError_t launch_any(const Launch& L, PcgArgs<T>& a, bool* ok) {
-    // preference: 8 systems on 8 CTAs (fewest clusters), 4 systems on 4 CTAs,
-    // 4 systems on 8 CTAs
-    cudaError_t e = cudaSuccess;
-    if (a.V.B >= 32) {
-        e = launch_cluster<T, MP, GEN, 8, 8>(L, a, ok);
-        if (*ok || e != cudaSuccess) return e;
+    int ncl = 0;
+    const int shape = choose_shape<T, MP, GEN>(L, a.M.N, a.V.B, &ncl);
+    *ok = shape != 0;
+    switch (shape) {
+        case 416: return launch_cluster<T, MP, GEN, 4, 16>(L, a, ncl);
+        case 408: return launch_cluster<T, MP, GEN, 4, 8>(L, a, ncl);
+        case 808: return launch_cluster<T, MP, GEN, 8, 8>(L, a, ncl);
+        case 404: return launch_cluster<T, MP, GEN, 4, 4>(L, a, ncl);
+        default: return cudaSuccess;
     }
-    e = launch_cluster<T, MP, GEN, 4, 4>(L, a, ok);
-    if (*ok || e != cudaSuccess) return e;
-    return launch_cluster<T, MP, GEN, 4, 8>(L, a, ok);
+}
+
+bool cluster_qualifies(const MeshView& M, int B, bool fp64, bool mixed_iter) {
+    if (fp64 && !mixed_iter) return false;
+    if (B % 4 != 0 || B < 16 || B > 512) return false;
+    return (size_t)M.N * 2 * B < ((size_t)1 << 31);   // 32-bit element offsets in the kernel
 }
 
 }  // namespace
 
-// The cluster variant when the batch has enough systems (B a multiple of 4 and
-// at least 16), its work vectors are FP32 (FP32 solves, or FP64 solves iterated
-// in FP32), z of a cluster's systems fits its CTAs' shared memory and all
-// clusters of the launch can be resident together.  Returns 1 when launched
-// (*err: the launch's status), 0 when no shape qualifies.
+int pcg_cluster_shape(const Launch& L, const MeshView& M, int B, bool fp64, bool mixed_iter) {
+    if (L.pcg_kernel == 1 || !cluster_qualifies(M, B, fp64, mixed_iter)) return 0;
+    int ncl = 0;
+    if (fp64) return M.gen ? choose_shape<double, true, true>(L, M.N, B, &ncl)
+                           : choose_shape<double, true, false>(L, M.N, B, &ncl);
+    return M.gen ? choose_shape<float, false, true>(L, M.N, B, &ncl) : choose_shape<float, false, false>(L, M.N, B, &ncl);
+}
+
+// The cluster variant when the batch has enough systems (B a multiple of 4,
+// 16 <= B <= 512), its work vectors are FP32 (FP32 solves, or FP64 solves
+// iterated in FP32), z of a cluster's systems fits its CTAs' shared memory and
+// the clusters serving the active groups can be resident together.  Returns 1
+// when launched (*err: the launch's status), 0 when no shape qualifies.
 template <typename T>
 int pcg_solve_cluster(const Launch& L, const MeshView& M, const BatchView<T>& V, int mode, double tol, int max_iter,
                       bool mixed_iter, cudaError_t* err) {
     *err = cudaSuccess;
     const bool mp = sizeof(T) == 8;
-    if (mp && !mixed_iter) return 0;
-    const int B = V.B;
-    if (B % 4 != 0 || B < 16) return 0;
-    if ((size_t)M.N * 2 * B >= ((size_t)1 << 31)) return 0;   // 32-bit element offsets in the kernel
+    if (!cluster_qualifies(M, V.B, mp, mixed_iter)) return 0;
     PcgArgs<T> a{M, V, mode, tol * tol, max_iter, L.bar, L.err, L.sweeps, L.fin};
     bool ok = false;
     cudaError_t e;
