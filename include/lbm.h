@@ -125,6 +125,14 @@ typedef struct {
                                mesh operators) and replayed; the first chunk of a solve
                                runs uncaptured.  0: kernels launched one by one.  The
                                same kernels run in the same order: the same bits */
+    double  cg_tol_fp32;    /* relative residual of the potential solves in the FP32
+                               phase of a mixed-precision minimisation (lbm_minimise,
+                               lbm_hysteresis, served requests); 0: cg_tol.  The FP32
+                               phase only brings the state to switch_tol, and the FP64
+                               phase's solves (cg_tol_polish) fix the final accuracy,
+                               so it can take a looser tolerance than an evaluation
+                               (lbm_evaluate of a mixed instance uses cg_tol).
+                               Default 3e-5 mixed, 0 FP64 */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -144,7 +152,8 @@ typedef struct {
 
 /* Fill `o` with the defaults for `precision` (tol 1e-6, memory 20, c1 1e-4,
  * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-6 mixed,
- * switch_tol 1e-4, cg_tol_polish 1e-10, cg_mixed_iter 1 mixed / 0 FP64). */
+ * switch_tol 1e-4, cg_tol_polish 1e-10, cg_mixed_iter 1 mixed / 0 FP64,
+ * cg_tol_fp32 3e-5 mixed / 0 FP64). */
 void lbm_default_opts(lbm_solve_opts* o, int32_t precision);
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t

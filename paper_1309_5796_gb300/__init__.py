@@ -37,7 +37,7 @@ class SolveOpts(C.Structure):
                 ("demag", C.c_int32), ("check_every", C.c_int32), ("switch_tol", C.c_double),
                 ("cg_tol_polish", C.c_double), ("cg_mixed_iter", C.c_int32), ("bb_rule", C.c_int32),
                 ("method", C.c_int32), ("omega", C.c_double), ("stall_iters", C.c_int32),
-                ("pcg_kernel", C.c_int32), ("use_graphs", C.c_int32)]
+                ("pcg_kernel", C.c_int32), ("use_graphs", C.c_int32), ("cg_tol_fp32", C.c_double)]
 
 
 class ProfileStats(C.Structure):

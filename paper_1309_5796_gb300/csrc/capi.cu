@@ -451,7 +451,7 @@ int check_opts(const lbm_solve_opts& o) {
         o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
         !(o.cg_tol_polish > 0) || o.bb_rule < 0 || o.bb_rule > 3 || o.method < 0 || o.method > 1 ||
         (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)) || o.stall_iters < 0 || o.pcg_kernel < 0 ||
-        o.pcg_kernel > 2 || o.use_graphs < 0 || o.use_graphs > 1)
+        o.pcg_kernel > 2 || o.use_graphs < 0 || o.use_graphs > 1 || !(o.cg_tol_fp32 >= 0))
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -694,6 +694,7 @@ int minimise_mixed(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* r
     Mesh& M = *ctx->meshes[I->mesh];
     const auto t0 = std::chrono::steady_clock::now();
     lbm_solve_opts o1 = o;
+    if (o.cg_tol_fp32 > 0) o1.cg_tol = o.cg_tol_fp32;
     o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;   // FP32 phase; it hands a stalled
                                                             // instance to the FP64 phase
     std::vector<InstState> s1, s2;
@@ -809,6 +810,7 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->stall_iters = precision == LBM_FP64 ? 0 : 200;
     o->pcg_kernel = 0;
     o->use_graphs = 1;
+    o->cg_tol_fp32 = precision == LBM_FP64 ? 0.0 : 3e-5;
     if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
@@ -2351,6 +2353,7 @@ void serve_loop(Server* Sp) {
     cudaSetDevice(ctx->device);
     const lbm_solve_opts o = S.opt.opt;
     lbm_solve_opts o1 = o;
+    if (o.cg_tol_fp32 > 0) o1.cg_tol = o.cg_tol_fp32;
     o1.tol = o.tol > o.switch_tol ? o.tol : o.switch_tol;
     lbm_solve_opts o2 = o;
     o2.cg_tol = o.cg_tol_polish;
