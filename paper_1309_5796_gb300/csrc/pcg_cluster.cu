@@ -86,7 +86,7 @@ __device__ __forceinline__ double ld_peer_f64(uint32_t a) {
 
 // Shared-memory layout of one CTA (offsets in bytes).
 struct ClSmem {
-    size_t z, dtab, scratch, out, slots, cold, coli, total;
+    size_t z, dtab, scratch, out, slots, cold, coldf, coli, total;
 };
 __host__ __device__ inline ClSmem cl_smem(int rpc, int cpc) {
     ClSmem s;
@@ -98,6 +98,7 @@ __host__ __device__ inline ClSmem cl_smem(int rpc, int cpc) {
     s.out = take(sizeof(double) * 4 * cpc);
     s.slots = take(sizeof(double) * 2 * 4 * cpc);
     s.cold = take(sizeof(double) * 5 * cpc);
+    s.coldf = take(sizeof(float) * cpc);
     s.coli = take(sizeof(int) * 5 * cpc);
     s.total = o;
     return s;
@@ -122,6 +123,9 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
     double* s_ab = s_rhop + CPC;
     double* s_tol = s_ab + CPC;
     double* s_tin = s_tol + CPC;
+    // alpha or beta of the current step as FP32 for the row loops (a conversion
+    // from FP64 per thread would issue at GB300's FP64 rate)
+    float* s_abf = reinterpret_cast<float*>(smraw + lay.coldf);
     int* s_flag = reinterpret_cast<int*>(smraw + lay.coli);
     int* s_act = s_flag + CPC;
     int* s_cur = s_act + CPC;
@@ -265,11 +269,13 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
     // bits in every lane and every CTA of the cluster)
     auto totals = [&](const double* slot, int nq) {
         const int nv = nq * CPC;
-        double v = 0.0;
-        if (tid < nv * CL) v = ld_peer_f64(peer_u32(smem_u32(slot + tid / CL), (unsigned)(tid % CL)));
+        if ((tid >> 5) <= ((nv * CL - 1) >> 5)) {   // only the warps holding values (FP64 issues slowly)
+            double v = 0.0;
+            if (tid < nv * CL) v = ld_peer_f64(peer_u32(smem_u32(slot + tid / CL), (unsigned)(tid % CL)));
 #pragma unroll
-        for (int off = CL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (tid < nv * CL && tid % CL == 0) out[tid / CL] = v;
+            for (int off = CL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (tid < nv * CL && tid % CL == 0) out[tid / CL] = v;
+        }
         __syncthreads();
     };
     auto reduce = [&](auto& vals) {
@@ -416,6 +422,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                         conv = !s_act[tid] || rr <= s_tol[tid] || it >= A.max_iter;
                     }
                     s_ab[tid] = (it == 0 || conv) ? 0.0 : rho / s_rhop[tid];
+                    s_abf[tid] = (float)s_ab[tid];
                     s_rho[tid] = rho;
                     s_flag[tid] = conv;
                 }
@@ -426,7 +433,7 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     run |= actk[k] && !s_flag[cl0 + k];
-                    beta[k] = W(s_ab[cl0 + k]);
+                    beta[k] = s_abf[cl0 + k];
                 }
                 W tpq[1][VEC];
 #pragma unroll
@@ -525,12 +532,15 @@ __global__ void __launch_bounds__(cl_threads<CPC>(), 1) k_pcg_cluster(PcgArgs<T>
                     }
                 {
                     totals(partial(tpq), 1);
-                    if (tid < CPC) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
+                    if (tid < CPC) {
+                        s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
+                        s_abf[tid] = (float)s_ab[tid];
+                    }
                     __syncthreads();
                 }
                 W alpha[VEC];
 #pragma unroll
-                for (int k = 0; k < VEC; ++k) alpha[k] = W(s_ab[cl0 + k]);
+                for (int k = 0; k < VEC; ++k) alpha[k] = s_abf[cl0 + k];
                 W v4[4][VEC];   // r.z, r.r, (unused), sum r: thread and block sums in W, cluster sums in FP64
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) v4[0][k] = v4[1][k] = v4[2][k] = v4[3][k] = W(0);
