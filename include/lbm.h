@@ -133,6 +133,17 @@ typedef struct {
                                so it can take a looser tolerance than an evaluation
                                (lbm_evaluate of a mixed instance uses cg_tol).
                                Default 3e-5 mixed, 0 FP64 */
+    int32_t resume;         /* lbm_minimise of an LBM_FP64 instance: 1 continues from
+                               the instance's current state (lbm_set_state, or an
+                               earlier run) instead of starting anew: instances that
+                               the iteration limit (or a stall) stopped continue
+                               with the step they had prepared, counters and the
+                               nonmonotone memory carry on, converged or failed
+                               instances stay done; max_iter counts the iterations
+                               of both runs.  A run stopped by max_iter = k and
+                               resumed gives the same bits as one uninterrupted run.
+                               0 (default): start anew.  LBM_E_INVALID for mixed
+                               instances and lbm_hysteresis */
 } lbm_solve_opts;
 
 /* Per-instance outcome of a minimisation or an evaluation. */
@@ -153,7 +164,7 @@ typedef struct {
 /* Fill `o` with the defaults for `precision` (tol 1e-6, memory 20, c1 1e-4,
  * 30 halvings, kappa0 0.5, m_alpha 3, cg_tol 1e-13 FP64 / 1e-6 mixed,
  * switch_tol 1e-4, cg_tol_polish 1e-10, cg_mixed_iter 1 mixed / 0 FP64,
- * cg_tol_fp32 3e-5 mixed / 0 FP64). */
+ * cg_tol_fp32 3e-5 mixed / 0 FP64, resume 0). */
 void lbm_default_opts(lbm_solve_opts* o, int32_t precision);
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t
@@ -399,6 +410,22 @@ int lbm_bem_apply(lbm_ctx* ctx, lbm_mesh mesh, int32_t precision, int32_t batch,
  * out[1] chunks captured, out[2] captures the driver refused (those chunks run
  * their kernels one by one).  The paper has no counterpart. */
 int lbm_graph_stats(lbm_ctx* ctx, int64_t out[3]);
+
+/* ---- checkpoint / resume ----------------------------------------------------
+ * The full state of an instance batch (SURVEY's checkpoint/resume subsystem;
+ * the paper has no counterpart): per instance the step state (phase, step
+ * length, kappa, the tau^2 and energy memories, counters), constants, the
+ * magnetisation and energy gradient at the base and trial points, the forward
+ * and adjoint potentials (the warm starts of the next solves) and, with the
+ * space-transformation boundary, the grid potential; materials and fields.
+ * lbm_get_state: buf NULL -> *bytes = the size needed; else buf of *bytes
+ * bytes (host, caller-owned) receives it.  lbm_set_state: a state of an
+ * instance with the same mesh size, batch, precision and boundary; then
+ * lbm_minimise with resume = 1 continues it bit for bit.  Both wait for the
+ * context's queued work.  LBM_E_INVALID for a short buffer or a mismatched
+ * state. */
+int lbm_get_state(lbm_ctx* ctx, lbm_inst inst, void* buf, int64_t* bytes);
+int lbm_set_state(lbm_ctx* ctx, lbm_inst inst, const void* buf, int64_t bytes);
 
 /* ---- device waits ------------------------------------------------------------
  * Every device-side wait of this context's kernels (the grid barrier of the

@@ -37,7 +37,8 @@ class SolveOpts(C.Structure):
                 ("demag", C.c_int32), ("check_every", C.c_int32), ("switch_tol", C.c_double),
                 ("cg_tol_polish", C.c_double), ("cg_mixed_iter", C.c_int32), ("bb_rule", C.c_int32),
                 ("method", C.c_int32), ("omega", C.c_double), ("stall_iters", C.c_int32),
-                ("pcg_kernel", C.c_int32), ("use_graphs", C.c_int32), ("cg_tol_fp32", C.c_double)]
+                ("pcg_kernel", C.c_int32), ("use_graphs", C.c_int32), ("cg_tol_fp32", C.c_double),
+                ("resume", C.c_int32)]
 
 
 class ProfileStats(C.Structure):
@@ -115,6 +116,8 @@ SIGNATURES = [
     ("lbm_serve_trace", C.c_int, [_P, _DP, _I64, C.POINTER(_I64)]),
     ("lbm_mesh_hmatrix", C.c_int, [_P, _I64, C.c_double, C.c_double, C.c_int32, C.c_int32, C.POINTER(_I64)]),
     ("lbm_mesh_shell", C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(_I64)]),
+    ("lbm_get_state", C.c_int, [_P, _I64, C.c_void_p, C.POINTER(_I64)]),
+    ("lbm_set_state", C.c_int, [_P, _I64, C.c_void_p, _I64]),
     ("lbm_bem_apply", C.c_int, [_P, _I64, C.c_int32, C.c_int32, _DP, _DP, _DP]),
     ("lbm_default_serve_opts", None, [C.POINTER(ServeOpts)]),
     ("lbm_serve_start", C.c_int, [_P, C.POINTER(ServeOpts)]),
@@ -426,6 +429,20 @@ class Instance:
     def set_m(self, m):
         m = np.ascontiguousarray(np.broadcast_to(np.asarray(m, np.float64), (self.B, self.N, 3)))
         _check(lib().lbm_set_m(self.ctx._h, self.h, _dptr(m)))
+
+    def get_state(self) -> bytes:
+        """lbm_get_state: the batch's full state (checkpoint)."""
+        n = _I64()
+        _check(lib().lbm_get_state(self.ctx._h, self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().lbm_get_state(self.ctx._h, self.h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def set_state(self, state: bytes):
+        """lbm_set_state: restore a state written by get_state (then minimise
+        with resume=1 continues it)."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(lib().lbm_set_state(self.ctx._h, self.h, buf, len(state)))
 
     def set_m_device(self, ptr: int):
         """m from a device buffer (batch*N*3 doubles), e.g. a torch tensor's data_ptr()."""

@@ -451,7 +451,8 @@ int check_opts(const lbm_solve_opts& o) {
         o.check_every < 1 || !(o.tau_min > 0) || !(o.tau_max >= o.tau_min) || !(o.switch_tol >= 0) ||
         !(o.cg_tol_polish > 0) || o.bb_rule < 0 || o.bb_rule > 3 || o.method < 0 || o.method > 1 ||
         (o.method == 1 && !(o.omega > 0.0 && o.omega <= 2.0)) || o.stall_iters < 0 || o.pcg_kernel < 0 ||
-        o.pcg_kernel > 2 || o.use_graphs < 0 || o.use_graphs > 1 || !(o.cg_tol_fp32 >= 0))
+        o.pcg_kernel > 2 || o.use_graphs < 0 || o.use_graphs > 1 || !(o.cg_tol_fp32 >= 0) || o.resume < 0 ||
+        o.resume > 1)
         return fail(LBM_E_INVALID, "invalid solve options");
     return LBM_OK;
 }
@@ -618,7 +619,8 @@ int run_minimise(lbm_ctx* ctx, Inst* I, const lbm_solve_opts& o, lbm_result* res
     lbm_solve_opts oo = o;
     if (evaluate_only) oo.max_iter = 0;
     const StepOpts so = step_opts(oo);
-    reset_states(L, I->st, I->B, so, 0, warm ? 1 : 0);
+    if (oo.resume && !evaluate_only) resume_states(L, I->st, I->B);
+    else reset_states(L, I->st, I->B, so, 0, warm ? 1 : 0);
     const int nblk_field = field_blocks(L, mv, I->B);
     std::vector<InstState> hs(I->B);
     // instances iterating at the start of each chunk (all after the reset); the
@@ -811,6 +813,7 @@ void lbm_default_opts(lbm_solve_opts* o, int32_t precision) {
     o->pcg_kernel = 0;
     o->use_graphs = 1;
     o->cg_tol_fp32 = precision == LBM_FP64 ? 0.0 : 3e-5;
+    o->resume = 0;
     if (precision != LBM_FP64) o->cg_tol = 1e-6;
 }
 
@@ -1754,6 +1757,107 @@ int lbm_get_m(lbm_ctx* ctx, lbm_inst inst, double* m) {
     LBM_CATCH
 }
 
+// ---- full instance state (checkpoint / resume) --------------------------------------
+namespace {
+constexpr int64_t STATE_MAGIC = 0x4554415453424c4cLL;   // "LLBSTATE"
+constexpr int64_t STATE_VERSION = 1;
+struct StateParts {
+    size_t st, ic, mg, pot, shx, mats, hh, total;
+};
+StateParts state_parts(const Mesh& M, const Inst& I) {
+    StateParts p;
+    const size_t B = I.B, N = M.N;
+    size_t o = 8 * sizeof(int64_t);
+    auto take = [&o](size_t b) { const size_t at = o; o += (b + 7) & ~(size_t)7; return at; };
+    p.st = take(sizeof(InstState) * B);
+    p.ic = take(sizeof(InstConst) * B);
+    p.mg = take(sizeof(double) * 2 * 2 * N * 3 * B);             // m[2] and grad phi[2]
+    p.pot = take((size_t)I.tsize * 2 * N * 2 * B);                // U1, U2
+    p.shx = take(M.shell ? sizeof(double) * M.shell->Ng * B : 0);  // grid potential
+    p.mats = take(sizeof(lbm_material) * B);
+    p.hh = take(sizeof(double) * 3 * B);
+    p.total = o;
+    return p;
+}
+}  // namespace
+
+int lbm_get_state(lbm_ctx* ctx, lbm_inst inst, void* buf, int64_t* bytes) {
+    LBM_TRY
+    Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
+    if (!I || !bytes) return fail(LBM_E_INVALID, "lbm_get_state: bad argument");
+    const Mesh& M = *ctx->meshes[I->mesh];
+    const StateParts p = state_parts(M, *I);
+    if (!buf) {
+        *bytes = (int64_t)p.total;
+        return LBM_OK;
+    }
+    if (*bytes < (int64_t)p.total) return fail(LBM_E_INVALID, "lbm_get_state: buffer of %lld bytes, need %zu",
+                                               (long long)*bytes, p.total);
+    CK(cudaSetDevice(ctx->device));
+    char* b = (char*)buf;
+    const int64_t hdr[8] = {STATE_MAGIC, STATE_VERSION, M.N, I->B, I->tsize, M.shell ? M.shell->Ng : 0,
+                            (int64_t)p.total, 0};
+    memcpy(b, hdr, sizeof hdr);
+    const VecLayout L = vec_layout(M, I->B, I->tsize);
+    const size_t B = I->B, N = M.N;
+    CK(cudaMemcpyAsync(b + p.st, I->st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + p.ic, I->ic, sizeof(InstConst) * B, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + p.mg, (char*)I->vec + L.m, sizeof(double) * 2 * N * 3 * B, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(b + p.mg + sizeof(double) * 2 * N * 3 * B, (char*)I->vec + L.g, sizeof(double) * 2 * N * 3 * B,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    const size_t pb = (size_t)I->tsize * N * 2 * B;
+    CK(cudaMemcpyAsync(b + p.pot, (char*)I->vec + L.U1, pb, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + p.pot + pb, (char*)I->vec + L.U2, pb, cudaMemcpyDeviceToHost, ctx->stream));
+    if (M.shell)
+        CK(cudaMemcpyAsync(b + p.shx, (char*)I->vec + L.shx, sizeof(double) * M.shell->Ng * B, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    memcpy(b + p.mats, I->mats.data(), sizeof(lbm_material) * B);
+    memcpy(b + p.hh, I->h.data(), sizeof(double) * 3 * B);
+    CK(cudaStreamSynchronize(ctx->stream));
+    *bytes = (int64_t)p.total;
+    return LBM_OK;
+    LBM_CATCH
+}
+
+int lbm_set_state(lbm_ctx* ctx, lbm_inst inst, const void* buf, int64_t bytes) {
+    LBM_TRY
+    Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
+    if (!I || !buf) return fail(LBM_E_INVALID, "lbm_set_state: bad argument");
+    const Mesh& M = *ctx->meshes[I->mesh];
+    const StateParts p = state_parts(M, *I);
+    const char* b = (const char*)buf;
+    int64_t hdr[8];
+    if (bytes < (int64_t)sizeof hdr) return fail(LBM_E_INVALID, "lbm_set_state: buffer too short");
+    memcpy(hdr, b, sizeof hdr);
+    if (hdr[0] != STATE_MAGIC || hdr[1] != STATE_VERSION)
+        return fail(LBM_E_INVALID, "lbm_set_state: not a state written by lbm_get_state of this version");
+    if (hdr[2] != M.N || hdr[3] != I->B || hdr[4] != I->tsize || hdr[5] != (M.shell ? M.shell->Ng : 0) ||
+        hdr[6] != (int64_t)p.total || bytes < (int64_t)p.total)
+        return fail(LBM_E_INVALID, "lbm_set_state: the state is of another mesh size, batch, precision or boundary");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const VecLayout L = vec_layout(M, I->B, I->tsize);
+    const size_t B = I->B, N = M.N;
+    CK(cudaMemcpyAsync(I->st, b + p.st, sizeof(InstState) * B, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(I->ic, b + p.ic, sizeof(InstConst) * B, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync((char*)I->vec + L.m, b + p.mg, sizeof(double) * 2 * N * 3 * B, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync((char*)I->vec + L.g, b + p.mg + sizeof(double) * 2 * N * 3 * B, sizeof(double) * 2 * N * 3 * B,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    const size_t pb = (size_t)I->tsize * N * 2 * B;
+    CK(cudaMemcpyAsync((char*)I->vec + L.U1, b + p.pot, pb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync((char*)I->vec + L.U2, b + p.pot + pb, pb, cudaMemcpyHostToDevice, ctx->stream));
+    if (M.shell)
+        CK(cudaMemcpyAsync((char*)I->vec + L.shx, b + p.shx, sizeof(double) * M.shell->Ng * B, cudaMemcpyHostToDevice,
+                           ctx->stream));
+    I->mats.assign((const lbm_material*)(b + p.mats), (const lbm_material*)(b + p.mats) + B);
+    I->h.assign((const double*)(b + p.hh), (const double*)(b + p.hh) + 3 * B);
+    CK(cudaStreamSynchronize(ctx->stream));   // the caller's buffer may go away
+    return LBM_OK;
+    LBM_CATCH
+}
+
 int lbm_evaluate(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, double* h, double* u, lbm_result* res) {
     LBM_TRY
     Inst* I = ctx ? get_inst(ctx, inst) : nullptr;
@@ -1793,6 +1897,7 @@ int lbm_minimise(lbm_ctx* ctx, lbm_inst inst, const lbm_solve_opts* opt, lbm_res
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
     if (I->tsize == 8) return run_minimise<double>(ctx, I, o, res, false, nullptr, nullptr);
+    if (o.resume) return fail(LBM_E_INVALID, "resume applies to LBM_FP64 instances (a mixed run has two batches)");
     return minimise_mixed(ctx, I, o, res);
     LBM_CATCH
 }
@@ -1894,6 +1999,7 @@ extern "C" int lbm_evaluate_noalloc(lbm_ctx* ctx, lbm_mesh mesh, const lbm_mater
     lbm_solve_opts o;
     if (opt) o = *opt; else lbm_default_opts(&o, LBM_FP64);
     int rc = check_opts(o);
+    if (o.resume) return fail(LBM_E_INVALID, "lbm_hysteresis: resume is not supported (every field point starts anew)");
     if (rc) return rc;
     if (ctx->device < 0 || ctx->device >= 64) return fail(LBM_E_INVALID, "device index out of range");
     CK(cudaSetDevice(ctx->device));
@@ -2033,6 +2139,7 @@ __global__ void k_slot_reset(InstState* st, int b, int phase) {
     s.iters = s.evals = s.line_searches = s.backtracks = 0;
     s.nhist = s.hpos = s.ntau2 = 0;
     s.warm = 0;
+    s.next_phase = PH_DONE;
     s.cg1 = s.cg2 = 0;
 }
 

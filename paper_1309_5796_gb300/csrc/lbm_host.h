@@ -285,6 +285,8 @@ void unpack_field(const Launch& L, const MeshView& M, const BatchView<T>& V, dou
 // warm: keep each instance's step state (tau, kappa, tau^2 memory) for the
 // first step after the first evaluation (a new precision phase at the same point)
 void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0, int warm = 0);
+// continue the instances stopped by the iteration limit or a stall (resume)
+void resume_states(const Launch& L, InstState* st, int B);
 
 // ---- tensor-core BEM products (tc_gemm.cu) ------------------------------------------
 int tc_ld(int nb);

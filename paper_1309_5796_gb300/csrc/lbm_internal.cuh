@@ -64,6 +64,8 @@ struct InstState {
     int best_iter;                 // the iteration where it was reached
     int warm;                      // 1: the first evaluation resumes the step state (tau, kappa,
                                    // tau^2 memory) of a previous phase instead of a line search
+    int next_phase;                // after a stop by the iteration limit or a stall: the phase the
+                                   // iteration would have continued in (lbm_solve_opts.resume)
     double terms[4];
     double mean_m[3];
     double hist[HIST_MAX];

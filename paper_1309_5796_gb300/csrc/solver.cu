@@ -1310,25 +1310,25 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
         s.best_torque = torque;
         s.best_iter = 0;
         if (conv) { s.status = 0; s.phase = PH_DONE; return; }
-        if (so.max_iter <= 0) { s.status = 3; s.phase = PH_DONE; return; }
         if (warm) {
             // a new precision phase at the point where the previous one stopped:
             // its next BB step (and kappa, tau^2 memory) continues the iteration;
             // the nonmonotone test against this evaluation's energy guards it
             s.tau = fmin(fmax(s.tau, so.tau_min), so.tau_max);
             s.phase = PH_BB;
-            return;
-        }
-        if (so.method == 1) {
+        } else if (so.method == 1) {
             s.tau = so.omega;
             s.phase = PH_LB;
             s.line_searches = 0;
-            return;
+        } else {
+            s.tau = 1.0 / v[Q_HMAX];
+            s.phase = PH_SEARCH;
+            s.E_ref = E;
+            s.line_searches = 1;
         }
-        s.tau = 1.0 / v[Q_HMAX];
-        s.phase = PH_SEARCH;
-        s.E_ref = E;
-        s.line_searches = 1;
+        // the iteration limit stops after the next step is prepared: a resumed
+        // run continues from next_phase exactly where this one would have gone on
+        if (so.max_iter <= 0) { s.next_phase = s.phase; s.status = 3; s.phase = PH_DONE; }
         return;
     }
     s.hist[s.hpos] = E;
@@ -1336,18 +1336,22 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     if (s.nhist < mem) s.nhist += 1;
     s.iters += 1;
     if (conv) { s.status = 0; s.phase = PH_DONE; return; }
-    if (s.iters >= so.max_iter) { s.status = 3; s.phase = PH_DONE; return; }
+    // the iteration limit and a stall stop after the next step is prepared (tau,
+    // kappa, tau^2 memory), so that a resumed run continues from next_phase
+    // exactly as this one would have gone on
+    bool stop = s.iters >= so.max_iter;
     // progress = the smallest torque so far halved; a phase that creeps (new
     // minima, but no halving within stall_iters steps) has stalled
     if (torque < 0.5 * s.best_torque) {
         s.best_torque = torque;
         s.best_iter = s.iters;
     } else if (so.stall_iters > 0 && s.iters - s.best_iter >= so.stall_iters) {
-        s.status = 3;
-        s.phase = PH_DONE;
+        stop = true;
+    }
+    if (s.phase == PH_LB) {   // LaBonte: the next step uses the same relaxation
+        if (stop) { s.next_phase = PH_LB; s.status = 3; s.phase = PH_DONE; }
         return;
     }
-    if (s.phase == PH_LB) return;   // LaBonte: the next step uses the same relaxation
     const double ss = v[Q_SS], sy = v[Q_SY], yy = v[Q_YY];
     double tau = 1.0 / v[Q_HMAX];   // s.y <= 0: restart with the first-step trial
     if (sy > 0.0 && so.bb_rule != 0) {
@@ -1377,6 +1381,7 @@ __global__ void k_decide(const double* __restrict__ part, int nblk, InstState* s
     s.tau = fmin(fmax(tau, so.tau_min), so.tau_max);
     s.phase = PH_BB;
     s.backtracks = 0;
+    if (stop) { s.next_phase = PH_BB; s.status = 3; s.phase = PH_DONE; }
 }
 
 template <typename T>
@@ -1472,12 +1477,27 @@ __global__ void k_reset(InstState* st, int B, int set_cur0, int warm) {
     s.nhist = s.hpos = 0;
     if (!warm) s.ntau2 = 0;   // warm: tau, kappa and the tau^2 memory are kept
     s.warm = warm;
+    s.next_phase = PH_DONE;
     s.cg1 = s.cg2 = 0;
 }
 
 void reset_states(const Launch& L, InstState* st, int B, const StepOpts& so, int set_cur0, int warm) {
     (void)so;
     k_reset<<<(B + 127) / 128, 128, 0, L.stream>>>(st, B, set_cur0, warm);
+    *L.launches += 1;
+}
+
+// Continue instances that the iteration limit (or a stall) stopped, from the
+// step they had prepared; converged and failed instances stay done.
+__global__ void k_resume(InstState* st, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    InstState& s = st[b];
+    if (s.phase == PH_DONE && s.status == 3 && s.next_phase != PH_DONE) s.phase = s.next_phase;
+}
+
+void resume_states(const Launch& L, InstState* st, int B) {
+    k_resume<<<(B + 127) / 128, 128, 0, L.stream>>>(st, B);
     *L.launches += 1;
 }
 

@@ -157,7 +157,7 @@ def test_default_options_are_the_documented_ones(library):
     documents (no GPU needed)."""
     import ctypes as C
     common = dict(tol=1e-6, grad_tol=0.0, memory=20, c1=1e-4, max_backtracks=30, kappa0=0.5, m_alpha=3,
-                  switch_tol=1e-4, cg_tol_polish=1e-10, bb_rule=0, method=0, omega=1.0, demag=1)
+                  switch_tol=1e-4, cg_tol_polish=1e-10, bb_rule=0, method=0, omega=1.0, demag=1, resume=0)
     per = {lbm.LBM_FP64: dict(cg_tol=1e-13, cg_mixed_iter=0, stall_iters=0, cg_tol_fp32=0.0),
            lbm.LBM_MIXED: dict(cg_tol=1e-6, cg_mixed_iter=1, stall_iters=200, cg_tol_fp32=3e-5),
            lbm.LBM_MIXED_TC: dict(cg_tol=1e-6, cg_mixed_iter=1, stall_iters=200, cg_tol_fp32=3e-5)}
