@@ -160,6 +160,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_shell_pcg(ShellArgs<W> A) {
     int* s_act = s_flag + B;
     int* s_it = s_act + B;
     int* s_done = s_it + B;
+    // alpha or beta of the current step in W for the row loops (a conversion from
+    // FP64 per thread would issue at GB300's FP64 rate)
+    W* s_abw = reinterpret_cast<W*>(s_done + B);   // 8-byte aligned: four int arrays of B
     for (int i = tid; i < B; i += bd) {
         s_act[i] = A.st[i].phase != PH_DONE;
         s_it[i] = 0;
@@ -250,6 +253,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_shell_pcg(ShellArgs<W> A) {
                 const double rho = out[tid], rr = out[B + tid];
                 const int conv = s_done[tid] || rr <= s_tin[tid] || s_it[tid] >= A.max_iter;
                 s_ab[tid] = (it == 0 || conv) ? 0.0 : rho / s_rhop[tid];
+                s_abw[tid] = W(s_ab[tid]);
                 s_rho[tid] = rho;
                 s_flag[tid] = conv;
             }
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_shell_pcg(ShellArgs<W> A) {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
                 run[k] = act[k] && !s_flag[c0 + k];
-                beta[k] = W(s_ab[c0 + k]);
+                beta[k] = s_abw[c0 + k];
             }
             W v[4][VEC];
 #pragma unroll
@@ -288,12 +292,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_shell_pcg(ShellArgs<W> A) {
                 }
             block_reduce_cols<4, VEC, W>(v, reinterpret_cast<W*>(scratch), out, B, G, RB);
             if (!publish()) return;
-            if (tid < B) s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
+            if (tid < B) {
+                s_ab[tid] = s_flag[tid] ? 0.0 : s_rho[tid] / out[tid];
+                s_abw[tid] = W(s_ab[tid]);
+            }
             __syncthreads();
             W alpha[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-                alpha[k] = W(s_ab[c0 + k]);
+                alpha[k] = s_abw[c0 + k];
                 v[0][k] = v[1][k] = v[2][k] = v[3][k] = W(0);
             }
             // two rows per pass (a stream: every load first); outer-face rows
@@ -397,7 +404,7 @@ int launch_shell(const Launch& L, const ShellDev& S, const double* bvec, double*
                  const InstState* st, double tol, int max_iter) {
     const int G = B / VEC, RB = THREADS / G;
     const int nrow = (G <= 32 && (32 % G) == 0) ? (THREADS >> 5) : RB;
-    const size_t smem = sizeof(double) * (4 * (size_t)nrow * B + 9 * (size_t)B) + sizeof(int) * 4 * B;
+    const size_t smem = sizeof(double) * (4 * (size_t)nrow * B + 9 * (size_t)B) + sizeof(int) * 4 * B + sizeof(W) * B;
     const void* fn = (const void*)k_shell_pcg<W, RES64, THREADS, VEC>;
     int occ = 1;
     cudaError_t e = kernel_smem_attr(fn, 160 * 1024, THREADS, smem, &occ);
