@@ -91,7 +91,7 @@ typedef struct {
     int32_t cg_mixed_iter;  /* FP64 potential solves (LBM_FP64 runs and the FP64
                                phase of mixed runs): 1 = CG iterations in FP32 with
                                the FP64 residual recomputed whenever they have
-                               reduced it 1e5-fold (restarted CG), the solve ending
+                               reduced it 1e4-fold (restarted CG), the solve ending
                                on the FP64 residual test; 0 = plain FP64 PCG.
                                Default 1 for LBM_MIXED / LBM_MIXED_TC, 0 for
                                LBM_FP64 */

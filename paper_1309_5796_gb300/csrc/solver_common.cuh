@@ -166,7 +166,7 @@ __device__ __forceinline__ void vstore(T* p, const T (&d)[VEC]) {
     }
 }
 
-constexpr double MP_INNER = 1e-5;   // residual reduction of one FP32 cycle of a mixed-iteration solve
+constexpr double MP_INNER = 1e-4;   // residual reduction of one FP32 cycle of a mixed-iteration solve
 constexpr int MP_MAX_CYCLES = 16;
 constexpr int MAXK = 8;   // stiffness entries served by the unrolled gather (interior Kuhn rows: 7)
 
