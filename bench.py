@@ -344,7 +344,7 @@ def run_reference(args, ws, rank):
 # kernels, from one ncu capture each of the batched workload (profiles/), used to
 # report the roofline's measured traffic per launch: (bytes/ms) x average launch ms.
 PROFILED_DRAM_BYTES_PER_MS = {
-    "fp32": (1387.8e6 / 9.128, "profiles/k_pcg_cluster_fp32_batched64_n30.md"),
+    "fp32": (1109.2e6 / 6.216, "profiles/k_pcg_cluster_fp32_batched64_n30.md"),
 }
 
 
