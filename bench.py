@@ -472,8 +472,8 @@ def large_leg(local, n, hm_eps, max_iter=100000, warmup=1):
 
 
 # DRAM bytes per ms of k_shell_pcg kernel time from the ncu capture in
-# profiles/k_shell_pcg_fp32_batched64_n30_shell4x8.md (185.03 GB in 38.277 ms)
-PROFILED_SHELL_DRAM_BYTES_PER_MS = 185.03e9 / 38.277
+# profiles/k_shell_pcg_fp32_batched64_n30_shell4x8.md (185.02 GB in 37.659 ms)
+PROFILED_SHELL_DRAM_BYTES_PER_MS = 185.02e9 / 37.659
 
 
 def shell_leg(ctx, local, insts, a=4, s=8, precision="mixed"):
