@@ -412,7 +412,7 @@ int lbm_bem_apply(lbm_ctx* ctx, lbm_mesh mesh, int32_t precision, int32_t batch,
 int lbm_graph_stats(lbm_ctx* ctx, int64_t out[3]);
 
 /* ---- checkpoint / resume ----------------------------------------------------
- * The full state of an instance batch (SURVEY's checkpoint/resume subsystem;
+ * The full state of an instance batch (checkpoint and resume of a solve;
  * the paper has no counterpart): per instance the step state (phase, step
  * length, kappa, the tau^2 and energy memories, counters), constants, the
  * magnetisation and energy gradient at the base and trial points, the forward
